@@ -1,0 +1,150 @@
+/* tcurve.h -- C ABI of the GB300 T-curve real-scheme engine (libtcurve.so).
+ *
+ * The engine computes, for a unimodular triangulation T of d*Delta_2 and a
+ * batch of sign distributions sigma: A -> F_2, the real scheme (isotopy type
+ * in RP^2) of the patchworked curve C(T, sigma) with Algorithm 1 of
+ * "Fast Isotopy Computation for T-Curves" (Sec. 2), on the GPU.
+ *
+ * Conventions (the paper fixes none of them):
+ *  - Lattice point set A = {(i,j) : i,j >= 0, i+j <= d} (Eq. 1); lattice
+ *    index k(i,j) = j*(d+1) - j*(j-1)/2 + i.
+ *  - A sign vector is ts_sign_words(tri) little-endian uint64 words; bit k
+ *    (word k/64, bit k%64) is sigma at lattice index k.  Bit 1 means a
+ *    negative coefficient: the coefficient of x^i y^j is (-1)^sigma(i,j)
+ *    (Thm. 1).  Bits at positions >= |A| must be zero.
+ *  - A scheme code is ts_code_words(tri) little-endian uint64 words holding
+ *    the integer (1 << nbits) | bits, where bits is the canonical encoding of
+ *    the nesting tree of the ovals: enc(oval) = '1' . (encodings of the ovals
+ *    directly inside it, in descending lexicographic order) . '0', and bits =
+ *    the encodings of the outermost ovals in descending order (MSB first);
+ *    nbits = 2 * #ovals.  The pseudoline of odd degree is implied by d.
+ *    Code 0 is never a valid scheme; it marks an instance that failed.
+ *  - Pointers documented as "device" must be CUDA device (or managed)
+ *    memory; "host" pointers are ordinary host memory.  Streams are passed
+ *    as void* holding a cudaStream_t (NULL = the legacy default stream).
+ *  - The caller owns every buffer it passes; the engine owns ts_tri and
+ *    ts_hist objects.  A ts_tri is immutable after loading and may be shared
+ *    by concurrent launches; a ts_hist must not be written by two
+ *    overlapping launches unless both are ts_enumerate calls (they merge by
+ *    atomics).
+ *  - There is no CPU fallback: without a usable CUDA device every call that
+ *    needs one returns TS_ECUDA.
+ */
+#ifndef TCURVE_H
+#define TCURVE_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ts_tri ts_tri;   /* a loaded triangulation (host + device tables) */
+typedef struct ts_hist ts_hist; /* a device hash histogram: scheme code -> count  */
+
+typedef enum ts_status {
+  TS_OK = 0,
+  TS_EINVAL = 1,       /* bad argument (range, null pointer, stray sign bits) */
+  TS_ENOTTRI = 2,      /* edges are not a unimodular triangulation of d*Delta_2 */
+  TS_ENOMEM = 3,       /* host or device allocation failed */
+  TS_ECUDA = 4,        /* CUDA error or no usable device */
+  TS_EOVERFLOW = 5,    /* histogram or output capacity exceeded */
+  TS_ETIMEOUT = 6,     /* a bounded device wait gave up */
+  TS_EINTERNAL = 7,    /* an instance violated an invariant (no unique root,
+                          region graph not a tree, scratch overflow) */
+  TS_EUNSUPPORTED = 8  /* degree outside the range this build supports */
+} ts_status;
+
+/* Flags of ts_enumerate. */
+#define TS_ENUM_FLIP 1u    /* mask = k << 1: one representative per global sign flip */
+#define TS_ENUM_REDUCED 2u /* zeros inserted at bits 0, 1, d+1 (sigma(0,0) = sigma(1,0) =
+                              sigma(0,1) = 0): one representative per (Z/2)^3 class (Sec. 3) */
+
+/* Human-readable name of a status code; never NULL. */
+const char *ts_status_str(int status);
+
+/* Largest degree this build supports. */
+int ts_max_degree(void);
+
+/* Load a triangulation T of d*Delta_2 given by its edge list (Sec. 2: "a
+ * triangulation ... represented by its edge list").
+ *   d        degree, 1 <= d <= ts_max_degree()
+ *   edges_ij host, n_edges rows of 4 int32 (i1, j1, i2, j2), each a pair of
+ *            lattice points of A; order and orientation are free
+ *   out      receives the new object (owned by the engine; free with
+ *            ts_free_triangulation)
+ * Validation (TS_ENOTTRI): every end point in A, no repeated edge, exactly
+ * d*d triangles (3-cliques of edges of area 1/2), every point of A used,
+ * each edge on the boundary of d*Delta_2 in one triangle and every other
+ * edge in two.  Regularity is not checked: Algorithm 1 does not need it
+ * (proof of Thm. 2).  Builds the reflected triangulation T^diamond (Alg. 1,
+ * line 1), its vertex sweep order and tables, and uploads them to the
+ * current CUDA device. */
+ts_status ts_load_triangulation(int d, const int32_t *edges_ij, int n_edges, ts_tri **out);
+void ts_free_triangulation(ts_tri *tri);
+
+int ts_degree(const ts_tri *tri);
+int ts_num_points(const ts_tri *tri);  /* |A| = (d+1)(d+2)/2 (Eq. 1) */
+int ts_sign_words(const ts_tri *tri);  /* ceil(|A| / 64)            */
+/* ceil((2*nmax + 1) / 64) with nmax = M for even d and M-1 for odd d,
+ * M = (d-1)(d-2)/2 + 1 Harnack's bound (Sec. 2). */
+int ts_code_words(const ts_tri *tri);
+
+/* Real schemes of n sign vectors (Algorithm 1 per instance).
+ *   signs     device, n * ts_sign_words(tri) uint64, read-only
+ *   out_codes device, n * ts_code_words(tri) uint64, written
+ * Asynchronous on `stream`; returns TS_OK once launched.  Instances that
+ * fail an invariant get code 0 and raise TS_EINTERNAL (TS_EOVERFLOW if the
+ * scheme exceeds Harnack's bound) in the triangulation's error word, which
+ * ts_sync reports.  Sign bits >= |A| are ignored. */
+ts_status ts_real_schemes(const ts_tri *tri, const uint64_t *signs, uint64_t n,
+                          uint64_t *out_codes, void *stream);
+
+/* Same computation with host buffers: copies signs to the device, runs,
+ * copies codes back and synchronises (allocates device memory per call).
+ * Returns the error status of the run. */
+ts_status ts_real_schemes_host(const ts_tri *tri, const uint64_t *signs_host, uint64_t n,
+                               uint64_t *codes_host);
+
+/* Wait for `stream`, then return and clear the triangulation's device error
+ * word (TS_OK if no instance failed since the last call). */
+ts_status ts_sync(const ts_tri *tri, void *stream);
+
+/* Device hash histogram of scheme codes with room for `capacity` distinct
+ * codes of `code_words` words each (rounded up to a power of two, x2). */
+ts_status ts_hist_create(uint64_t capacity, int code_words, ts_hist **out);
+void ts_hist_free(ts_hist *hist);
+/* Reset counts and error state (asynchronous on stream). */
+ts_status ts_hist_clear(ts_hist *hist, void *stream);
+
+/* Exhaustive sweep (Sec. 3, "check all sign distributions for one or a few
+ * triangulations"): adds the scheme of every mask m(k), k in [lo, hi), to
+ * `hist`.  m(k) = k by default; k << 1 with TS_ENUM_FLIP; k with zero bits
+ * inserted at positions 0, 1 and d+1 with TS_ENUM_REDUCED.  Requires
+ * m(hi-1) < 2^|A| and |A| <= 64 (d <= 9).  One persistent launch on
+ * `stream`; asynchronous.  Failed instances are counted, not inserted, and
+ * set the histogram's error word. */
+ts_status ts_enumerate(const ts_tri *tri, uint64_t lo, uint64_t hi, uint32_t flags,
+                       ts_hist *hist, void *stream);
+
+/* Copy the histogram to the host, sorted by code (little-endian word
+ * order, most significant word first in the comparison).  Synchronises
+ * `stream`.
+ *   codes   host, cap * code_words uint64 (may be NULL when cap == 0)
+ *   counts  host, cap uint64
+ *   n_out   receives the number of distinct codes
+ *   n_failed (may be NULL) receives the number of failed instances
+ * Returns TS_EOVERFLOW if n_out > cap (nothing beyond cap is written) or if
+ * the device table overflowed; otherwise the histogram's error status. */
+ts_status ts_hist_read(ts_hist *hist, uint64_t *codes, uint64_t *counts, uint64_t cap,
+                       uint64_t *n_out, uint64_t *n_failed, void *stream);
+
+/* Rohlin-Viro notation of a code (Sec. 2): "<0>", "<J>", "<4>", "<1<1>>",
+ * "<J + 1<1> + 2>" ('+' stands for the disjoint union); writes at most len
+ * bytes including the terminating NUL. */
+ts_status ts_scheme_string(int d, const uint64_t *code, int code_words, char *buf, size_t len);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,233 @@
+"""GB300 engine for the real schemes of T-curves (Algorithm 1, Sec. 2 of
+"Fast Isotopy Computation for T-Curves").
+
+This package is a thin ctypes binding of the C ABI in include/tcurve.h
+(libtcurve.so, built in-tree by ``build.build()``).  It only marshals
+arguments: every step of the computation runs in the library's sm_103a
+kernels.  PyTorch provides device memory and streams.  If the library is
+missing, every entry point raises; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+TS_ENUM_FLIP = 1
+TS_ENUM_REDUCED = 2
+
+STATUS = {0: "TS_OK", 1: "TS_EINVAL", 2: "TS_ENOTTRI", 3: "TS_ENOMEM", 4: "TS_ECUDA",
+          5: "TS_EOVERFLOW", 6: "TS_ETIMEOUT", 7: "TS_EINTERNAL", 8: "TS_EUNSUPPORTED"}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class TSError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = int(status)
+        name = STATUS.get(self.status, str(status))
+        super().__init__(f"{what}: {name}" if what else name)
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_build.LIB):
+                raise ImportError(f"libtcurve.so is not built ({_build.LIB}); run "
+                                  "paper_2604_09221_gb300.build.build() first")
+            L = ctypes.CDLL(_build.LIB)
+            P, U64, I = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int
+            sig = {
+                "ts_status_str": ([I], ctypes.c_char_p),
+                "ts_max_degree": ([], I),
+                "ts_load_triangulation": ([I, P, I, ctypes.POINTER(P)], I),
+                "ts_free_triangulation": ([P], None),
+                "ts_degree": ([P], I),
+                "ts_num_points": ([P], I),
+                "ts_sign_words": ([P], I),
+                "ts_code_words": ([P], I),
+                "ts_real_schemes": ([P, P, U64, P, P], I),
+                "ts_real_schemes_host": ([P, P, U64, P], I),
+                "ts_sync": ([P, P], I),
+                "ts_hist_create": ([U64, I, ctypes.POINTER(P)], I),
+                "ts_hist_free": ([P], None),
+                "ts_hist_clear": ([P, P], I),
+                "ts_enumerate": ([P, U64, U64, ctypes.c_uint32, P, P], I),
+                "ts_hist_read": ([P, P, P, U64, ctypes.POINTER(U64), ctypes.POINTER(U64), P], I),
+                "ts_scheme_string": ([I, P, I, ctypes.c_char_p, ctypes.c_size_t], I),
+            }
+            for name, (args, res) in sig.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = L
+    return _lib
+
+
+def library():
+    """The loaded ctypes library (raises if it is not built)."""
+    return _load()
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        raise TSError(status, what)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def max_degree() -> int:
+    return _load().ts_max_degree()
+
+
+class Triangulation:
+    """A loaded triangulation (ts_tri).  ``edges`` is an (E, 4) array of
+    lattice-point pairs (i1, j1, i2, j2) of d*Delta_2 (Sec. 2)."""
+
+    def __init__(self, d: int, edges):
+        e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 4))
+        h = ctypes.c_void_p()
+        _check(_load().ts_load_triangulation(int(d), e.ctypes.data, len(e), ctypes.byref(h)),
+               "ts_load_triangulation")
+        self._h = h
+        self.d = int(d)
+        self.sign_words = _lib.ts_sign_words(h)
+        self.code_words = _lib.ts_code_words(h)
+        self.num_points = _lib.ts_num_points(h)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.ts_free_triangulation(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def real_schemes(self, signs, out=None, stream=None, sync: bool = True):
+        """Codes of the sign vectors in ``signs`` (a CUDA int64/uint64 tensor of
+        shape (n, sign_words) or (n,)).  Returns an int64 tensor (n, code_words)
+        of code words on the same device.  With ``sync`` the call waits and
+        raises on instance errors (ts_sync)."""
+        import torch
+        if not signs.is_cuda:
+            raise ValueError("signs must be a CUDA tensor (use real_schemes_host for host arrays)")
+        s = signs.contiguous()
+        n = s.numel() // self.sign_words
+        if out is None:
+            out = torch.empty((n, self.code_words), dtype=torch.int64, device=s.device)
+        st = _stream_handle(stream)
+        _check(_lib.ts_real_schemes(self._h, s.data_ptr(), n, out.data_ptr(), st), "ts_real_schemes")
+        if sync:
+            _check(_lib.ts_sync(self._h, st), "ts_sync")
+        return out
+
+    def real_schemes_host(self, signs: np.ndarray) -> np.ndarray:
+        """Host-buffer variant (copies in and out inside the call)."""
+        s = np.ascontiguousarray(np.asarray(signs, dtype=np.uint64).reshape(-1, self.sign_words))
+        out = np.zeros((s.shape[0], self.code_words), dtype=np.uint64)
+        _check(_lib.ts_real_schemes_host(self._h, s.ctypes.data, s.shape[0], out.ctypes.data),
+               "ts_real_schemes_host")
+        return out
+
+    def sync(self, stream=None):
+        _check(_lib.ts_sync(self._h, _stream_handle(stream)), "ts_sync")
+
+
+class Histogram:
+    """Device hash histogram (ts_hist) of scheme codes."""
+
+    def __init__(self, capacity: int = 4096, code_words: int = 1):
+        h = ctypes.c_void_p()
+        _check(_load().ts_hist_create(int(capacity), int(code_words), ctypes.byref(h)),
+               "ts_hist_create")
+        self._h = h
+        self.code_words = int(code_words)
+        self.capacity = int(capacity)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.ts_hist_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def clear(self, stream=None):
+        _check(_lib.ts_hist_clear(self._h, _stream_handle(stream)), "ts_hist_clear")
+
+    def read(self, stream=None, cap: int | None = None):
+        """(codes (n, code_words) uint64, counts (n,) uint64, n_failed), sorted by code."""
+        cap = self.capacity if cap is None else int(cap)
+        codes = np.zeros((max(cap, 1), self.code_words), dtype=np.uint64)
+        counts = np.zeros(max(cap, 1), dtype=np.uint64)
+        n = ctypes.c_uint64()
+        nf = ctypes.c_uint64()
+        _check(_lib.ts_hist_read(self._h, codes.ctypes.data, counts.ctypes.data, cap,
+                                 ctypes.byref(n), ctypes.byref(nf), _stream_handle(stream)),
+               "ts_hist_read")
+        k = n.value
+        return codes[:k], counts[:k], nf.value
+
+
+def enumerate_schemes(tri: Triangulation, lo: int, hi: int, hist: Histogram, flags: int = 0,
+                      stream=None):
+    """Add the schemes of masks m(k), k in [lo, hi), to ``hist`` (ts_enumerate)."""
+    _check(_lib.ts_enumerate(tri.handle, int(lo), int(hi), int(flags), hist.handle,
+                             _stream_handle(stream)), "ts_enumerate")
+
+
+def scheme_string(d: int, code) -> str:
+    """Rohlin-Viro notation of a code (int or word array)."""
+    if isinstance(code, (int, np.integer)):
+        c = int(code)
+        words = []
+        while True:
+            words.append(c & ((1 << 64) - 1))
+            c >>= 64
+            if not c:
+                break
+        arr = np.array(words, dtype=np.uint64)
+    else:
+        arr = np.ascontiguousarray(np.asarray(code, dtype=np.uint64).ravel())
+    buf = ctypes.create_string_buffer(4096)
+    _check(_load().ts_scheme_string(int(d), arr.ctypes.data, len(arr), buf, len(buf)),
+           "ts_scheme_string")
+    return buf.value.decode()
+
+
+def code_to_int(words) -> int:
+    v = 0
+    for k, w in enumerate(np.asarray(words).astype(np.uint64).ravel().tolist()):
+        v |= int(w) << (64 * k)
+    return v

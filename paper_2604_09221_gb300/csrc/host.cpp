@@ -1,0 +1,456 @@
+// host.cpp -- host side of libtcurve: validation of the input triangulation,
+// construction of the reflected triangulation T^diamond (Alg. 1, line 1) and
+// of the per-vertex tables the kernels stage into shared memory, device
+// object management and the C ABI of include/tcurve.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <set>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "engine.h"
+
+using namespace tcurve;
+
+namespace {
+
+int lattice_index(int d, int i, int j) { return j * (d + 1) - j * (j - 1) / 2 + i; }
+
+int harnack(int d) { return (d - 1) * (d - 2) / 2 + 1; }
+
+struct Pt {
+  int x, y;
+  bool operator<(const Pt &o) const { return y != o.y ? y < o.y : x < o.x; }
+  bool operator==(const Pt &o) const { return x == o.x && y == o.y; }
+};
+
+long cross(int ax, int ay, int bx, int by) { return (long)ax * by - (long)ay * bx; }
+
+// Triangles of T from the edge list: 3-cliques of area 1/2 (unimodular).
+// Returns false if the edges do not form a unimodular triangulation.
+bool triangles_of(int d, const int32_t *e, int n_edges, std::vector<std::array<Pt, 3>> &tris) {
+  std::map<Pt, std::set<Pt>> nb;
+  for (int r = 0; r < n_edges; ++r) {
+    Pt a{e[4 * r], e[4 * r + 1]}, b{e[4 * r + 2], e[4 * r + 3]};
+    for (const Pt &p : {a, b})
+      if (p.x < 0 || p.y < 0 || p.x + p.y > d) return false;
+    if (a == b || nb[a].count(b)) return false;
+    nb[a].insert(b);
+    nb[b].insert(a);
+  }
+  if ((int)nb.size() != (d + 1) * (d + 2) / 2) return false;  // every point used
+  std::map<std::pair<Pt, Pt>, int> uses;
+  for (auto &kv : nb) {
+    const Pt &a = kv.first;
+    for (const Pt &b : kv.second) {
+      if (!(a < b)) continue;
+      for (const Pt &c : kv.second) {
+        if (!(b < c) || !nb[b].count(c)) continue;
+        long o = cross(b.x - a.x, b.y - a.y, c.x - a.x, c.y - a.y);
+        if (o != 1 && o != -1) continue;
+        tris.push_back(o > 0 ? std::array<Pt, 3>{a, b, c} : std::array<Pt, 3>{a, c, b});
+        uses[{a, b}]++;
+        uses[{a, c}]++;
+        uses[{b, c}]++;
+      }
+    }
+  }
+  if ((int)tris.size() != d * d) return false;
+  for (auto &kv : nb)
+    for (const Pt &b : kv.second) {
+      const Pt &a = kv.first;
+      if (!(a < b)) continue;
+      bool side = (a.x == 0 && b.x == 0) || (a.y == 0 && b.y == 0) ||
+                  (a.x + a.y == d && b.x + b.y == d);
+      auto it = uses.find({a, b});
+      int u = it == uses.end() ? 0 : it->second;
+      if (u != (side ? 1 : 2)) return false;
+    }
+  return true;
+}
+
+// Build T^diamond and the sweep tables.
+//
+// Sweep order: diamond vertices sorted by (y, x).  The "back neighbours" of
+// v (neighbours earlier in the sweep) lie in the half-plane below v plus its
+// left neighbour, so in angular order they form one fan, and two entries
+// that are consecutive in that order span a triangle with v unless the fan
+// is cut by the boundary of the diamond.  The link bit records which.
+bool build_tables(int d, const std::vector<std::array<Pt, 3>> &tris, ts_tri *t) {
+  std::vector<Pt> verts;
+  for (int y = -d; y <= d; ++y)
+    for (int x = -d; x <= d; ++x)
+      if (std::abs(x) + std::abs(y) <= d) verts.push_back({x, y});
+  std::sort(verts.begin(), verts.end());
+  const int V = (int)verts.size();
+  if (V > 255) return false;
+  std::map<Pt, int> pos;
+  for (int v = 0; v < V; ++v) pos[verts[v]] = v;
+
+  static const int qx[4] = {1, -1, -1, 1}, qy[4] = {1, 1, -1, -1};
+  std::set<std::array<int, 3>> dtris;
+  std::vector<std::set<int>> adj(V);
+  for (int q = 0; q < 4; ++q)
+    for (auto &tr : tris) {
+      std::array<int, 3> id;
+      for (int k = 0; k < 3; ++k) id[k] = pos.at({qx[q] * tr[k].x, qy[q] * tr[k].y});
+      for (int k = 0; k < 3; ++k) {
+        adj[id[k]].insert(id[(k + 1) % 3]);
+        adj[id[(k + 1) % 3]].insert(id[k]);
+      }
+      std::sort(id.begin(), id.end());
+      dtris.insert(id);
+    }
+  if ((int)dtris.size() != 4 * d * d) return false;
+
+  auto kc = [&](int v, int &k, int &c) {
+    int x = verts[v].x, y = verts[v].y, i = std::abs(x), j = std::abs(y);
+    k = lattice_index(d, i, j);
+    c = ((x < 0) ? (i & 1) : 0) ^ ((y < 0) ? (j & 1) : 0);  // Eq. 2
+  };
+  auto has_tri = [&](int a, int b, int c) {
+    std::array<int, 3> id{a, b, c};
+    std::sort(id.begin(), id.end());
+    return dtris.count(id) > 0;
+  };
+
+  std::vector<uint32_t> vdesc(V), fan;
+  for (int v = 0; v < V; ++v) {
+    std::vector<int> back;
+    for (int u : adj[v])
+      if (u < v) back.push_back(u);
+    // angular order from the left neighbour, counter-clockwise below v
+    std::sort(back.begin(), back.end(), [&](int a, int b) {
+      int ax = verts[a].x - verts[v].x, ay = verts[a].y - verts[v].y;
+      int bx = verts[b].x - verts[v].x, by = verts[b].y - verts[v].y;
+      return cross(ax, ay, bx, by) > 0;
+    });
+    int k, c;
+    kc(v, k, c);
+    if (back.size() > 63 || fan.size() > 65535) return false;
+    vdesc[v] = (uint32_t)k | ((uint32_t)c << 6) | ((uint32_t)back.size() << 7) |
+               ((uint32_t)fan.size() << 16);
+    for (size_t n = 0; n < back.size(); ++n) {
+      int u = back[n], ku, cu;
+      kc(u, ku, cu);
+      uint32_t link = (n > 0 && has_tri(v, back[n - 1], u)) ? 1u : 0u;
+      fan.push_back((uint32_t)u | ((uint32_t)ku << 8) | ((uint32_t)cu << 14) | (link << 15));
+    }
+  }
+  std::vector<uint32_t> anti, bedge;
+  for (int v = 0; v < V; ++v) {
+    const Pt p = verts[v];
+    if (std::abs(p.x) + std::abs(p.y) != d) continue;
+    int w = pos.at({-p.x, -p.y});
+    if (v < w) anti.push_back((uint32_t)v | ((uint32_t)w << 8));
+  }
+  std::set<std::pair<int, int>> seen;
+  for (int a = 0; a < V; ++a)
+    for (int b : adj[a]) {
+      if (b < a) continue;
+      const Pt pa = verts[a], pb = verts[b];
+      if (std::abs(pa.x) + std::abs(pa.y) != d || std::abs(pb.x) + std::abs(pb.y) != d) continue;
+      int a2 = pos.at({-pa.x, -pa.y}), b2 = pos.at({-pb.x, -pb.y});
+      auto key2 = std::make_pair(std::min(a2, b2), std::max(a2, b2));
+      if (seen.count(key2)) continue;
+      seen.insert({a, b});
+      int ka, ca, kb, cb;
+      kc(a, ka, ca);
+      kc(b, kb, cb);
+      bedge.push_back((uint32_t)a | ((uint32_t)b << 8) | ((uint32_t)ka << 16) | ((uint32_t)ca << 22) |
+                      ((uint32_t)kb << 23) | ((uint32_t)cb << 29));
+    }
+  if ((int)anti.size() != 2 * d || (int)bedge.size() != 2 * d) return false;
+
+  TableLayout L{};
+  L.V = V;
+  L.NF = (uint32_t)fan.size();
+  L.n_anti = (uint32_t)anti.size();
+  L.n_bedge = (uint32_t)bedge.size();
+  L.off_vdesc = 0;
+  L.off_fan = L.off_vdesc + V;
+  L.off_anti = L.off_fan + L.NF;
+  L.off_bedge = L.off_anti + L.n_anti;
+  L.words = (L.off_bedge + L.n_bedge + 3) & ~3u;
+  std::vector<uint32_t> buf(L.words, 0);
+  std::copy(vdesc.begin(), vdesc.end(), buf.begin() + L.off_vdesc);
+  std::copy(fan.begin(), fan.end(), buf.begin() + L.off_fan);
+  std::copy(anti.begin(), anti.end(), buf.begin() + L.off_anti);
+  std::copy(bedge.begin(), bedge.end(), buf.begin() + L.off_bedge);
+  t->lay = L;
+  t->host_tables = std::move(buf);
+  t->V = V;
+  return true;
+}
+
+ts_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return TS_OK;
+  if (e == cudaErrorMemoryAllocation) return TS_ENOMEM;
+  return TS_ECUDA;
+}
+
+ts_status err_word_status(uint32_t w) {
+  if (w & kErrTimeout) return TS_ETIMEOUT;
+  if (w & kErrOverflow) return TS_EOVERFLOW;
+  if (w & kErrInternal) return TS_EINTERNAL;
+  return TS_OK;
+}
+
+void put_scheme(std::string &out, const std::vector<std::vector<int>> &kids, int node) {
+  // children encodings are already in canonical (descending) order; group
+  // equal consecutive siblings as k or k<X>
+  std::vector<std::string> parts;
+  for (int c : kids[node]) {
+    std::string s;
+    put_scheme(s, kids, c);
+    parts.push_back(s);
+  }
+  std::string res;
+  for (size_t a = 0; a < parts.size();) {
+    size_t b = a;
+    while (b < parts.size() && parts[b] == parts[a]) ++b;
+    if (!res.empty()) res += " + ";
+    res += std::to_string(b - a);
+    if (!parts[a].empty()) res += "<" + parts[a] + ">";
+    a = b;
+  }
+  out += res;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ts_status_str(int s) {
+  switch (s) {
+    case TS_OK: return "TS_OK";
+    case TS_EINVAL: return "TS_EINVAL: invalid argument";
+    case TS_ENOTTRI: return "TS_ENOTTRI: not a unimodular triangulation of d*Delta_2";
+    case TS_ENOMEM: return "TS_ENOMEM: out of memory";
+    case TS_ECUDA: return "TS_ECUDA: CUDA error or no usable device";
+    case TS_EOVERFLOW: return "TS_EOVERFLOW: capacity exceeded";
+    case TS_ETIMEOUT: return "TS_ETIMEOUT: bounded device wait gave up";
+    case TS_EINTERNAL: return "TS_EINTERNAL: invariant violated on some instance";
+    case TS_EUNSUPPORTED: return "TS_EUNSUPPORTED: degree not supported by this build";
+    default: return "unknown ts_status";
+  }
+}
+
+int ts_max_degree(void) { return kMaxDegree; }
+
+ts_status ts_load_triangulation(int d, const int32_t *edges_ij, int n_edges, ts_tri **out) {
+  if (!out || (!edges_ij && n_edges > 0) || n_edges < 0) return TS_EINVAL;
+  *out = nullptr;
+  if (d < 1) return TS_EINVAL;
+  if (d > kMaxDegree) return TS_EUNSUPPORTED;
+  std::vector<std::array<Pt, 3>> tris;
+  if (!triangles_of(d, edges_ij, n_edges, tris)) return TS_ENOTTRI;
+  ts_tri *t = new (std::nothrow) ts_tri();
+  if (!t) return TS_ENOMEM;
+  t->d = d;
+  t->np = (d + 1) * (d + 2) / 2;
+  t->sw = (t->np + 63) / 64;
+  t->nmax = (d % 2 == 0) ? harnack(d) : harnack(d) - 1;
+  t->cw = (2 * t->nmax + 1 + 63) / 64;
+  if (!build_tables(d, tris, t)) {
+    delete t;
+    return TS_ENOTTRI;
+  }
+  cudaError_t e = cudaGetDevice(&t->device);
+  if (e == cudaSuccess) e = cudaMalloc(&t->d_tables, t->lay.words * sizeof(uint32_t));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(t->d_tables, t->host_tables.data(), t->lay.words * sizeof(uint32_t),
+                   cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&t->d_err, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemset(t->d_err, 0, sizeof(uint32_t));
+  if (e != cudaSuccess) {
+    ts_status s = cuda_status(e);
+    ts_free_triangulation(t);
+    return s;
+  }
+  *out = t;
+  return TS_OK;
+}
+
+void ts_free_triangulation(ts_tri *t) {
+  if (!t) return;
+  if (t->d_tables) cudaFree(t->d_tables);
+  if (t->d_err) cudaFree(t->d_err);
+  delete t;
+}
+
+int ts_degree(const ts_tri *t) { return t ? t->d : 0; }
+int ts_num_points(const ts_tri *t) { return t ? t->np : 0; }
+int ts_sign_words(const ts_tri *t) { return t ? t->sw : 0; }
+int ts_code_words(const ts_tri *t) { return t ? t->cw : 0; }
+
+ts_status ts_real_schemes(const ts_tri *t, const uint64_t *signs, uint64_t n, uint64_t *codes,
+                          void *stream) {
+  if (!t || (n && (!signs || !codes))) return TS_EINVAL;
+  if (n == 0) return TS_OK;
+  return cuda_status(launch_real_schemes(t, signs, n, codes, (cudaStream_t)stream));
+}
+
+ts_status ts_sync(const ts_tri *t, void *stream) {
+  if (!t) return TS_EINVAL;
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  uint32_t w = 0;
+  e = cudaMemcpy(&w, t->d_err, sizeof(w), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && w) e = cudaMemset(t->d_err, 0, sizeof(uint32_t));
+  if (e != cudaSuccess) return cuda_status(e);
+  return err_word_status(w);
+}
+
+ts_status ts_real_schemes_host(const ts_tri *t, const uint64_t *signs_host, uint64_t n,
+                               uint64_t *codes_host) {
+  if (!t || (n && (!signs_host || !codes_host))) return TS_EINVAL;
+  if (n == 0) return TS_OK;
+  uint64_t *ds = nullptr, *dc = nullptr;
+  size_t bs = n * t->sw * sizeof(uint64_t), bc = n * t->cw * sizeof(uint64_t);
+  cudaError_t e = cudaMalloc(&ds, bs);
+  if (e == cudaSuccess) e = cudaMalloc(&dc, bc);
+  if (e == cudaSuccess) e = cudaMemcpy(ds, signs_host, bs, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = launch_real_schemes(t, ds, n, dc, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(codes_host, dc, bc, cudaMemcpyDeviceToHost);
+  if (ds) cudaFree(ds);
+  if (dc) cudaFree(dc);
+  if (e != cudaSuccess) return cuda_status(e);
+  return ts_sync(t, 0);
+}
+
+ts_status ts_hist_create(uint64_t capacity, int code_words, ts_hist **out) {
+  if (!out || code_words < 1 || code_words > 4 || capacity == 0 || capacity > (1ull << 30))
+    return TS_EINVAL;
+  *out = nullptr;
+  ts_hist *h = new (std::nothrow) ts_hist();
+  if (!h) return TS_ENOMEM;
+  h->cw = code_words;
+  uint64_t s = 16;
+  while (s < 2 * capacity) s <<= 1;
+  h->slots = s;
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_keys, s * code_words * sizeof(uint64_t));
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_counts, s * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_err, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_failed, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_work, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = launch_hist_clear(h, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    ts_status st = cuda_status(e);
+    ts_hist_free(h);
+    return st;
+  }
+  *out = h;
+  return TS_OK;
+}
+
+void ts_hist_free(ts_hist *h) {
+  if (!h) return;
+  if (h->d_keys) cudaFree(h->d_keys);
+  if (h->d_counts) cudaFree(h->d_counts);
+  if (h->d_err) cudaFree(h->d_err);
+  if (h->d_failed) cudaFree(h->d_failed);
+  if (h->d_work) cudaFree(h->d_work);
+  delete h;
+}
+
+ts_status ts_hist_clear(ts_hist *h, void *stream) {
+  if (!h) return TS_EINVAL;
+  return cuda_status(launch_hist_clear(h, (cudaStream_t)stream));
+}
+
+ts_status ts_enumerate(const ts_tri *t, uint64_t lo, uint64_t hi, uint32_t flags, ts_hist *h,
+                       void *stream) {
+  if (!t || !h || hi < lo || (flags & ~(TS_ENUM_FLIP | TS_ENUM_REDUCED)) ||
+      flags == (TS_ENUM_FLIP | TS_ENUM_REDUCED))
+    return TS_EINVAL;
+  if (h->cw != t->cw) return TS_EINVAL;
+  if (t->np > 64) return TS_EUNSUPPORTED;
+  int free_bits = t->np - ((flags & TS_ENUM_FLIP) ? 1 : 0) - ((flags & TS_ENUM_REDUCED) ? 3 : 0);
+  if (free_bits < 64 && hi > (1ull << free_bits)) return TS_EINVAL;
+  if (lo == hi) return TS_OK;
+  return cuda_status(launch_enumerate(t, lo, hi, flags, h, (cudaStream_t)stream));
+}
+
+ts_status ts_hist_read(ts_hist *h, uint64_t *codes, uint64_t *counts, uint64_t cap,
+                       uint64_t *n_out, uint64_t *n_failed, void *stream) {
+  if (!h || !n_out || (cap && (!codes || !counts))) return TS_EINVAL;
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  std::vector<uint64_t> keys(h->slots * h->cw);
+  std::vector<unsigned long long> cnt(h->slots);
+  uint32_t err = 0;
+  unsigned long long failed = 0;
+  if (e == cudaSuccess)
+    e = cudaMemcpy(keys.data(), h->d_keys, keys.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(cnt.data(), h->d_counts, cnt.size() * sizeof(unsigned long long),
+                   cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&err, h->d_err, sizeof(err), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(&failed, h->d_failed, sizeof(failed), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_status(e);
+  const int cw = h->cw;
+  std::vector<uint64_t> idx;
+  for (uint64_t s = 0; s < h->slots; ++s) {
+    bool nz = false;
+    for (int w = 0; w < cw; ++w) nz |= keys[s * cw + w] != 0;
+    if (nz) idx.push_back(s);
+  }
+  std::sort(idx.begin(), idx.end(), [&](uint64_t a, uint64_t b) {
+    for (int w = cw - 1; w >= 0; --w)
+      if (keys[a * cw + w] != keys[b * cw + w]) return keys[a * cw + w] < keys[b * cw + w];
+    return false;
+  });
+  *n_out = idx.size();
+  if (n_failed) *n_failed = failed;
+  for (uint64_t r = 0; r < idx.size() && r < cap; ++r) {
+    for (int w = 0; w < cw; ++w) codes[r * cw + w] = keys[idx[r] * cw + w];
+    counts[r] = cnt[idx[r]];
+  }
+  if (idx.size() > cap) return TS_EOVERFLOW;
+  return err_word_status(err);
+}
+
+ts_status ts_scheme_string(int d, const uint64_t *code, int code_words, char *buf, size_t len) {
+  if (!code || !buf || len == 0 || code_words < 1 || d < 1) return TS_EINVAL;
+  int top = -1;
+  for (int b = 64 * code_words - 1; b >= 0; --b)
+    if ((code[b >> 6] >> (b & 63)) & 1) { top = b; break; }
+  if (top < 0 || (top & 1)) return TS_EINVAL;  // code 0, or odd bit count
+  // parse the Dyck word below the sentinel into a tree (node 0 = root)
+  std::vector<std::vector<int>> kids(1);
+  std::vector<int> stack{0};
+  for (int b = top - 1; b >= 0; --b) {
+    int bit = (int)((code[b >> 6] >> (b & 63)) & 1);
+    if (bit) {
+      int n = (int)kids.size();
+      kids.push_back({});
+      kids[stack.back()].push_back(n);
+      stack.push_back(n);
+    } else {
+      if (stack.size() < 2) return TS_EINVAL;
+      stack.pop_back();
+    }
+  }
+  if (stack.size() != 1) return TS_EINVAL;
+  std::string body;
+  put_scheme(body, kids, 0);
+  std::string s = "<";
+  if (d % 2) s += body.empty() ? "J" : "J + " + body;
+  else s += body.empty() ? "0" : body;
+  s += ">";
+  if (s.size() + 1 > len) return TS_EOVERFLOW;
+  std::memcpy(buf, s.c_str(), s.size() + 1);
+  return TS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,85 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads and
+exports every entry point declared in include/tcurve.h, input validation
+rejects malformed triangulations, and the Rohlin-Viro printer agrees with an
+independent printer on the codes the oracle produces."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import tcurve_inputs as ti
+from schemes import rohlin_viro
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def eng():
+    from paper_2604_09221_gb300 import build
+    build.build()
+    import paper_2604_09221_gb300 as e
+    e.library()
+    return e
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "tcurve.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ts_\w+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(eng):
+    names = declared_functions()
+    assert len(names) >= 15
+    lib = eng.library()
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert missing == []
+
+
+def load_status(eng, d, edges):
+    e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 4))
+    h = ctypes.c_void_p()
+    rc = eng.library().ts_load_triangulation(d, e.ctypes.data, len(e), ctypes.byref(h))
+    if rc == 0:
+        eng.library().ts_free_triangulation(h)
+    return rc
+
+
+def test_validation_rejects_bad_triangulations(eng):
+    good = ti.standard_triangulation(5)
+    assert load_status(eng, 5, good[:-1]) == 2                    # an edge missing
+    assert load_status(eng, 5, np.vstack([good, good[:1]])) == 2  # repeated edge
+    bad = good.copy()
+    bad[0] = [0, 0, 5, 0]                                         # not primitive
+    assert load_status(eng, 5, bad) == 2
+    out = good.copy()
+    out[3, 2] = 9                                                 # point outside A
+    assert load_status(eng, 5, out) == 2
+    assert load_status(eng, 4, good) == 2                         # wrong degree
+    assert load_status(eng, 0, good) == 1
+    assert load_status(eng, 10, ti.standard_triangulation(10)) == 8
+
+
+def test_valid_triangulation_needs_a_device(eng):
+    import torch
+    rc = load_status(eng, 6, ti.regular_triangulation(6, seed=6))
+    assert rc == (0 if torch.cuda.is_available() else 4)
+
+
+def test_status_strings(eng):
+    lib = eng.library()
+    for s in range(9):
+        assert lib.ts_status_str(s).decode().startswith("TS_")
+
+
+@pytest.mark.parametrize("d", [4, 5, 6, 7, 8])
+def test_scheme_string_matches_independent_printer(eng, orc, d):
+    tri = orc.triangles(d, ti.standard_triangulation(d))
+    codes = orc.real_schemes(d, tri, ti.random_masks(2000, d, 17))
+    for c in sorted(set(orc.code_to_int(r) for r in codes)):
+        assert eng.scheme_string(d, c).replace("+", "+") == rohlin_viro(d, c)
+    assert eng.scheme_string(6, 458) == "<1<1> + 2>"
+    assert eng.scheme_string(7, 1) == "<J>"
+    assert eng.scheme_string(6, 1) == "<0>"

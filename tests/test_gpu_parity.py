@@ -1,0 +1,189 @@
+"""GPU parity: codes from the CUDA path (through the C ABI) must equal the CPU
+oracle's bit for bit on the same seeded inputs.
+
+Covers every supported degree, seeded regular triangulations, the paper's
+three degree-8 triangulations (Fig. 2), exhaustive small degrees, ragged
+batch sizes, stray high bits, the host-buffer entry point, and the
+enumeration kernel (all three mask maps) against oracle histograms,
+including a full-size degree-7 sweep checked on a sampled sub-range and by
+properties that hold at any size.
+"""
+import collections
+import os
+
+import numpy as np
+import pytest
+
+import tcurve_inputs as ti
+from schemes import check_classical
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def eng():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_09221_gb300 import build
+    build.build()
+    import paper_2604_09221_gb300 as e
+    e.library()
+    return e
+
+
+def gpu_codes(eng, tri, masks):
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(masks).view(np.int64)).cuda()
+    return tri.real_schemes(t).cpu().numpy().view(np.uint64)
+
+
+def triangulations(d, k=2, seed=0):
+    out = [("standard", ti.standard_triangulation(d))]
+    if d >= 3:
+        out += [(f"regular{n}", e) for n, e in enumerate(ti.regular_triangulations(d, k, seed=1000 + d + seed))]
+    return out
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4])
+def test_exhaustive_small_degrees(eng, orc, d):
+    masks = np.arange(1 << ti.num_points(d), dtype=np.uint64).reshape(-1, 1)
+    for name, e in triangulations(d, 3):
+        tri = eng.Triangulation(d, e)
+        got = gpu_codes(eng, tri, masks)
+        want = orc.real_schemes(d, orc.triangles(d, e), masks)
+        assert (got == want).all(), (d, name)
+
+
+@pytest.mark.parametrize("d", [5, 6, 7, 8, 9])
+def test_random_sign_vectors(eng, orc, d):
+    n = 20011  # several blocks and a ragged tail
+    for idx, (name, e) in enumerate(triangulations(d, 3)):
+        masks = ti.random_masks(n, d, 31 + d, stream=idx)
+        tri = eng.Triangulation(d, e)
+        got = gpu_codes(eng, tri, masks)
+        want = orc.real_schemes(d, orc.triangles(d, e), masks)
+        bad = np.nonzero((got != want).any(axis=1))[0]
+        assert bad.size == 0, (d, name, bad[:5], masks[bad[:5]])
+
+
+@pytest.mark.parametrize("name", ["bow_tie", "rank016", "rank015"])
+def test_fig2_triangulations(eng, orc, name):
+    e = np.loadtxt(os.path.join(GOLDEN, f"fig2_{name}.edges"), dtype=np.int32, comments="#")
+    masks = ti.random_masks(30000, 8, 99, stream=len(name))
+    tri = eng.Triangulation(8, e)
+    got = gpu_codes(eng, tri, masks)
+    want = orc.real_schemes(8, orc.triangles(8, e), masks)
+    assert (got == want).all()
+
+
+def test_special_sign_vectors(eng, orc):
+    for d in range(1, 10):
+        npts = ti.num_points(d)
+        full = (1 << npts) - 1
+        pts = [(i, j) for j in range(d + 1) for i in range(d + 1 - j)]
+        harnack = sum(1 << n for n, (i, j) in enumerate(pts) if i % 2 == 0 and j % 2 == 0)
+        alt = sum(1 << n for n, (i, j) in enumerate(pts) if (i + j) % 2)
+        masks = np.array([[0], [full], [harnack], [alt], [full ^ alt], [1], [full >> 1]], dtype=np.uint64)
+        for name, e in triangulations(d, 1):
+            tri = eng.Triangulation(d, e)
+            assert (gpu_codes(eng, tri, masks) == orc.real_schemes(d, orc.triangles(d, e), masks)).all()
+
+
+def test_stray_high_bits_are_ignored(eng):
+    d = 6
+    e = ti.regular_triangulation(d, seed=5)
+    tri = eng.Triangulation(d, e)
+    masks = ti.random_masks(4096, d, 1)
+    dirty = masks | (np.uint64(0xABCDEF) << np.uint64(ti.num_points(d)))
+    assert (gpu_codes(eng, tri, masks) == gpu_codes(eng, tri, dirty)).all()
+
+
+@pytest.mark.parametrize("n", [0, 1, 31, 127, 128, 129, 4097])
+def test_batch_sizes(eng, orc, n):
+    import torch
+    d = 7
+    e = ti.regular_triangulation(d, seed=77)
+    tri = eng.Triangulation(d, e)
+    masks = ti.random_masks(max(n, 1), d, 3)[:n]
+    got = tri.real_schemes(torch.from_numpy(masks.view(np.int64)).cuda().reshape(-1, 1))
+    assert got.shape == (n, 1)
+    if n:
+        want = orc.real_schemes(d, orc.triangles(d, e), masks)
+        assert (got.cpu().numpy().view(np.uint64) == want).all()
+
+
+def test_host_buffer_entry_point(eng, orc):
+    d = 6
+    e = ti.regular_triangulation(d, seed=8)
+    tri = eng.Triangulation(d, e)
+    masks = ti.random_masks(5000, d, 8)
+    assert (tri.real_schemes_host(masks) == orc.real_schemes(d, orc.triangles(d, e), masks)).all()
+
+
+def oracle_hist(orc, d, e, masks):
+    codes = orc.real_schemes(d, orc.triangles(d, e), masks)
+    return collections.Counter(codes[:, 0].tolist())
+
+
+def gpu_hist(eng, tri, lo, hi, flags=0):
+    h = eng.Histogram(4096, tri.code_words)
+    eng.enumerate_schemes(tri, lo, hi, h, flags)
+    codes, counts, failed = h.read()
+    assert failed == 0
+    return collections.Counter(dict(zip(codes[:, 0].tolist(), counts.tolist())))
+
+
+def reduced_masks(d, ks):
+    ks = np.asarray(ks, dtype=np.uint64)
+    low = ks & np.uint64((1 << (d - 1)) - 1)
+    return ((low << np.uint64(2)) | ((ks >> np.uint64(d - 1)) << np.uint64(d + 2))).reshape(-1, 1)
+
+
+@pytest.mark.parametrize("d", [4, 5])
+def test_enumerate_full_range(eng, orc, d):
+    e = ti.regular_triangulation(d, seed=50 + d)
+    tri = eng.Triangulation(d, e)
+    n = 1 << ti.num_points(d)
+    assert gpu_hist(eng, tri, 0, n) == oracle_hist(orc, d, e, np.arange(n, dtype=np.uint64).reshape(-1, 1))
+
+
+@pytest.mark.parametrize("d", [6, 7, 8, 9])
+def test_enumerate_ragged_ranges_and_flags(eng, orc, d):
+    e = ti.regular_triangulation(d, seed=60 + d)
+    tri = eng.Triangulation(d, e)
+    lo, hi = 123457, 123457 + 50001
+    ks = np.arange(lo, hi, dtype=np.uint64)
+    assert gpu_hist(eng, tri, lo, hi) == oracle_hist(orc, d, e, ks.reshape(-1, 1))
+    assert gpu_hist(eng, tri, lo, hi, eng.TS_ENUM_FLIP) == oracle_hist(orc, d, e, (ks << np.uint64(1)).reshape(-1, 1))
+    assert gpu_hist(eng, tri, lo, hi, eng.TS_ENUM_REDUCED) == oracle_hist(orc, d, e, reduced_masks(d, ks))
+
+
+def test_enumerate_reduced_equals_full_over_8(eng):
+    # (Z/2)^3 acts freely and preserves schemes (Sec. 3): the full histogram is
+    # 8 times the histogram over the representatives.
+    d = 5
+    e = ti.regular_triangulation(d, seed=3)
+    tri = eng.Triangulation(d, e)
+    full = gpu_hist(eng, tri, 0, 1 << ti.num_points(d))
+    red = gpu_hist(eng, tri, 0, 1 << (ti.num_points(d) - 3), eng.TS_ENUM_REDUCED)
+    assert full == collections.Counter({k: 8 * v for k, v in red.items()})
+
+
+def test_enumerate_d7_full_size_slice(eng, orc):
+    """The benchmark workload (degree 7, masks [0, 2^32)) in the launch
+    configuration the bench uses: every count accounted for, every scheme a
+    valid septic scheme, no more than the 121 that exist, and the sub-range
+    [2^31, 2^31 + 2^16) equal to the oracle's histogram."""
+    d = 7
+    e = ti.regular_triangulation(d, seed=7)
+    tri = eng.Triangulation(d, e)
+    full = gpu_hist(eng, tri, 0, 1 << 32)
+    assert sum(full.values()) == 1 << 32
+    assert len(full) <= 121
+    for c in full:
+        assert check_classical(d, c) == []
+    lo = 1 << 31
+    ks = np.arange(lo, lo + (1 << 16), dtype=np.uint64).reshape(-1, 1)
+    assert gpu_hist(eng, tri, lo, lo + (1 << 16)) == oracle_hist(orc, d, e, ks)
