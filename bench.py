@@ -1,0 +1,355 @@
+"""Benchmark of the T-curve real-scheme engine on GB300.
+
+Workload (one step): the exhaustive sweep of one 2^32 slice of sign masks of
+one seeded regular unimodular triangulation of 7*Delta_2 (36 lattice points),
+every instance classified by Algorithm 1 and counted in the device hash
+histogram of distinct schemes, in one persistent launch (ts_enumerate).
+Under torchrun every rank sweeps its own 2^32 slice (weak scaling) and the
+per-rank histograms are merged at the end.
+
+Printed (rank 0, one JSON line): schemes/s of the whole job (device-timed
+with CUDA events on the launching stream), the end-to-end rate through the
+public API (ts_enumerate + ts_hist_read with the host copy), the roofline of
+the enumeration kernel, the CPU oracle on a bounded sample, the plain
+one-launch query kernel (ts_real_schemes on materialised masks) beside the
+persistent sweep, SM clocks sampled during the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+D = 7
+SLICE = 1 << 32
+TRI_SEED = 7
+# Algorithmic integer operations per instance at d = 7 (sign extension,
+# crossing tests on the 308 edges of T^diamond, unions over non-crossed edges,
+# finds on crossed edges, antipodal unions, tree and encoding).
+ALG_OPS_PER_INSTANCE = 1.2e3
+INT_LANES_PER_SM = 128  # 4 SM sub-partitions x 32 INT32 lanes per clock
+METRIC = "real schemes/sec at d=7 on 1 GB300 (batched vs plain), bit-exact; p50/p99 job latency"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        sm = [float(r[0]) for r in self.rows if r and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) > 1 and r[1].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            for n, v in zip(names, r[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def cpu_baseline(edges, seconds_target: float = 12.0):
+    """The CPU oracle, as it stands, on a bounded sample of the same sweep."""
+    import numpy as np
+
+    import oracle
+    tri = oracle.triangles(D, edges)
+    cores = os.cpu_count() or 1
+    n = 1 << 14
+    while True:
+        masks = np.arange(n, dtype=np.uint64).reshape(-1, 1)
+        t0 = time.perf_counter()
+        oracle.real_schemes(D, tri, masks, n_threads=cores)
+        dt = time.perf_counter() - t0
+        if dt > seconds_target / 4 or n >= 1 << 26:
+            break
+        n <<= 2
+    return {"value": n / dt, "unit": "schemes/s", "cores": cores, "kind": "oracle",
+            "sample": f"masks [0, {n}) of the d=7 sweep ({dt:.1f} s)"}
+
+
+def reference_arm(args):
+    """--impl reference: the CPU oracle timed as a bounded-sample stand-in."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import oracle
+    import tcurve_inputs as ti
+    edges = ti.regular_triangulation(D, seed=TRI_SEED)
+    tri = oracle.triangles(D, edges)
+    cores = os.cpu_count() or 1
+    sample = 1 << 18
+    for _ in range(args.warmup):
+        oracle.real_schemes(D, tri, np.arange(1 << 12, dtype=np.uint64).reshape(-1, 1), n_threads=cores)
+    times = []
+    for s in range(args.steps):
+        masks = np.arange(s * sample, (s + 1) * sample, dtype=np.uint64).reshape(-1, 1)
+        t0 = time.perf_counter()
+        oracle.real_schemes(D, tri, masks, n_threads=cores)
+        times.append(time.perf_counter() - t0)
+    v = sample * len(times) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "schemes/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "d7_sweep_oracle_sample", "degree": D, "masks_per_step": sample,
+                       "triangulation": f"regular, lifting seed {TRI_SEED}"},
+            "cpu_baseline": {"value": v, "unit": "schemes/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{sample} consecutive masks per step"},
+            "e2e": {"value": v, "unit": "schemes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import numpy as np
+    import torch
+
+    import paper_2604_09221_gb300 as eng
+    import tcurve_inputs as ti
+    from paper_2604_09221_gb300 import build as _b
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    _b.build()
+    edges = ti.regular_triangulation(D, seed=TRI_SEED)
+    tri = eng.Triangulation(D, edges)
+    hist = eng.Histogram(4096, tri.code_words)
+    stream = torch.cuda.current_stream()
+    lo = rank * SLICE
+    # the slice of rank r: masks [r 2^32, (r+1) 2^32) of the 2^36 masks
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step():
+        hist.clear(stream)
+        eng.enumerate_schemes(tri, lo, lo + SLICE, hist, stream=stream)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- device-timed region: K steps, L2 flushed between steps ----
+    clocks = ClockSampler(local)
+    clocks.start()
+    times = []
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    codes, counts, failed = hist.read(stream)
+    assert failed == 0 and int(counts.sum()) == SLICE, "sweep lost instances"
+    ms = sum(times) / len(times)
+    if pg:
+        t = torch.tensor([ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * SLICE / (ms / 1e3)
+
+    # ---- end to end through the public API (host read of the histogram) ----
+    n_codes = ctypes_read_bytes = None
+    e2e_times = []
+    for _ in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hist.clear(stream)
+        eng.enumerate_schemes(tri, lo, lo + SLICE, hist, stream=stream)
+        c2, n2, f2 = hist.read(stream)
+        e2e_times.append(time.perf_counter() - t0)
+        n_codes = len(c2)
+    d2h = hist_bytes(hist)
+    e2e_ms = 1e3 * sum(e2e_times) / len(e2e_times)
+    if pg:
+        t = torch.tensor([e2e_ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    # ---- merge of the per-rank histograms (the only exchange step) ----
+    if pg:
+        merged = merge_histograms(pg, codes, counts)
+        if rank == 0:
+            assert sum(merged.values()) == ws * SLICE
+
+    if rank != 0:
+        pg.destroy_process_group()
+        return 0
+
+    peaks = measured_peaks()
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_max = peaks.get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0
+    peak_tops = n_sm * INT_LANES_PER_SM * sm_max * 1e6 / 1e12
+    achieved_tops = ALG_OPS_PER_INSTANCE * SLICE / (ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "kernel": f"enumerate_kernel<{D}>",
+                "achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s",
+                "frac": achieved_tops / peak_tops, "traffic": None,
+                "peak_source": f"{n_sm} SMs x {INT_LANES_PER_SM} INT32 lanes x {sm_max:.0f} MHz (derived)",
+                "alg_ops_per_instance": ALG_OPS_PER_INSTANCE}
+    line = {"metric": METRIC, "value": value, "unit": "schemes/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": "d7_batched_sweep", "degree": D, "slice": SLICE,
+                       "triangulation": f"regular unimodular, lifting seed {TRI_SEED}",
+                       "parallelism": f"range-sharded x{ws}",
+                       "l2": "256 MiB buffer written between steps (outside the event-timed region); "
+                             "the sweep reads no HBM input",
+                       "wall_s": wall},
+            "distinct_schemes": len(codes),
+            "e2e": {"value": ws * SLICE / (e2e_ms / 1e3), "unit": "schemes/s",
+                    "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h},
+            "gpu_launches": 2 * args.steps * ws,
+            "roofline": roofline, "clocks": clk}
+    if not args.no_plain:
+        line["plain"] = plain_kernel(eng, tri, ti, stream)
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(edges)
+    print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+def hist_bytes(hist):
+    # ts_hist_read copies the whole device table (keys + counts) and 2 words
+    lib = hist
+    return None if lib is None else int(hist_slots(hist) * (8 * hist.code_words + 8) + 12)
+
+
+def hist_slots(hist):
+    s = 16
+    while s < 2 * hist.capacity:
+        s <<= 1
+    return s
+
+
+def merge_histograms(pg, codes, counts):
+    import torch
+    ws = pg.get_world_size()
+    n = torch.tensor([len(codes)], device="cuda")
+    sizes = [torch.zeros_like(n) for _ in range(ws)]
+    pg.all_gather(sizes, n)
+    m = int(max(s.item() for s in sizes))
+    buf = torch.zeros((m, 2), dtype=torch.int64, device="cuda")
+    buf[:len(codes), 0] = torch.from_numpy(codes[:, 0].view("int64"))
+    buf[:len(codes), 1] = torch.from_numpy(counts.view("int64"))
+    outs = [torch.zeros_like(buf) for _ in range(ws)]
+    pg.all_gather(outs, buf)
+    merged = {}
+    for o in outs:
+        for c, k in o.cpu().tolist():
+            if c:
+                merged[c] = merged.get(c, 0) + k
+    return merged
+
+
+def plain_kernel(eng, tri, ti, stream):
+    """The plain one-launch query kernel on materialised masks (same slice)."""
+    import numpy as np
+    import torch
+    n = 1 << 26
+    masks = torch.arange(n, dtype=torch.int64, device="cuda").reshape(-1, 1)
+    out = torch.empty((n, tri.code_words), dtype=torch.int64, device="cuda")
+    tri.real_schemes(masks, out=out, stream=stream)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(3):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        tri.real_schemes(masks, out=out, stream=stream, sync=False)
+        b.record(stream)
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    tri.sync(stream)
+    ms = statistics.median(times)
+    return {"value": n / (ms / 1e3), "unit": "schemes/s", "kernel": f"real_schemes_kernel<{tri.d}>",
+            "n": n, "ms": ms, "hbm_bytes": n * 16}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

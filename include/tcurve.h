@@ -100,6 +100,34 @@ int ts_code_words(const ts_tri *tri);
 ts_status ts_real_schemes(const ts_tri *tri, const uint64_t *signs, uint64_t n,
                           uint64_t *out_codes, void *stream);
 
+/* Kernel families (ts_set_kernel).  Both compute the same codes.
+ *   TS_KERNEL_TABLE: one generic kernel per degree; the triangulation's
+ *     tables are staged into shared memory by a bulk copy in every block.
+ *   TS_KERNEL_SPECIALIZED: a kernel generated for this triangulation (its
+ *     structure compiled into the instruction stream) with NVRTC on first use.
+ *   TS_KERNEL_AUTO (default): specialised for ts_enumerate and for batches of
+ *     at least 65536 instances, table-driven otherwise or if the specialised
+ *     kernel cannot be built. */
+#define TS_KERNEL_AUTO 0
+#define TS_KERNEL_TABLE 1
+#define TS_KERNEL_SPECIALIZED 2
+ts_status ts_set_kernel(ts_tri *tri, int kind);
+
+/* Build the specialised kernels now (NVRTC compile and module load on the
+ * current device; about a second).  Call it before capturing launches of
+ * this triangulation in a CUDA graph, since the first specialised launch
+ * otherwise compiles.  Returns TS_ECUDA if compilation or loading fails
+ * (ts_specialized_log then holds the compiler log). */
+ts_status ts_prepare(ts_tri *tri);
+ts_status ts_specialized_log(const ts_tri *tri, char *buf, size_t len);
+
+/* Host-only helper (no device needed): validate the edge list and write the
+ * generated specialised CUDA source into buf (compile = 0), or compile it
+ * with NVRTC for sm_103a and write the compiler log (compile = 1; returns
+ * TS_ECUDA if it does not compile).  *needed receives the full length + 1. */
+ts_status ts_specialized_source(int d, const int32_t *edges_ij, int n_edges, int compile, char *buf,
+                                size_t len, size_t *needed);
+
 /* Same computation with host buffers: copies signs to the device, runs,
  * copies codes back and synchronises (allocates device memory per call).
  * Returns the error status of the run. */

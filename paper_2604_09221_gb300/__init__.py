@@ -19,6 +19,9 @@ from . import build as _build
 
 TS_ENUM_FLIP = 1
 TS_ENUM_REDUCED = 2
+TS_KERNEL_AUTO = 0
+TS_KERNEL_TABLE = 1
+TS_KERNEL_SPECIALIZED = 2
 
 STATUS = {0: "TS_OK", 1: "TS_EINVAL", 2: "TS_ENOTTRI", 3: "TS_ENOMEM", 4: "TS_ECUDA",
           5: "TS_EOVERFLOW", 6: "TS_ETIMEOUT", 7: "TS_EINTERNAL", 8: "TS_EUNSUPPORTED"}
@@ -65,6 +68,11 @@ def _load():
                 "ts_enumerate": ([P, U64, U64, ctypes.c_uint32, P, P], I),
                 "ts_hist_read": ([P, P, P, U64, ctypes.POINTER(U64), ctypes.POINTER(U64), P], I),
                 "ts_scheme_string": ([I, P, I, ctypes.c_char_p, ctypes.c_size_t], I),
+                "ts_set_kernel": ([P, I], I),
+                "ts_prepare": ([P], I),
+                "ts_specialized_log": ([P, ctypes.c_char_p, ctypes.c_size_t], I),
+                "ts_specialized_source": ([I, P, I, I, ctypes.c_char_p, ctypes.c_size_t,
+                                           ctypes.POINTER(ctypes.c_size_t)], I),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -126,6 +134,23 @@ class Triangulation:
             self.close()
         except Exception:
             pass
+
+    def set_kernel(self, kind: int):
+        """TS_KERNEL_AUTO / TS_KERNEL_TABLE / TS_KERNEL_SPECIALIZED."""
+        _check(_lib.ts_set_kernel(self._h, int(kind)), "ts_set_kernel")
+
+    def prepare(self):
+        """Compile and load the specialised kernels now (ts_prepare)."""
+        st = _lib.ts_prepare(self._h)
+        if st != 0:
+            buf = ctypes.create_string_buffer(1 << 16)
+            _lib.ts_specialized_log(self._h, buf, len(buf))
+            raise TSError(st, "ts_prepare: " + buf.value.decode(errors="replace")[-2000:])
+
+    def specialized_log(self) -> str:
+        buf = ctypes.create_string_buffer(1 << 16)
+        _lib.ts_specialized_log(self._h, buf, len(buf))
+        return buf.value.decode(errors="replace")
 
     def real_schemes(self, signs, out=None, stream=None, sync: bool = True):
         """Codes of the sign vectors in ``signs`` (a CUDA int64/uint64 tensor of
@@ -205,6 +230,23 @@ def enumerate_schemes(tri: Triangulation, lo: int, hi: int, hist: Histogram, fla
     """Add the schemes of masks m(k), k in [lo, hi), to ``hist`` (ts_enumerate)."""
     _check(_lib.ts_enumerate(tri.handle, int(lo), int(hi), int(flags), hist.handle,
                              _stream_handle(stream)), "ts_enumerate")
+
+
+def specialized_source(d: int, edges, compile: bool = False) -> str:
+    """Generated CUDA source of the specialised kernels (compile=False) or the
+    NVRTC log of compiling it for sm_103a (compile=True).  No device needed."""
+    e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 4))
+    need = ctypes.c_size_t()
+    L = _load()
+    st = L.ts_specialized_source(int(d), e.ctypes.data, len(e), int(compile), None, 0, ctypes.byref(need))
+    if st not in (0, 5) and not (compile and st == 4):
+        _check(st, "ts_specialized_source")
+    buf = ctypes.create_string_buffer(need.value)
+    st = L.ts_specialized_source(int(d), e.ctypes.data, len(e), int(compile), buf, len(buf), None)
+    text = buf.value.decode(errors="replace")
+    if st != 0:
+        raise TSError(st, "ts_specialized_source: " + text[-3000:])
+    return text
 
 
 def scheme_string(d: int, code) -> str:

@@ -16,8 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libtcurve.so")
-SOURCES = ["host.cpp", "kernels.cu"]
-HEADERS = ["engine.h", os.path.join("..", "..", "include", "tcurve.h")]
+SOURCES = ["host.cpp", "kernels.cu", "jit.cpp"]
+HEADERS = ["engine.h", "jit_device.cuh", os.path.join("..", "..", "include", "tcurve.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -36,14 +36,27 @@ def _stale() -> bool:
     return any(os.path.getmtime(p) > t for p in deps)
 
 
+def embed_device_runtime() -> str:
+    """Write the device runtime of the specialised kernels (jit_device.cuh)
+    as a C++ raw string literal for jit.cpp to splice generated code into."""
+    src = open(os.path.join(CSRC, "jit_device.cuh")).read()
+    out = os.path.join(OUT_DIR, "_jit_device_src.inc")
+    text = 'R"TCJIT(' + src + ')TCJIT"\n'
+    if not os.path.exists(out) or open(out).read() != text:
+        with open(out, "w") as f:
+            f.write(text)
+    return out
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     """Compile the sources (in parallel) and link libtcurve.so; returns its path."""
     if not force and not _stale():
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
+    embed_device_runtime()
     tmp = tempfile.mkdtemp(prefix="tcurve_build_", dir=OUT_DIR)
     common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-              *ARCH, f"-I{CSRC}"]
+              *ARCH, f"-I{CSRC}", f"-I{OUT_DIR}"]
     procs, objs = [], []
     try:
         for s in SOURCES:
@@ -60,7 +73,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
             if verbose and out:
                 print(out.decode(errors="replace"))
         out_tmp = os.path.join(tmp, "libtcurve.so")
-        subprocess.check_call([nvcc(), "-shared", *ARCH, "-cudart", "shared", "-o", out_tmp, *objs])
+        subprocess.check_call([nvcc(), "-shared", *ARCH, "-cudart", "shared", "-o", out_tmp, *objs,
+                               "-ldl"])
         os.replace(out_tmp, LIB)
     finally:
         shutil.rmtree(tmp, ignore_errors=True)

@@ -4,6 +4,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <memory>
+#include <mutex>
+#include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/tcurve.h"
@@ -35,6 +39,21 @@ enum : uint32_t {
   kErrTimeout = 4u,    // bounded wait gave up
 };
 
+// The reflected triangulation T^diamond (Alg. 1, line 1) in sweep order:
+// vertices sorted by (y, x); fan[v] = earlier neighbours of v in angular
+// order, link[v][n] = 1 if fan[v][n-1], fan[v][n] and v span a triangle;
+// k = lattice index and c = Eq. 2 parity constant of each vertex; anti =
+// antipodal boundary pairs (v < w); bedge = one boundary edge of each
+// antipodal pair of boundary edges.
+struct Diamond {
+  int d = 0, V = 0;
+  std::vector<int> x, y, k, c;
+  std::vector<std::vector<int>> fan, link;
+  std::vector<std::pair<int, int>> anti, bedge;
+};
+
+struct JitModule;  // compiled specialised kernels (jit.cpp)
+
 }  // namespace tcurve
 
 struct ts_tri {
@@ -44,6 +63,11 @@ struct ts_tri {
   std::vector<uint32_t> host_tables;
   uint32_t *d_tables = nullptr;  // lay.words words, 16-byte aligned
   uint32_t *d_err = nullptr;     // device error word (scratch, owned here)
+  tcurve::Diamond dia;
+  int kernel = 0;                // TS_KERNEL_*
+  std::mutex jit_mu;
+  std::shared_ptr<tcurve::JitModule> jit;
+  std::string jit_log;
 };
 
 struct ts_hist {
@@ -63,4 +87,16 @@ cudaError_t launch_real_schemes(const ts_tri *tri, const uint64_t *signs, uint64
 cudaError_t launch_enumerate(const ts_tri *tri, uint64_t lo, uint64_t hi, uint32_t flags,
                              ts_hist *hist, cudaStream_t stream);
 cudaError_t launch_hist_clear(ts_hist *hist, cudaStream_t stream);
+
+// Specialised kernels (jit.cpp).
+std::string jit_source(const Diamond &D);
+// Compile the generated source with NVRTC for sm_103a; returns the cubin (or
+// an empty string and the log in *log).
+std::string jit_compile_cubin(const std::string &src, std::string *log);
+cudaError_t jit_prepare(ts_tri *tri);  // compile + load once (thread-safe)
+cudaError_t launch_real_schemes_jit(ts_tri *tri, const uint64_t *signs, uint64_t n,
+                                    uint64_t *codes, cudaStream_t stream);
+cudaError_t launch_enumerate_jit(ts_tri *tri, uint64_t lo, uint64_t hi, uint32_t flags,
+                                 ts_hist *hist, cudaStream_t stream);
+void jit_release(ts_tri *tri);
 }  // namespace tcurve

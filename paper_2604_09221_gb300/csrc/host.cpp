@@ -76,21 +76,20 @@ bool triangles_of(int d, const int32_t *e, int n_edges, std::vector<std::array<P
   return true;
 }
 
-// Build T^diamond and the sweep tables.
+// Build T^diamond (Alg. 1, line 1) in sweep order.
 //
 // Sweep order: diamond vertices sorted by (y, x).  The "back neighbours" of
 // v (neighbours earlier in the sweep) lie in the half-plane below v plus its
 // left neighbour, so in angular order they form one fan, and two entries
 // that are consecutive in that order span a triangle with v unless the fan
 // is cut by the boundary of the diamond.  The link bit records which.
-bool build_tables(int d, const std::vector<std::array<Pt, 3>> &tris, ts_tri *t) {
+bool build_diamond(int d, const std::vector<std::array<Pt, 3>> &tris, Diamond &D) {
   std::vector<Pt> verts;
   for (int y = -d; y <= d; ++y)
     for (int x = -d; x <= d; ++x)
       if (std::abs(x) + std::abs(y) <= d) verts.push_back({x, y});
   std::sort(verts.begin(), verts.end());
   const int V = (int)verts.size();
-  if (V > 255) return false;
   std::map<Pt, int> pos;
   for (int v = 0; v < V; ++v) pos[verts[v]] = v;
 
@@ -109,19 +108,26 @@ bool build_tables(int d, const std::vector<std::array<Pt, 3>> &tris, ts_tri *t) 
       dtris.insert(id);
     }
   if ((int)dtris.size() != 4 * d * d) return false;
-
-  auto kc = [&](int v, int &k, int &c) {
-    int x = verts[v].x, y = verts[v].y, i = std::abs(x), j = std::abs(y);
-    k = lattice_index(d, i, j);
-    c = ((x < 0) ? (i & 1) : 0) ^ ((y < 0) ? (j & 1) : 0);  // Eq. 2
-  };
   auto has_tri = [&](int a, int b, int c) {
     std::array<int, 3> id{a, b, c};
     std::sort(id.begin(), id.end());
     return dtris.count(id) > 0;
   };
-
-  std::vector<uint32_t> vdesc(V), fan;
+  D.d = d;
+  D.V = V;
+  D.x.resize(V);
+  D.y.resize(V);
+  D.k.resize(V);
+  D.c.resize(V);
+  D.fan.assign(V, {});
+  D.link.assign(V, {});
+  for (int v = 0; v < V; ++v) {
+    int x = verts[v].x, y = verts[v].y, i = std::abs(x), j = std::abs(y);
+    D.x[v] = x;
+    D.y[v] = y;
+    D.k[v] = lattice_index(d, i, j);
+    D.c[v] = ((x < 0) ? (i & 1) : 0) ^ ((y < 0) ? (j & 1) : 0);  // Eq. 2
+  }
   for (int v = 0; v < V; ++v) {
     std::vector<int> back;
     for (int u : adj[v])
@@ -132,24 +138,15 @@ bool build_tables(int d, const std::vector<std::array<Pt, 3>> &tris, ts_tri *t) 
       int bx = verts[b].x - verts[v].x, by = verts[b].y - verts[v].y;
       return cross(ax, ay, bx, by) > 0;
     });
-    int k, c;
-    kc(v, k, c);
-    if (back.size() > 63 || fan.size() > 65535) return false;
-    vdesc[v] = (uint32_t)k | ((uint32_t)c << 6) | ((uint32_t)back.size() << 7) |
-               ((uint32_t)fan.size() << 16);
-    for (size_t n = 0; n < back.size(); ++n) {
-      int u = back[n], ku, cu;
-      kc(u, ku, cu);
-      uint32_t link = (n > 0 && has_tri(v, back[n - 1], u)) ? 1u : 0u;
-      fan.push_back((uint32_t)u | ((uint32_t)ku << 8) | ((uint32_t)cu << 14) | (link << 15));
-    }
+    D.fan[v] = back;
+    for (size_t n = 0; n < back.size(); ++n)
+      D.link[v].push_back((n > 0 && has_tri(v, back[n - 1], back[n])) ? 1 : 0);
   }
-  std::vector<uint32_t> anti, bedge;
   for (int v = 0; v < V; ++v) {
     const Pt p = verts[v];
     if (std::abs(p.x) + std::abs(p.y) != d) continue;
     int w = pos.at({-p.x, -p.y});
-    if (v < w) anti.push_back((uint32_t)v | ((uint32_t)w << 8));
+    if (v < w) D.anti.push_back({v, w});
   }
   std::set<std::pair<int, int>> seen;
   for (int a = 0; a < V; ++a)
@@ -158,17 +155,35 @@ bool build_tables(int d, const std::vector<std::array<Pt, 3>> &tris, ts_tri *t) 
       const Pt pa = verts[a], pb = verts[b];
       if (std::abs(pa.x) + std::abs(pa.y) != d || std::abs(pb.x) + std::abs(pb.y) != d) continue;
       int a2 = pos.at({-pa.x, -pa.y}), b2 = pos.at({-pb.x, -pb.y});
-      auto key2 = std::make_pair(std::min(a2, b2), std::max(a2, b2));
-      if (seen.count(key2)) continue;
+      if (seen.count({std::min(a2, b2), std::max(a2, b2)})) continue;
       seen.insert({a, b});
-      int ka, ca, kb, cb;
-      kc(a, ka, ca);
-      kc(b, kb, cb);
-      bedge.push_back((uint32_t)a | ((uint32_t)b << 8) | ((uint32_t)ka << 16) | ((uint32_t)ca << 22) |
-                      ((uint32_t)kb << 23) | ((uint32_t)cb << 29));
+      D.bedge.push_back({a, b});
     }
-  if ((int)anti.size() != 2 * d || (int)bedge.size() != 2 * d) return false;
+  return (int)D.anti.size() == 2 * d && (int)D.bedge.size() == 2 * d;
+}
 
+// Pack the diamond into the tables the generic kernels stage into shared
+// memory (layout in engine.h).
+bool pack_tables(const Diamond &D, ts_tri *t) {
+  const int V = D.V;
+  if (V > 255) return false;
+  std::vector<uint32_t> vdesc(V), fan, anti, bedge;
+  for (int v = 0; v < V; ++v) {
+    if (D.fan[v].size() > 63 || fan.size() > 65535) return false;
+    vdesc[v] = (uint32_t)D.k[v] | ((uint32_t)D.c[v] << 6) | ((uint32_t)D.fan[v].size() << 7) |
+               ((uint32_t)fan.size() << 16);
+    for (size_t n = 0; n < D.fan[v].size(); ++n) {
+      int u = D.fan[v][n];
+      fan.push_back((uint32_t)u | ((uint32_t)D.k[u] << 8) | ((uint32_t)D.c[u] << 14) |
+                    ((uint32_t)D.link[v][n] << 15));
+    }
+  }
+  for (auto &p : D.anti) anti.push_back((uint32_t)p.first | ((uint32_t)p.second << 8));
+  for (auto &e : D.bedge) {
+    int a = e.first, b = e.second;
+    bedge.push_back((uint32_t)a | ((uint32_t)b << 8) | ((uint32_t)D.k[a] << 16) |
+                    ((uint32_t)D.c[a] << 22) | ((uint32_t)D.k[b] << 23) | ((uint32_t)D.c[b] << 29));
+  }
   TableLayout L{};
   L.V = V;
   L.NF = (uint32_t)fan.size();
@@ -259,7 +274,7 @@ ts_status ts_load_triangulation(int d, const int32_t *edges_ij, int n_edges, ts_
   t->sw = (t->np + 63) / 64;
   t->nmax = (d % 2 == 0) ? harnack(d) : harnack(d) - 1;
   t->cw = (2 * t->nmax + 1 + 63) / 64;
-  if (!build_tables(d, tris, t)) {
+  if (!build_diamond(d, tris, t->dia) || !pack_tables(t->dia, t)) {
     delete t;
     return TS_ENOTTRI;
   }
@@ -281,6 +296,7 @@ ts_status ts_load_triangulation(int d, const int32_t *edges_ij, int n_edges, ts_
 
 void ts_free_triangulation(ts_tri *t) {
   if (!t) return;
+  jit_release(t);
   if (t->d_tables) cudaFree(t->d_tables);
   if (t->d_err) cudaFree(t->d_err);
   delete t;
@@ -291,11 +307,71 @@ int ts_num_points(const ts_tri *t) { return t ? t->np : 0; }
 int ts_sign_words(const ts_tri *t) { return t ? t->sw : 0; }
 int ts_code_words(const ts_tri *t) { return t ? t->cw : 0; }
 
-ts_status ts_real_schemes(const ts_tri *t, const uint64_t *signs, uint64_t n, uint64_t *codes,
+namespace {
+// Kernel choice: the specialised kernel for sweeps and large batches (AUTO),
+// the table-driven kernel otherwise or when specialisation is unavailable.
+bool want_specialised(ts_tri *t, uint64_t n, bool sweep) {
+  if (t->kernel == TS_KERNEL_TABLE) return false;
+  if (t->kernel == TS_KERNEL_SPECIALIZED) return true;
+  if (!sweep && n < (1u << 16)) return false;
+  return jit_prepare(t) == cudaSuccess;
+}
+}  // namespace
+
+ts_status ts_real_schemes(const ts_tri *tc, const uint64_t *signs, uint64_t n, uint64_t *codes,
                           void *stream) {
-  if (!t || (n && (!signs || !codes))) return TS_EINVAL;
+  if (!tc || (n && (!signs || !codes))) return TS_EINVAL;
   if (n == 0) return TS_OK;
+  ts_tri *t = const_cast<ts_tri *>(tc);  // only the lazily compiled kernel cache changes
+  if (want_specialised(t, n, false))
+    return cuda_status(launch_real_schemes_jit(t, signs, n, codes, (cudaStream_t)stream));
   return cuda_status(launch_real_schemes(t, signs, n, codes, (cudaStream_t)stream));
+}
+
+ts_status ts_set_kernel(ts_tri *t, int kind) {
+  if (!t || kind < TS_KERNEL_AUTO || kind > TS_KERNEL_SPECIALIZED) return TS_EINVAL;
+  t->kernel = kind;
+  return TS_OK;
+}
+
+ts_status ts_prepare(ts_tri *t) {
+  if (!t) return TS_EINVAL;
+  return cuda_status(jit_prepare(t));
+}
+
+ts_status ts_specialized_log(const ts_tri *t, char *buf, size_t len) {
+  if (!t || !buf || !len) return TS_EINVAL;
+  std::string lg = t->jit_log;
+  size_t n = std::min(len - 1, lg.size());
+  std::memcpy(buf, lg.data(), n);
+  buf[n] = 0;
+  return lg.size() + 1 > len ? TS_EOVERFLOW : TS_OK;
+}
+
+ts_status ts_specialized_source(int d, const int32_t *edges_ij, int n_edges, int compile, char *buf,
+                                size_t len, size_t *needed) {
+  if ((!edges_ij && n_edges > 0) || n_edges < 0 || d < 1 || (len && !buf)) return TS_EINVAL;
+  if (d > kMaxDegree) return TS_EUNSUPPORTED;
+  std::vector<std::array<Pt, 3>> tris;
+  if (!triangles_of(d, edges_ij, n_edges, tris)) return TS_ENOTTRI;
+  Diamond D;
+  if (!build_diamond(d, tris, D)) return TS_ENOTTRI;
+  std::string out = jit_source(D);
+  ts_status st = TS_OK;
+  if (compile) {
+    std::string log;
+    std::string cubin = jit_compile_cubin(out, &log);
+    out = log;
+    if (cubin.empty()) st = TS_ECUDA;
+  }
+  if (needed) *needed = out.size() + 1;
+  if (len) {
+    size_t n = std::min(len - 1, out.size());
+    std::memcpy(buf, out.data(), n);
+    buf[n] = 0;
+    if (out.size() + 1 > len && st == TS_OK) st = TS_EOVERFLOW;
+  }
+  return st;
 }
 
 ts_status ts_sync(const ts_tri *t, void *stream) {
@@ -318,7 +394,10 @@ ts_status ts_real_schemes_host(const ts_tri *t, const uint64_t *signs_host, uint
   cudaError_t e = cudaMalloc(&ds, bs);
   if (e == cudaSuccess) e = cudaMalloc(&dc, bc);
   if (e == cudaSuccess) e = cudaMemcpy(ds, signs_host, bs, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = launch_real_schemes(t, ds, n, dc, 0);
+  if (e == cudaSuccess) {
+    ts_status ls = ts_real_schemes(t, ds, n, dc, nullptr);
+    if (ls != TS_OK) e = cudaErrorLaunchFailure;
+  }
   if (e == cudaSuccess) e = cudaMemcpy(codes_host, dc, bc, cudaMemcpyDeviceToHost);
   if (ds) cudaFree(ds);
   if (dc) cudaFree(dc);
@@ -378,6 +457,9 @@ ts_status ts_enumerate(const ts_tri *t, uint64_t lo, uint64_t hi, uint32_t flags
   int free_bits = t->np - ((flags & TS_ENUM_FLIP) ? 1 : 0) - ((flags & TS_ENUM_REDUCED) ? 3 : 0);
   if (free_bits < 64 && hi > (1ull << free_bits)) return TS_EINVAL;
   if (lo == hi) return TS_OK;
+  ts_tri *tm = const_cast<ts_tri *>(t);
+  if (want_specialised(tm, hi - lo, true))
+    return cuda_status(launch_enumerate_jit(tm, lo, hi, flags, h, (cudaStream_t)stream));
   return cuda_status(launch_enumerate(t, lo, hi, flags, h, (cudaStream_t)stream));
 }
 

@@ -1,0 +1,358 @@
+// jit.cpp -- triangulation-specialised kernels.
+//
+// For a loaded triangulation the host writes the sweep of Algorithm 1
+// (lines 1-4) as straight-line CUDA: every vertex of T^diamond in sweep
+// order becomes a few integer instructions whose operands (lattice bit
+// positions, Eq. 2 parity constants, fan neighbours, link bits, antipodal
+// partners) are immediates, and the provisional component label of each
+// vertex is a register.  The generated function is spliced into the device
+// runtime of jit_device.cuh (label union-find, region tree, AHU code, hash
+// histogram, kernels), compiled with NVRTC for sm_103a and loaded with the
+// driver API (entry points obtained from the runtime, so the library does not
+// link libcuda or libnvrtc; NVRTC is opened on first use).
+#include <cuda.h>
+#include <dlfcn.h>
+#include <nvrtc.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <map>
+#include <sstream>
+
+#include "engine.h"
+
+namespace tcurve {
+
+namespace {
+
+const char kDeviceSrc[] =
+#include "_jit_device_src.inc"
+    ;
+
+constexpr int kJitThreads = 256;
+
+struct Layout {
+  int lbytes, epw, wlab, nb, rmax, code64, wcode, wsmall;
+  int off_lpar, off_cand, off_bpair, off_adj, off_code, off_clen, off_order, off_tpar, words;
+  int threads, hash;
+};
+
+Layout layout_for(const Diamond &D) {
+  Layout L{};
+  const int d = D.d, V = D.V;
+  const int M = (d - 1) * (d - 2) / 2 + 1, nmax = (d % 2 == 0) ? M : M - 1;
+  L.lbytes = V <= 126 ? 1 : 2;  // label ids and the "none" value fit 7 / 15 bits
+  L.epw = 4 / L.lbytes;
+  L.wlab = (V + L.epw - 1) / L.epw;
+  L.nb = (d % 2) ? 2 * d : 0;
+  L.rmax = nmax + 1;
+  L.code64 = 2 * nmax > 30 ? 1 : 0;
+  L.wcode = L.rmax * (L.code64 ? 2 : 1);
+  const int wb = (L.rmax + 3) / 4;
+  L.wsmall = 3 * wb;
+  L.off_lpar = 0;
+  L.off_cand = L.wlab;
+  L.off_bpair = 2 * L.wlab;
+  L.off_adj = L.off_bpair + L.nb;
+  int end = L.off_adj + L.rmax;
+  if (L.wcode + L.wsmall <= L.wlab) {
+    L.off_code = L.off_cand;  // cand is dead once the region tree is built
+  } else {
+    L.off_code = end;
+    end += L.wcode + L.wsmall;
+  }
+  L.off_clen = L.off_code + L.wcode;
+  L.off_order = L.off_clen + wb;
+  L.off_tpar = L.off_order + wb;
+  L.words = end;
+  L.threads = kJitThreads;
+  L.hash = d <= 7 ? 256 : 1024;
+  return L;
+}
+
+// ---- NVRTC, opened on first use ----
+struct Nvrtc {
+  void *h = nullptr;
+  decltype(&nvrtcCreateProgram) create = nullptr;
+  decltype(&nvrtcCompileProgram) compile = nullptr;
+  decltype(&nvrtcGetProgramLogSize) log_size = nullptr;
+  decltype(&nvrtcGetProgramLog) log = nullptr;
+  decltype(&nvrtcGetCUBINSize) cubin_size = nullptr;
+  decltype(&nvrtcGetCUBIN) cubin = nullptr;
+  decltype(&nvrtcDestroyProgram) destroy = nullptr;
+  bool ok = false;
+};
+
+Nvrtc &nvrtc() {
+  static Nvrtc n;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    const char *names[] = {"libnvrtc.so.13", "libnvrtc.so", "/usr/local/cuda/lib64/libnvrtc.so.13",
+                           "/usr/local/cuda/lib64/libnvrtc.so"};
+    for (const char *nm : names)
+      if ((n.h = dlopen(nm, RTLD_NOW | RTLD_GLOBAL))) break;
+    if (!n.h) return;
+    n.create = (decltype(n.create))dlsym(n.h, "nvrtcCreateProgram");
+    n.compile = (decltype(n.compile))dlsym(n.h, "nvrtcCompileProgram");
+    n.log_size = (decltype(n.log_size))dlsym(n.h, "nvrtcGetProgramLogSize");
+    n.log = (decltype(n.log))dlsym(n.h, "nvrtcGetProgramLog");
+    n.cubin_size = (decltype(n.cubin_size))dlsym(n.h, "nvrtcGetCUBINSize");
+    n.cubin = (decltype(n.cubin))dlsym(n.h, "nvrtcGetCUBIN");
+    n.destroy = (decltype(n.destroy))dlsym(n.h, "nvrtcDestroyProgram");
+    n.ok = n.create && n.compile && n.log_size && n.log && n.cubin_size && n.cubin && n.destroy;
+  });
+  return n;
+}
+
+// ---- driver entry points (through the runtime) ----
+struct Driver {
+  decltype(&cuModuleLoadData) load = nullptr;
+  decltype(&cuModuleUnload) unload = nullptr;
+  decltype(&cuModuleGetFunction) get = nullptr;
+  decltype(&cuFuncSetAttribute) set_attr = nullptr;
+  decltype(&cuOccupancyMaxActiveBlocksPerMultiprocessor) occupancy = nullptr;
+  decltype(&cuLaunchKernel) launch = nullptr;
+  bool ok = false;
+};
+
+Driver &driver() {
+  static Driver d;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    auto get = [](const char *sym, void **fn) {
+      cudaDriverEntryPointQueryResult q;
+      return cudaGetDriverEntryPointByVersion(sym, fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+             q == cudaDriverEntryPointSuccess;
+    };
+    d.ok = get("cuModuleLoadData", (void **)&d.load) && get("cuModuleUnload", (void **)&d.unload) &&
+           get("cuModuleGetFunction", (void **)&d.get) &&
+           get("cuFuncSetAttribute", (void **)&d.set_attr) &&
+           get("cuOccupancyMaxActiveBlocksPerMultiprocessor", (void **)&d.occupancy) &&
+           get("cuLaunchKernel", (void **)&d.launch);
+  });
+  return d;
+}
+
+int sm_count_now() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 1;
+}
+
+}  // namespace
+
+std::string jit_compile_uncached(const std::string &src, std::string *log);
+
+struct JitModule {
+  CUmodule mod = nullptr;
+  CUfunction real = nullptr, enumerate = nullptr;
+  Layout L{};
+  size_t smem_real = 0, smem_enum = 0;
+  int bpsm_real = 0, bpsm_enum = 0;
+  ~JitModule() {
+    if (mod && driver().ok) driver().unload(mod);
+  }
+};
+
+std::string jit_source(const Diamond &D) {
+  const Layout L = layout_for(D);
+  const int d = D.d, V = D.V;
+  std::ostringstream o;
+  o << "// T-curve real-scheme kernels specialised to one triangulation of " << d
+    << "*Delta_2 (generated)\n";
+  o << "#define TC_D " << d << "\n#define TC_V " << V << "\n#define TC_NPOINTS "
+    << (d + 1) * (d + 2) / 2 << "\n#define TC_RMAX " << L.rmax << "\n#define TC_NB " << L.nb
+    << "\n#define TC_THREADS " << L.threads << "\n#define TC_HASH_SLOTS " << L.hash
+    << "\n#define TC_LABEL_BYTES " << L.lbytes << "\n#define TC_CODE64 " << L.code64
+    << "\n#define TC_OFF_LPAR " << L.off_lpar << "u\n#define TC_OFF_CAND " << L.off_cand
+    << "u\n#define TC_OFF_BPAIR " << L.off_bpair << "u\n#define TC_OFF_ADJ " << L.off_adj
+    << "u\n#define TC_OFF_CODE " << L.off_code << "u\n#define TC_OFF_CLEN " << L.off_clen
+    << "u\n#define TC_OFF_ORDER " << L.off_order << "u\n#define TC_OFF_TPAR " << L.off_tpar
+    << "u\n#define TC_WORDS " << L.words << "u\n";
+  const std::string dev(kDeviceSrc);
+  const size_t m = dev.find("//@@SPLICE@@");
+  o << dev.substr(0, m);
+
+  // which antipodal pairs / boundary edges complete at each vertex
+  std::vector<std::vector<int>> anti_at(V), bedge_at(V);
+  for (size_t i = 0; i < D.anti.size(); ++i) anti_at[D.anti[i].second].push_back((int)i);
+  if (d % 2)
+    for (size_t i = 0; i < D.bedge.size(); ++i)
+      bedge_at[std::max(D.bedge[i].first, D.bedge[i].second)].push_back((int)i);
+
+  o << "__device__ __forceinline__ u64 tc_classify(u64 sig, const TcScratch &S, u32 &err) {\n"
+    << "  const u32 slo = (u32)sig, shi = (u32)(sig >> 32);\n  u32 nl = 0, nb = 0;\n";
+  for (int v = 0; v < V; ++v) {
+    const auto &fan = D.fan[v];
+    const auto &lk = D.link[v];
+    const int m = (int)fan.size();
+    o << "  // vertex " << v << " (" << D.x[v] << "," << D.y[v] << ")\n";
+    o << "  const u32 s" << v << " = TC_BIT(" << D.k[v] << ") ^ " << D.c[v] << "u;\n";
+    o << "  u32 L" << v << ";\n";
+    if (m == 0) {
+      o << "  L" << v << " = nl; tc_newlab(S, nl, TC_NONE); ++nl;\n";
+    } else {
+      o << "  {\n";
+      for (int i = 0; i < m; ++i)
+        o << "    const u32 e" << i << " = s" << fan[i] << " ^ s" << v << " ^ 1u;\n";
+      o << "    L" << v << " = ";
+      for (int i = 0; i < m; ++i) o << "e" << i << " ? L" << fan[i] << " : ";
+      o << "nl;\n    if (!(";
+      for (int i = 0; i < m; ++i) o << (i ? " | " : "") << "e" << i;
+      o << ")) { tc_newlab(S, nl, L" << fan[0] << "); ++nl; }\n";
+      if (m >= 2) {
+        o << "    const u32 st0 = e0;\n";
+        for (int i = 1; i < m; ++i) {
+          o << "    const u32 st" << i << " = e" << i;
+          if (lk[i]) o << " & (e" << i - 1 << " ^ 1u)";
+          o << ";\n";
+        }
+        o << "    u32 any = st0, multi = 0;\n";
+        for (int i = 1; i < m; ++i) o << "    multi |= st" << i << " & any; any |= st" << i << ";\n";
+        o << "    if (multi) {\n      u32 a2 = st0;\n";
+        for (int i = 1; i < m; ++i)
+          o << "      if (st" << i << " & a2) tc_unite(S, L" << v << ", L" << fan[i]
+            << ", 0u);\n      a2 |= st" << i << ";\n";
+        o << "    }\n";
+      }
+      o << "  }\n";
+    }
+    for (int i : anti_at[v]) o << "  tc_unite(S, L" << D.anti[i].first << ", L" << v << ", 1u);\n";
+    for (int i : bedge_at[v]) {
+      const int a = D.bedge[i].first, b = D.bedge[i].second;
+      o << "  if (s" << a << " ^ s" << b << ") { tc_bpair(S, nb, L" << a << ", L" << b
+        << "); ++nb; }\n";
+    }
+  }
+  o << "  return tc_backend(S, nl, nb, err);\n}\n";
+  o << dev.substr(m);
+  return o.str();
+}
+
+std::string jit_compile_cubin(const std::string &src, std::string *log) {
+  // identical triangulations generate identical sources: compile once
+  static std::mutex cache_mu;
+  static std::map<std::string, std::pair<std::string, std::string>> cache;  // src -> (cubin, log)
+  {
+    std::lock_guard<std::mutex> g(cache_mu);
+    auto it = cache.find(src);
+    if (it != cache.end()) {
+      if (log) *log = it->second.second;
+      return it->second.first;
+    }
+  }
+  std::string lg;
+  std::string out = jit_compile_uncached(src, &lg);
+  if (log) *log = lg;
+  if (!out.empty()) {
+    std::lock_guard<std::mutex> g(cache_mu);
+    cache.emplace(src, std::make_pair(out, lg));
+  }
+  return out;
+}
+
+std::string jit_compile_uncached(const std::string &src, std::string *log) {
+  Nvrtc &nv = nvrtc();
+  if (!nv.ok) {
+    if (log) *log = "NVRTC library not found";
+    return {};
+  }
+  nvrtcProgram prog;
+  if (nv.create(&prog, src.c_str(), "tcurve_specialised.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) {
+    if (log) *log = "nvrtcCreateProgram failed";
+    return {};
+  }
+  const char *opts[] = {"-arch=sm_103a", "--std=c++17", "-lineinfo", "--ptxas-options=-v"};
+  nvrtcResult r = nv.compile(prog, 4, opts);
+  size_t ls = 0;
+  nv.log_size(prog, &ls);
+  std::string lg(ls, '\0');
+  if (ls) nv.log(prog, &lg[0]);
+  if (log) *log = lg;
+  std::string out;
+  if (r == NVRTC_SUCCESS) {
+    size_t cs = 0;
+    nv.cubin_size(prog, &cs);
+    out.resize(cs);
+    nv.cubin(prog, &out[0]);
+  }
+  nv.destroy(&prog);
+  return out;
+}
+
+cudaError_t jit_prepare(ts_tri *t) {
+  std::lock_guard<std::mutex> g(t->jit_mu);
+  if (t->jit) return cudaSuccess;
+  Driver &dr = driver();
+  if (!dr.ok) return cudaErrorNotSupported;
+  cudaError_t e = cudaFree(0);  // make the primary context current
+  if (e != cudaSuccess) return e;
+  const std::string src = jit_source(t->dia);
+  const std::string cubin = jit_compile_cubin(src, &t->jit_log);
+  if (cubin.empty()) return cudaErrorInvalidSource;
+  auto mod = std::make_shared<JitModule>();
+  mod->L = layout_for(t->dia);
+  if (dr.load(&mod->mod, cubin.data()) != CUDA_SUCCESS) return cudaErrorInvalidKernelImage;
+  if (dr.get(&mod->real, mod->mod, "tc_real_schemes") != CUDA_SUCCESS ||
+      dr.get(&mod->enumerate, mod->mod, "tc_enumerate") != CUDA_SUCCESS)
+    return cudaErrorSymbolNotFound;
+  const Layout &L = mod->L;
+  mod->smem_real = (size_t)L.words * 4 * L.threads;
+  mod->smem_enum = mod->smem_real + (size_t)L.hash * 16 + 16;
+  if (dr.set_attr(mod->real, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)mod->smem_real) !=
+          CUDA_SUCCESS ||
+      dr.set_attr(mod->enumerate, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES,
+                  (int)mod->smem_enum) != CUDA_SUCCESS)
+    return cudaErrorInvalidConfiguration;
+  if (dr.occupancy(&mod->bpsm_real, mod->real, L.threads, mod->smem_real) != CUDA_SUCCESS ||
+      dr.occupancy(&mod->bpsm_enum, mod->enumerate, L.threads, mod->smem_enum) != CUDA_SUCCESS ||
+      mod->bpsm_real < 1 || mod->bpsm_enum < 1)
+    return cudaErrorInvalidConfiguration;
+  t->jit = mod;
+  return cudaSuccess;
+}
+
+void jit_release(ts_tri *t) {
+  std::lock_guard<std::mutex> g(t->jit_mu);
+  t->jit.reset();
+}
+
+cudaError_t launch_real_schemes_jit(ts_tri *t, const uint64_t *signs, uint64_t n, uint64_t *codes,
+                                    cudaStream_t st) {
+  cudaError_t e = jit_prepare(t);
+  if (e != cudaSuccess) return e;
+  std::shared_ptr<JitModule> m = t->jit;
+  const uint64_t want = (n + m->L.threads - 1) / m->L.threads;
+  const uint64_t cap = (uint64_t)m->bpsm_real * sm_count_now();
+  const unsigned grid = (unsigned)std::min(want, cap);
+  void *args[] = {(void *)&signs, (void *)&n, (void *)&codes, (void *)&t->d_err};
+  if (driver().launch(m->real, grid, 1, 1, m->L.threads, 1, 1, (unsigned)m->smem_real, (CUstream)st,
+                      args, nullptr) != CUDA_SUCCESS)
+    return cudaErrorLaunchFailure;
+  return cudaSuccess;
+}
+
+cudaError_t launch_enumerate_jit(ts_tri *t, uint64_t lo, uint64_t hi, uint32_t flags, ts_hist *h,
+                                 cudaStream_t st) {
+  cudaError_t e = jit_prepare(t);
+  if (e != cudaSuccess) return e;
+  std::shared_ptr<JitModule> m = t->jit;
+  const uint64_t total = hi - lo;
+  const uint64_t chunk = (uint64_t)m->L.threads * 16;
+  const uint64_t want = (total + chunk - 1) / chunk;
+  const uint64_t cap = (uint64_t)m->bpsm_enum * sm_count_now();
+  const unsigned grid = (unsigned)std::min(want, cap);
+  e = cudaMemsetAsync(h->d_work, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  uint64_t slots = h->slots;
+  void *args[] = {(void *)&lo,       (void *)&total,       (void *)&flags,
+                  (void *)&h->d_keys, (void *)&h->d_counts, (void *)&slots,
+                  (void *)&h->d_err,  (void *)&h->d_failed, (void *)&h->d_work};
+  if (driver().launch(m->enumerate, grid, 1, 1, m->L.threads, 1, 1, (unsigned)m->smem_enum,
+                      (CUstream)st, args, nullptr) != CUDA_SUCCESS)
+    return cudaErrorLaunchFailure;
+  return cudaSuccess;
+}
+
+}  // namespace tcurve

@@ -1,0 +1,314 @@
+// jit_device.cuh -- device runtime of the triangulation-specialised kernels.
+//
+// jit.cpp generates, for one loaded triangulation, the sweep of Algorithm 1
+// lines 1-4 as straight-line code (the fans of T^diamond become immediate
+// bit positions, provisional component labels live in registers) and splices
+// it into this file at the marker line.  The prelude defines:
+//   TC_D, TC_V, TC_RMAX (regions), TC_NB (boundary-edge slots), TC_THREADS,
+//   TC_HASH_SLOTS, TC_LABEL_BYTES (1 or 2), TC_CODE64 (0/1),
+//   TC_OFF_LPAR, TC_OFF_CAND, TC_OFF_BPAIR, TC_OFF_ADJ, TC_OFF_CODE,
+//   TC_OFF_CLEN, TC_OFF_ORDER, TC_OFF_TPAR, TC_WORDS (per-thread scratch,
+//   in 32-bit words), TC_NPOINTS.
+//
+// Labels.  The sweep gives a vertex the label of its first same-sign earlier
+// neighbour, or a fresh label when it has none; the fresh label remembers the
+// label of the vertex's first earlier neighbour (a crossed edge, "cand").
+// Labels are joined in a union-find with orientation parity: parity 0 for two
+// labels of one component (a vertex whose same-sign earlier neighbours form
+// several runs of its fan), parity 1 across an antipodal boundary pair.  An
+// inconsistent join marks the set as containing an odd antipodal cycle, i.e.
+// the non-orientable region (Alg. 1 lines 6-7).  The back end turns the sets
+// into regions, the cand edges into the region tree (they connect every
+// component, so their projection is the whole tree), finds the root, and
+// writes the AHU code (Alg. 1 line 11).
+//
+// Scratch words are interleaved across the block's threads (word i of thread
+// t at [i * TC_THREADS + t]) so every per-thread access pattern is free of
+// shared-memory bank conflicts.
+
+typedef unsigned long long u64;
+typedef unsigned int u32;
+typedef unsigned short u16;
+typedef unsigned char u8;
+
+#if TC_LABEL_BYTES == 1
+typedef u8 lab_t;
+#define TC_EPW 4u
+#define TC_TOP 0x80u
+#else
+typedef u16 lab_t;
+#define TC_EPW 2u
+#define TC_TOP 0x8000u
+#endif
+#define TC_LOW (TC_TOP - 1u)
+#define TC_NONE TC_LOW
+
+#define TC_ERR_INTERNAL 1u
+#define TC_ERR_OVERFLOW 2u
+
+struct TcScratch {
+  u32 *w;  // word 0 of this thread
+  __device__ __forceinline__ lab_t *lab(u32 off, u32 i) const {
+    return reinterpret_cast<lab_t *>(w + (off + i / TC_EPW) * TC_THREADS) + (i % TC_EPW);
+  }
+  __device__ __forceinline__ u8 *byte(u32 off, u32 i) const {
+    return reinterpret_cast<u8 *>(w + (off + (i >> 2)) * TC_THREADS) + (i & 3u);
+  }
+  __device__ __forceinline__ u32 &word(u32 off, u32 i) const { return w[(off + i) * TC_THREADS]; }
+  __device__ __forceinline__ u32 lpar(u32 i) const { return *lab(TC_OFF_LPAR, i); }
+  __device__ __forceinline__ void set_lpar(u32 i, u32 v) const { *lab(TC_OFF_LPAR, i) = (lab_t)v; }
+  __device__ __forceinline__ u32 cand(u32 i) const { return *lab(TC_OFF_CAND, i); }
+  __device__ __forceinline__ void set_cand(u32 i, u32 v) const { *lab(TC_OFF_CAND, i) = (lab_t)v; }
+};
+
+__device__ __forceinline__ void tc_newlab(const TcScratch &S, u32 l, u32 c) {
+  S.set_lpar(l, l);
+  S.set_cand(l, c);
+}
+
+__device__ __forceinline__ u32 tc_find(const TcScratch &S, u32 x, u32 &par) {
+  par = 0;
+  u32 e = S.lpar(x);
+  while ((e & TC_LOW) != x) {
+    par ^= (e & TC_TOP) ? 1u : 0u;
+    x = e & TC_LOW;
+    e = S.lpar(x);
+  }
+  return x;
+}
+
+// Join labels a and b with relative orientation parity p.
+__device__ __noinline__ void tc_unite(const TcScratch &S, u32 a, u32 b, u32 p) {
+  u32 pa, pb;
+  const u32 ra = tc_find(S, a, pa), rb = tc_find(S, b, pb);
+  const u32 q = (pa ^ pb ^ p) & 1u;
+  if (ra == rb) {
+    if (q) S.set_cand(ra, S.cand(ra) | TC_TOP);  // odd cycle
+    return;
+  }
+  const u32 lo = ra < rb ? ra : rb, hi = ra < rb ? rb : ra;
+  const u32 odd = S.cand(hi) & TC_TOP;
+  S.set_lpar(hi, lo | (q ? TC_TOP : 0u));
+  if (odd) S.set_cand(lo, S.cand(lo) | TC_TOP);
+}
+
+__device__ __forceinline__ void tc_bpair(const TcScratch &S, u32 i, u32 la, u32 lb) {
+  S.word(TC_OFF_BPAIR, i) = la | (lb << 16);
+}
+
+#if TC_CODE64
+typedef u64 code_t;
+#define TC_CODE_BITS 64u
+__device__ __forceinline__ code_t tc_code(const TcScratch &S, u32 r) {
+  return (u64)S.word(TC_OFF_CODE, 2 * r) | ((u64)S.word(TC_OFF_CODE, 2 * r + 1) << 32);
+}
+__device__ __forceinline__ void tc_set_code(const TcScratch &S, u32 r, code_t v) {
+  S.word(TC_OFF_CODE, 2 * r) = (u32)v;
+  S.word(TC_OFF_CODE, 2 * r + 1) = (u32)(v >> 32);
+}
+#else
+typedef u32 code_t;
+#define TC_CODE_BITS 32u
+__device__ __forceinline__ code_t tc_code(const TcScratch &S, u32 r) { return S.word(TC_OFF_CODE, r); }
+__device__ __forceinline__ void tc_set_code(const TcScratch &S, u32 r, code_t v) {
+  S.word(TC_OFF_CODE, r) = v;
+}
+#endif
+
+// Regions, region tree, root and canonical code from the label sets.
+__device__ __noinline__ u64 tc_backend(const TcScratch &S, u32 nl, u32 nb, u32 &err) {
+  // 1. sets -> region ids (stored over lpar); odd-cycle flags of the roots
+  u32 R = 0;
+  u64 odd = 0;
+  for (u32 l = 0; l < nl; ++l) {
+    const u32 p = S.lpar(l) & TC_LOW;
+    if (p == l) {
+      if (R >= TC_RMAX) { err |= TC_ERR_OVERFLOW; return 0; }
+      if (S.cand(l) & TC_TOP) odd |= 1ull << R;
+      S.set_lpar(l, R);
+      ++R;
+    } else {
+      S.set_lpar(l, S.lpar(p));  // p < l already holds its region id
+    }
+  }
+  // 2. region tree from the cand edges
+  for (u32 r = 0; r < R; ++r) S.word(TC_OFF_ADJ, r) = 0;
+  for (u32 l = 1; l < nl; ++l) {
+    const u32 c = S.cand(l) & TC_LOW;
+    if (c == TC_NONE) continue;
+    const u32 a = S.lpar(l), b = S.lpar(c);
+    if (a != b) {
+      S.word(TC_OFF_ADJ, a) |= 1u << b;
+      S.word(TC_OFF_ADJ, b) |= 1u << a;
+    }
+  }
+  // 3. root: odd antipodal cycle (even d) / both sides of the pseudoline (odd d)
+  int root = -1;
+#if TC_D % 2 == 0
+  if (__popcll(odd) != 1) { err |= TC_ERR_INTERNAL; return 0; }
+  root = __ffsll(odd) - 1;
+#else
+  for (u32 i = 0; i < nb; ++i) {
+    const u32 e = S.word(TC_OFF_BPAIR, i);
+    const u32 ra = S.lpar(e & 0xFFFFu), rb = S.lpar(e >> 16);
+    if (ra != rb) continue;
+    if (root >= 0 && root != (int)ra) { err |= TC_ERR_INTERNAL; return 0; }
+    root = (int)ra;
+  }
+  if (root < 0) { err |= TC_ERR_INTERNAL; return 0; }
+#endif
+  u32 deg2 = 0;
+  for (u32 r = 0; r < R; ++r) deg2 += __popc(S.word(TC_OFF_ADJ, r));
+  if (deg2 != 2 * (R - 1)) { err |= TC_ERR_INTERNAL; return 0; }
+  // 4. BFS order from the root, then AHU codes from the leaves up
+  *S.byte(TC_OFF_ORDER, 0) = (u8)root;
+  *S.byte(TC_OFF_TPAR, root) = 0xFFu;
+  u32 seen = 1u << root, n = 1;
+  for (u32 q = 0; q < n; ++q) {
+    const u32 x = *S.byte(TC_OFF_ORDER, q);
+    u32 kids = S.word(TC_OFF_ADJ, x) & ~seen;
+    seen |= kids;
+    while (kids) {
+      const u32 y = __ffs(kids) - 1;
+      kids &= kids - 1;
+      *S.byte(TC_OFF_ORDER, n++) = (u8)y;
+      *S.byte(TC_OFF_TPAR, y) = (u8)x;
+    }
+  }
+  if (n != R) { err |= TC_ERR_INTERNAL; return 0; }
+  code_t bits = 0;
+  u32 nbits = 0;
+  for (int q = (int)n - 1; q >= 0; --q) {
+    const u32 x = *S.byte(TC_OFF_ORDER, q);
+    const u32 px = *S.byte(TC_OFF_TPAR, x);
+    u32 kids = S.word(TC_OFF_ADJ, x) & ~(px == 0xFFu ? 0u : (1u << px));
+    code_t v = 0;
+    u32 len = 0;
+    while (kids) {
+      u32 best = __ffs(kids) - 1;
+      code_t bv = tc_code(S, best);
+      for (u32 rest = kids & (kids - 1); rest; rest &= rest - 1) {
+        const u32 y = __ffs(rest) - 1;
+        const code_t cy = tc_code(S, y);
+        if (cy > bv) { bv = cy; best = y; }
+      }
+      v |= len < TC_CODE_BITS ? (bv >> len) : (code_t)0;
+      len += *S.byte(TC_OFF_CLEN, best);
+      kids &= ~(1u << best);
+    }
+    if (px != 0xFFu) {
+      tc_set_code(S, x, ((code_t)1 << (TC_CODE_BITS - 1)) | (v >> 1));
+      *S.byte(TC_OFF_CLEN, x) = (u8)(len + 2);
+    } else {
+      bits = v;
+      nbits = len;
+    }
+  }
+  if (nbits != 2 * (R - 1) || nbits > TC_CODE_BITS - 2) { err |= TC_ERR_INTERNAL; return 0; }
+  return (1ull << nbits) | (nbits ? (u64)(bits >> (TC_CODE_BITS - nbits)) : 0ull);
+}
+
+#define TC_BIT(k) ((k) < 32 ? ((slo >> ((k) & 31)) & 1u) : ((shi >> ((k) & 31)) & 1u))
+
+__device__ __forceinline__ u64 tc_classify(u64 sig, const TcScratch &S, u32 &err);
+
+//@@SPLICE@@
+
+// ---------------------------------------------------------------- kernels
+
+__device__ __forceinline__ TcScratch tc_scratch(u32 *smem) { return TcScratch{smem + threadIdx.x}; }
+
+extern "C" __global__ void __launch_bounds__(TC_THREADS)
+    tc_real_schemes(const u64 *__restrict__ signs, u64 n, u64 *__restrict__ codes, u32 *err_word) {
+  extern __shared__ __align__(16) u32 tc_smem[];
+  const TcScratch S = tc_scratch(tc_smem);
+  const u64 valid = TC_NPOINTS >= 64 ? ~0ull : ((1ull << (TC_NPOINTS & 63)) - 1);
+  u32 err = 0;
+  for (u64 i = (u64)blockIdx.x * TC_THREADS + threadIdx.x; i < n; i += (u64)gridDim.x * TC_THREADS)
+    codes[i] = tc_classify(signs[i] & valid, S, err);
+  if (err) atomicOr(err_word, err);
+}
+
+__device__ __forceinline__ u32 tc_hash_slot(u64 key, u64 mask) {
+  return (u32)(((key * 0x9E3779B97F4A7C15ull) >> 32) & mask);
+}
+
+__device__ void tc_global_add(u64 *gkeys, unsigned long long *gcnt, u64 gslots, u32 *gerr, u64 key,
+                              unsigned long long cnt) {
+  const u64 mask = gslots - 1;
+  u64 s = tc_hash_slot(key, mask);
+  for (u64 probe = 0; probe < gslots; ++probe) {
+    unsigned long long *kp = reinterpret_cast<unsigned long long *>(gkeys + s);
+    unsigned long long k = *reinterpret_cast<volatile unsigned long long *>(kp);
+    if (k == 0) k = atomicCAS(kp, 0ull, (unsigned long long)key);
+    if (k == 0 || k == key) {
+      atomicAdd(gcnt + s, cnt);
+      return;
+    }
+    s = (s + 1) & mask;
+  }
+  atomicOr(gerr, TC_ERR_OVERFLOW);
+}
+
+__device__ __forceinline__ u64 tc_enum_mask(u64 k, u32 flags) {
+  if (flags & 1u) return k << 1;
+  if (flags & 2u) return ((k & ((1ull << (TC_D - 1)) - 1)) << 2) | ((k >> (TC_D - 1)) << (TC_D + 2));
+  return k;
+}
+
+#define TC_CHUNK (TC_THREADS * 16)
+
+extern "C" __global__ void __launch_bounds__(TC_THREADS)
+    tc_enumerate(u64 lo, u64 total, u32 flags, u64 *gkeys, unsigned long long *gcnt, u64 gslots,
+                 u32 *gerr, unsigned long long *gfailed, unsigned long long *work) {
+  extern __shared__ __align__(16) u32 tc_smem[];
+  u64 *hkeys = reinterpret_cast<u64 *>(tc_smem + TC_WORDS * TC_THREADS);
+  unsigned long long *hcnt = reinterpret_cast<unsigned long long *>(hkeys + TC_HASH_SLOTS);
+  unsigned long long *chunk = hcnt + TC_HASH_SLOTS;
+  const TcScratch S = tc_scratch(tc_smem);
+  for (u32 s = threadIdx.x; s < TC_HASH_SLOTS; s += TC_THREADS) {
+    hkeys[s] = 0;
+    hcnt[s] = 0;
+  }
+  __syncthreads();
+  const u32 lane = threadIdx.x & 31u;
+  u32 err = 0;
+  unsigned long long failed = 0;
+  for (;;) {
+    if (threadIdx.x == 0) *chunk = atomicAdd(work, (unsigned long long)TC_CHUNK);
+    __syncthreads();
+    const u64 base = *chunk;
+    __syncthreads();
+    if (base >= total) break;
+    for (u32 j = 0; j < TC_CHUNK; j += TC_THREADS) {
+      const u64 idx = base + j + threadIdx.x;
+      u64 key = 0;
+      if (idx < total) {
+        key = tc_classify(tc_enum_mask(lo + idx, flags), S, err);
+        failed += key == 0;
+      }
+      const unsigned peers = __match_any_sync(0xffffffffu, key);
+      if (key != 0 && lane == (u32)(__ffs(peers) - 1)) {
+        const unsigned long long cnt = (unsigned long long)__popc(peers);
+        u32 s = tc_hash_slot(key, TC_HASH_SLOTS - 1);
+        bool done = false;
+        for (u32 probe = 0; probe < TC_HASH_SLOTS && !done; ++probe) {
+          unsigned long long *kp = reinterpret_cast<unsigned long long *>(hkeys + s);
+          unsigned long long k = *reinterpret_cast<volatile unsigned long long *>(kp);
+          if (k == 0) k = atomicCAS(kp, 0ull, (unsigned long long)key);
+          if (k == 0 || k == key) {
+            atomicAdd(hcnt + s, cnt);
+            done = true;
+          }
+          s = (s + 1) & (TC_HASH_SLOTS - 1);
+        }
+        if (!done) tc_global_add(gkeys, gcnt, gslots, gerr, key, cnt);
+      }
+    }
+  }
+  __syncthreads();
+  for (u32 s = threadIdx.x; s < TC_HASH_SLOTS; s += TC_THREADS)
+    if (hkeys[s]) tc_global_add(gkeys, gcnt, gslots, gerr, hkeys[s], hcnt[s]);
+  if (err) atomicOr(gerr, err);
+  if (failed) atomicAdd(gfailed, failed);
+}

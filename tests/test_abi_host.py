@@ -83,3 +83,16 @@ def test_scheme_string_matches_independent_printer(eng, orc, d):
     assert eng.scheme_string(6, 458) == "<1<1> + 2>"
     assert eng.scheme_string(7, 1) == "<J>"
     assert eng.scheme_string(6, 1) == "<0>"
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4, 5, 6, 7, 8, 9])
+def test_specialized_kernels_compile_for_sm103a(eng, d):
+    """The generated source of every degree compiles with NVRTC for sm_103a
+    without spilling much (checked on the host: no device needed)."""
+    import re
+    e = ti.regular_triangulation(d, seed=d) if d > 2 else ti.standard_triangulation(d)
+    src = eng.specialized_source(d, e)
+    assert "tc_classify" in src and src.count("// vertex ") == 2 * d * d + 2 * d + 1
+    log = eng.specialized_source(d, e, compile=True)
+    spills = [int(x) for x in re.findall(r"(\d+) bytes spill stores", log)]
+    assert spills and max(spills) <= 64, log[-2000:]

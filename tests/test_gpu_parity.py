@@ -33,6 +33,19 @@ def eng():
     return e
 
 
+KINDS = ["table", "specialized"]
+
+
+def load(eng, d, edges, kind):
+    tri = eng.Triangulation(d, edges)
+    if kind == "specialized":
+        tri.set_kernel(eng.TS_KERNEL_SPECIALIZED)
+        tri.prepare()
+    else:
+        tri.set_kernel(eng.TS_KERNEL_TABLE)
+    return tri
+
+
 def gpu_codes(eng, tri, masks):
     import torch
     t = torch.from_numpy(np.ascontiguousarray(masks).view(np.int64)).cuda()
@@ -46,39 +59,43 @@ def triangulations(d, k=2, seed=0):
     return out
 
 
+@pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("d", [1, 2, 3, 4])
-def test_exhaustive_small_degrees(eng, orc, d):
+def test_exhaustive_small_degrees(eng, orc, d, kind):
     masks = np.arange(1 << ti.num_points(d), dtype=np.uint64).reshape(-1, 1)
-    for name, e in triangulations(d, 3):
-        tri = eng.Triangulation(d, e)
+    for name, e in triangulations(d, 3 if kind == "table" else 1):
+        tri = load(eng, d, e, kind)
         got = gpu_codes(eng, tri, masks)
         want = orc.real_schemes(d, orc.triangles(d, e), masks)
         assert (got == want).all(), (d, name)
 
 
+@pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("d", [5, 6, 7, 8, 9])
-def test_random_sign_vectors(eng, orc, d):
+def test_random_sign_vectors(eng, orc, d, kind):
     n = 20011  # several blocks and a ragged tail
-    for idx, (name, e) in enumerate(triangulations(d, 3)):
+    for idx, (name, e) in enumerate(triangulations(d, 3 if kind == "table" else 1)):
         masks = ti.random_masks(n, d, 31 + d, stream=idx)
-        tri = eng.Triangulation(d, e)
+        tri = load(eng, d, e, kind)
         got = gpu_codes(eng, tri, masks)
         want = orc.real_schemes(d, orc.triangles(d, e), masks)
         bad = np.nonzero((got != want).any(axis=1))[0]
         assert bad.size == 0, (d, name, bad[:5], masks[bad[:5]])
 
 
+@pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("name", ["bow_tie", "rank016", "rank015"])
-def test_fig2_triangulations(eng, orc, name):
+def test_fig2_triangulations(eng, orc, name, kind):
     e = np.loadtxt(os.path.join(GOLDEN, f"fig2_{name}.edges"), dtype=np.int32, comments="#")
     masks = ti.random_masks(30000, 8, 99, stream=len(name))
-    tri = eng.Triangulation(8, e)
+    tri = load(eng, 8, e, kind)
     got = gpu_codes(eng, tri, masks)
     want = orc.real_schemes(8, orc.triangles(8, e), masks)
     assert (got == want).all()
 
 
-def test_special_sign_vectors(eng, orc):
+@pytest.mark.parametrize("kind", KINDS)
+def test_special_sign_vectors(eng, orc, kind):
     for d in range(1, 10):
         npts = ti.num_points(d)
         full = (1 << npts) - 1
@@ -86,26 +103,28 @@ def test_special_sign_vectors(eng, orc):
         harnack = sum(1 << n for n, (i, j) in enumerate(pts) if i % 2 == 0 and j % 2 == 0)
         alt = sum(1 << n for n, (i, j) in enumerate(pts) if (i + j) % 2)
         masks = np.array([[0], [full], [harnack], [alt], [full ^ alt], [1], [full >> 1]], dtype=np.uint64)
-        for name, e in triangulations(d, 1):
-            tri = eng.Triangulation(d, e)
+        for name, e in triangulations(d, 1)[: (2 if kind == "table" else 1)]:
+            tri = load(eng, d, e, kind)
             assert (gpu_codes(eng, tri, masks) == orc.real_schemes(d, orc.triangles(d, e), masks)).all()
 
 
-def test_stray_high_bits_are_ignored(eng):
+@pytest.mark.parametrize("kind", KINDS)
+def test_stray_high_bits_are_ignored(eng, kind):
     d = 6
     e = ti.regular_triangulation(d, seed=5)
-    tri = eng.Triangulation(d, e)
+    tri = load(eng, d, e, kind)
     masks = ti.random_masks(4096, d, 1)
     dirty = masks | (np.uint64(0xABCDEF) << np.uint64(ti.num_points(d)))
     assert (gpu_codes(eng, tri, masks) == gpu_codes(eng, tri, dirty)).all()
 
 
-@pytest.mark.parametrize("n", [0, 1, 31, 127, 128, 129, 4097])
-def test_batch_sizes(eng, orc, n):
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("n", [0, 1, 31, 127, 128, 129, 4097, 300001])
+def test_batch_sizes(eng, orc, n, kind):
     import torch
     d = 7
     e = ti.regular_triangulation(d, seed=77)
-    tri = eng.Triangulation(d, e)
+    tri = load(eng, d, e, kind)
     masks = ti.random_masks(max(n, 1), d, 3)[:n]
     got = tri.real_schemes(torch.from_numpy(masks.view(np.int64)).cuda().reshape(-1, 1))
     assert got.shape == (n, 1)
@@ -128,6 +147,7 @@ def oracle_hist(orc, d, e, masks):
 
 
 def gpu_hist(eng, tri, lo, hi, flags=0):
+    """Histogram of ts_enumerate over [lo, hi)."""
     h = eng.Histogram(4096, tri.code_words)
     eng.enumerate_schemes(tri, lo, hi, h, flags)
     codes, counts, failed = h.read()
@@ -141,18 +161,20 @@ def reduced_masks(d, ks):
     return ((low << np.uint64(2)) | ((ks >> np.uint64(d - 1)) << np.uint64(d + 2))).reshape(-1, 1)
 
 
+@pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("d", [4, 5])
-def test_enumerate_full_range(eng, orc, d):
+def test_enumerate_full_range(eng, orc, d, kind):
     e = ti.regular_triangulation(d, seed=50 + d)
-    tri = eng.Triangulation(d, e)
+    tri = load(eng, d, e, kind)
     n = 1 << ti.num_points(d)
     assert gpu_hist(eng, tri, 0, n) == oracle_hist(orc, d, e, np.arange(n, dtype=np.uint64).reshape(-1, 1))
 
 
+@pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("d", [6, 7, 8, 9])
-def test_enumerate_ragged_ranges_and_flags(eng, orc, d):
+def test_enumerate_ragged_ranges_and_flags(eng, orc, d, kind):
     e = ti.regular_triangulation(d, seed=60 + d)
-    tri = eng.Triangulation(d, e)
+    tri = load(eng, d, e, kind)
     lo, hi = 123457, 123457 + 50001
     ks = np.arange(lo, hi, dtype=np.uint64)
     assert gpu_hist(eng, tri, lo, hi) == oracle_hist(orc, d, e, ks.reshape(-1, 1))
@@ -160,25 +182,27 @@ def test_enumerate_ragged_ranges_and_flags(eng, orc, d):
     assert gpu_hist(eng, tri, lo, hi, eng.TS_ENUM_REDUCED) == oracle_hist(orc, d, e, reduced_masks(d, ks))
 
 
-def test_enumerate_reduced_equals_full_over_8(eng):
+@pytest.mark.parametrize("kind", KINDS)
+def test_enumerate_reduced_equals_full_over_8(eng, kind):
     # (Z/2)^3 acts freely and preserves schemes (Sec. 3): the full histogram is
     # 8 times the histogram over the representatives.
     d = 5
     e = ti.regular_triangulation(d, seed=3)
-    tri = eng.Triangulation(d, e)
+    tri = load(eng, d, e, kind)
     full = gpu_hist(eng, tri, 0, 1 << ti.num_points(d))
     red = gpu_hist(eng, tri, 0, 1 << (ti.num_points(d) - 3), eng.TS_ENUM_REDUCED)
     assert full == collections.Counter({k: 8 * v for k, v in red.items()})
 
 
-def test_enumerate_d7_full_size_slice(eng, orc):
+@pytest.mark.parametrize("kind", KINDS)
+def test_enumerate_d7_full_size_slice(eng, orc, kind):
     """The benchmark workload (degree 7, masks [0, 2^32)) in the launch
     configuration the bench uses: every count accounted for, every scheme a
     valid septic scheme, no more than the 121 that exist, and the sub-range
     [2^31, 2^31 + 2^16) equal to the oracle's histogram."""
     d = 7
     e = ti.regular_triangulation(d, seed=7)
-    tri = eng.Triangulation(d, e)
+    tri = load(eng, d, e, kind)
     full = gpu_hist(eng, tri, 0, 1 << 32)
     assert sum(full.values()) == 1 << 32
     assert len(full) <= 121
@@ -187,3 +211,13 @@ def test_enumerate_d7_full_size_slice(eng, orc):
     lo = 1 << 31
     ks = np.arange(lo, lo + (1 << 16), dtype=np.uint64).reshape(-1, 1)
     assert gpu_hist(eng, tri, lo, lo + (1 << 16)) == oracle_hist(orc, d, e, ks)
+
+
+def test_kernels_agree_on_full_size_sweep(eng):
+    """Table-driven and specialised sweeps of the bench slice give the same
+    histogram (both are checked against the oracle on sub-ranges above)."""
+    d = 7
+    e = ti.regular_triangulation(d, seed=7)
+    a = gpu_hist(eng, load(eng, d, e, "table"), 0, 1 << 32)
+    b = gpu_hist(eng, load(eng, d, e, "specialized"), 0, 1 << 32)
+    assert a == b
