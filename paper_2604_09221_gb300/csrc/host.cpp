@@ -78,17 +78,25 @@ bool triangles_of(int d, const int32_t *e, int n_edges, std::vector<std::array<P
 
 // Build T^diamond (Alg. 1, line 1) in sweep order.
 //
-// Sweep order: diamond vertices sorted by (y, x).  The "back neighbours" of
-// v (neighbours earlier in the sweep) lie in the half-plane below v plus its
-// left neighbour, so in angular order they form one fan, and two entries
-// that are consecutive in that order span a triangle with v unless the fan
-// is cut by the boundary of the diamond.  The link bit records which.
+// Sweep order: the lower half (y < 0) row by row upwards, then the upper half
+// (y > 0) row by row downwards, then the middle row y = 0; x ascending in
+// every row.  No edge of T^diamond crosses the x-axis (each edge lies in one
+// quadrant), so the two halves never meet before the middle row.  The "back
+// neighbours" of v (neighbours earlier in the sweep) then lie in one angular
+// range around v, listed counter-clockwise from the +x direction; two
+// consecutive entries span a triangle with v unless the range is cut by the
+// boundary of the diamond, which the link bit records.  Every vertex except
+// the first of each half, (0,-d) and (0,d), has a back neighbour, and those two
+// are antipodal, which the region-tree construction relies on.
 bool build_diamond(int d, const std::vector<std::array<Pt, 3>> &tris, Diamond &D) {
   std::vector<Pt> verts;
-  for (int y = -d; y <= d; ++y)
+  for (int y = -d; y <= -1; ++y)
     for (int x = -d; x <= d; ++x)
       if (std::abs(x) + std::abs(y) <= d) verts.push_back({x, y});
-  std::sort(verts.begin(), verts.end());
+  for (int y = d; y >= 1; --y)
+    for (int x = -d; x <= d; ++x)
+      if (std::abs(x) + std::abs(y) <= d) verts.push_back({x, y});
+  for (int x = -d; x <= d; ++x) verts.push_back({x, 0});
   const int V = (int)verts.size();
   std::map<Pt, int> pos;
   for (int v = 0; v < V; ++v) pos[verts[v]] = v;
@@ -132,10 +140,13 @@ bool build_diamond(int d, const std::vector<std::array<Pt, 3>> &tris, Diamond &D
     std::vector<int> back;
     for (int u : adj[v])
       if (u < v) back.push_back(u);
-    // angular order from the left neighbour, counter-clockwise below v
+    // counter-clockwise angle from the +x direction, in (0, 2 pi]
+    auto half = [](int dx, int dy) { return (dy > 0 || (dy == 0 && dx < 0)) ? 0 : 1; };
     std::sort(back.begin(), back.end(), [&](int a, int b) {
       int ax = verts[a].x - verts[v].x, ay = verts[a].y - verts[v].y;
       int bx = verts[b].x - verts[v].x, by = verts[b].y - verts[v].y;
+      int ha = half(ax, ay), hb = half(bx, by);
+      if (ha != hb) return ha < hb;
       return cross(ax, ay, bx, by) > 0;
     });
     D.fan[v] = back;

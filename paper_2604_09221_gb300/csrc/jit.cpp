@@ -32,11 +32,18 @@ const char kDeviceSrc[] =
 constexpr int kJitThreads = 256;
 
 struct Layout {
-  int lbytes, epw, wlab, nb, rmax, code64, wcode, wsmall;
-  int off_lpar, off_cand, off_bpair, off_adj, off_code, off_clen, off_order, off_tpar, words;
+  int lbytes, epw, wlab, nb, rmax, code64, wcode, wsmall, pcap;
+  int off_lpar, off_cand, off_bpair, off_pend, off_adj, off_code, off_clen, off_order, off_tpar,
+      words;
   int threads, hash;
 };
 
+// Per-thread scratch (32-bit words, interleaved across the block):
+//   [lpar | cand]  one entry per label (at most one label per vertex)
+//   [bpair]        crossed boundary edges (odd d), root detection
+//   [pend]         pending joins; later the region adjacency words
+// The AHU codes and the BFS arrays reuse [lpar | cand] once the region tree
+// is built, or get their own words when they do not fit there.
 Layout layout_for(const Diamond &D) {
   Layout L{};
   const int d = D.d, V = D.V;
@@ -50,13 +57,15 @@ Layout layout_for(const Diamond &D) {
   L.wcode = L.rmax * (L.code64 ? 2 : 1);
   const int wb = (L.rmax + 3) / 4;
   L.wsmall = 3 * wb;
+  L.pcap = 2 * d + 24;
   L.off_lpar = 0;
   L.off_cand = L.wlab;
   L.off_bpair = 2 * L.wlab;
-  L.off_adj = L.off_bpair + L.nb;
-  int end = L.off_adj + L.rmax;
-  if (L.wcode + L.wsmall <= L.wlab) {
-    L.off_code = L.off_cand;  // cand is dead once the region tree is built
+  L.off_pend = L.off_bpair + L.nb;
+  L.off_adj = L.off_pend;
+  int end = L.off_pend + std::max(L.pcap, L.rmax);
+  if (L.wcode + L.wsmall <= 2 * L.wlab) {
+    L.off_code = 0;
   } else {
     L.off_code = end;
     end += L.wcode + L.wsmall;
@@ -65,8 +74,12 @@ Layout layout_for(const Diamond &D) {
   L.off_order = L.off_clen + wb;
   L.off_tpar = L.off_order + wb;
   L.words = end;
-  L.threads = kJitThreads;
   L.hash = d <= 7 ? 256 : 1024;
+  // the largest block (multiple of 32, <= 256 threads) of which two fit per SM
+  L.threads = kJitThreads;
+  while (L.threads > 32 &&
+         2 * ((size_t)L.words * 4 * L.threads + L.hash * 16 + 16) > 224 * 1024)
+    L.threads -= 32;
   return L;
 }
 
@@ -165,6 +178,7 @@ std::string jit_source(const Diamond &D) {
     << (d + 1) * (d + 2) / 2 << "\n#define TC_RMAX " << L.rmax << "\n#define TC_NB " << L.nb
     << "\n#define TC_THREADS " << L.threads << "\n#define TC_HASH_SLOTS " << L.hash
     << "\n#define TC_LABEL_BYTES " << L.lbytes << "\n#define TC_CODE64 " << L.code64
+    << "\n#define TC_PCAP " << L.pcap << "u\n#define TC_OFF_PEND " << L.off_pend << "u"
     << "\n#define TC_OFF_LPAR " << L.off_lpar << "u\n#define TC_OFF_CAND " << L.off_cand
     << "u\n#define TC_OFF_BPAIR " << L.off_bpair << "u\n#define TC_OFF_ADJ " << L.off_adj
     << "u\n#define TC_OFF_CODE " << L.off_code << "u\n#define TC_OFF_CLEN " << L.off_clen
@@ -182,12 +196,14 @@ std::string jit_source(const Diamond &D) {
       bedge_at[std::max(D.bedge[i].first, D.bedge[i].second)].push_back((int)i);
 
   o << "__device__ __forceinline__ u64 tc_classify(u64 sig, const TcScratch &S, u32 &err) {\n"
-    << "  const u32 slo = (u32)sig, shi = (u32)(sig >> 32);\n  u32 nl = 0, nb = 0;\n";
+    << "  const u32 slo = (u32)sig, shi = (u32)(sig >> 32);\n  u32 nl = 0, nb = 0, np = 0;\n";
   for (int v = 0; v < V; ++v) {
     const auto &fan = D.fan[v];
     const auto &lk = D.link[v];
     const int m = (int)fan.size();
     o << "  // vertex " << v << " (" << D.x[v] << "," << D.y[v] << ")\n";
+    const int pushes = (m >= 2 ? m - 1 : 0) + (int)anti_at[v].size();
+    if (pushes) o << "  if (np > TC_PCAP - " << pushes << "u) { tc_unions(S, np); np = 0; }\n";
     o << "  const u32 s" << v << " = TC_BIT(" << D.k[v] << ") ^ " << D.c[v] << "u;\n";
     o << "  u32 L" << v << ";\n";
     if (m == 0) {
@@ -201,30 +217,28 @@ std::string jit_source(const Diamond &D) {
       o << "nl;\n    if (!(";
       for (int i = 0; i < m; ++i) o << (i ? " | " : "") << "e" << i;
       o << ")) { tc_newlab(S, nl, L" << fan[0] << "); ++nl; }\n";
+      // a same-sign entry that starts a new run after an earlier run: join
       if (m >= 2) {
-        o << "    const u32 st0 = e0;\n";
+        o << "    u32 any = e0;\n";
         for (int i = 1; i < m; ++i) {
-          o << "    const u32 st" << i << " = e" << i;
+          o << "    { const u32 st = e" << i;
           if (lk[i]) o << " & (e" << i - 1 << " ^ 1u)";
-          o << ";\n";
+          o << "; S.word(TC_OFF_PEND, np) = L" << v << " | (L" << fan[i]
+            << " << 16); np += st & any; any |= st; }\n";
         }
-        o << "    u32 any = st0, multi = 0;\n";
-        for (int i = 1; i < m; ++i) o << "    multi |= st" << i << " & any; any |= st" << i << ";\n";
-        o << "    if (multi) {\n      u32 a2 = st0;\n";
-        for (int i = 1; i < m; ++i)
-          o << "      if (st" << i << " & a2) tc_unite(S, L" << v << ", L" << fan[i]
-            << ", 0u);\n      a2 |= st" << i << ";\n";
-        o << "    }\n";
       }
       o << "  }\n";
     }
-    for (int i : anti_at[v]) o << "  tc_unite(S, L" << D.anti[i].first << ", L" << v << ", 1u);\n";
+    for (int i : anti_at[v])
+      o << "  S.word(TC_OFF_PEND, np) = L" << D.anti[i].first << " | (L" << v
+        << " << 16) | 0x80000000u; ++np;\n";
     for (int i : bedge_at[v]) {
       const int a = D.bedge[i].first, b = D.bedge[i].second;
       o << "  if (s" << a << " ^ s" << b << ") { tc_bpair(S, nb, L" << a << ", L" << b
         << "); ++nb; }\n";
     }
   }
+  o << "  tc_unions(S, np);\n";
   o << "  return tc_backend(S, nl, nb, err);\n}\n";
   o << dev.substr(m);
   return o.str();

@@ -5,17 +5,20 @@
 // bit positions, provisional component labels live in registers) and splices
 // it into this file at the marker line.  The prelude defines:
 //   TC_D, TC_V, TC_RMAX (regions), TC_NB (boundary-edge slots), TC_THREADS,
-//   TC_HASH_SLOTS, TC_LABEL_BYTES (1 or 2), TC_CODE64 (0/1),
-//   TC_OFF_LPAR, TC_OFF_CAND, TC_OFF_BPAIR, TC_OFF_ADJ, TC_OFF_CODE,
-//   TC_OFF_CLEN, TC_OFF_ORDER, TC_OFF_TPAR, TC_WORDS (per-thread scratch,
-//   in 32-bit words), TC_NPOINTS.
+//   TC_HASH_SLOTS, TC_LABEL_BYTES (1 or 2), TC_CODE64 (0/1), TC_PCAP
+//   (pending-union slots), TC_OFF_LPAR, TC_OFF_CAND, TC_OFF_BPAIR,
+//   TC_OFF_PEND, TC_OFF_ADJ, TC_OFF_CODE, TC_OFF_CLEN, TC_OFF_ORDER,
+//   TC_OFF_TPAR, TC_WORDS (per-thread scratch, in 32-bit words), TC_NPOINTS.
 //
 // Labels.  The sweep gives a vertex the label of its first same-sign earlier
 // neighbour, or a fresh label when it has none; the fresh label remembers the
 // label of the vertex's first earlier neighbour (a crossed edge, "cand").
 // Labels are joined in a union-find with orientation parity: parity 0 for two
 // labels of one component (a vertex whose same-sign earlier neighbours form
-// several runs of its fan), parity 1 across an antipodal boundary pair.  An
+// several runs of its fan), parity 1 across an antipodal boundary pair.  The
+// sweep only appends the joins to a per-thread list without branching; one
+// loop after the sweep applies them (a full list is applied early), so the
+// warp's lanes stay converged during the sweep.  An
 // inconsistent join marks the set as containing an odd antipodal cycle, i.e.
 // the non-orientable region (Alg. 1 lines 6-7).  The back end turns the sets
 // into regions, the cand edges into the region tree (they connect every
@@ -78,7 +81,7 @@ __device__ __forceinline__ u32 tc_find(const TcScratch &S, u32 x, u32 &par) {
 }
 
 // Join labels a and b with relative orientation parity p.
-__device__ __noinline__ void tc_unite(const TcScratch &S, u32 a, u32 b, u32 p) {
+__device__ __forceinline__ void tc_unite(const TcScratch &S, u32 a, u32 b, u32 p) {
   u32 pa, pb;
   const u32 ra = tc_find(S, a, pa), rb = tc_find(S, b, pb);
   const u32 q = (pa ^ pb ^ p) & 1u;
@@ -94,6 +97,14 @@ __device__ __noinline__ void tc_unite(const TcScratch &S, u32 a, u32 b, u32 p) {
 
 __device__ __forceinline__ void tc_bpair(const TcScratch &S, u32 i, u32 la, u32 lb) {
   S.word(TC_OFF_BPAIR, i) = la | (lb << 16);
+}
+
+// Pending joins: a | b << 16 | parity << 31.
+__device__ __noinline__ void tc_unions(const TcScratch &S, u32 np) {
+  for (u32 i = 0; i < np; ++i) {
+    const u32 e = S.word(TC_OFF_PEND, i);
+    tc_unite(S, e & 0xFFFFu, (e >> 16) & 0x7FFFu, e >> 31);
+  }
 }
 
 #if TC_CODE64
@@ -131,18 +142,7 @@ __device__ __noinline__ u64 tc_backend(const TcScratch &S, u32 nl, u32 nb, u32 &
       S.set_lpar(l, S.lpar(p));  // p < l already holds its region id
     }
   }
-  // 2. region tree from the cand edges
-  for (u32 r = 0; r < R; ++r) S.word(TC_OFF_ADJ, r) = 0;
-  for (u32 l = 1; l < nl; ++l) {
-    const u32 c = S.cand(l) & TC_LOW;
-    if (c == TC_NONE) continue;
-    const u32 a = S.lpar(l), b = S.lpar(c);
-    if (a != b) {
-      S.word(TC_OFF_ADJ, a) |= 1u << b;
-      S.word(TC_OFF_ADJ, b) |= 1u << a;
-    }
-  }
-  // 3. root: odd antipodal cycle (even d) / both sides of the pseudoline (odd d)
+  // 2. root: odd antipodal cycle (even d) / both sides of the pseudoline (odd d)
   int root = -1;
 #if TC_D % 2 == 0
   if (__popcll(odd) != 1) { err |= TC_ERR_INTERNAL; return 0; }
@@ -157,10 +157,27 @@ __device__ __noinline__ u64 tc_backend(const TcScratch &S, u32 nl, u32 nb, u32 &
   }
   if (root < 0) { err |= TC_ERR_INTERNAL; return 0; }
 #endif
-  u32 deg2 = 0;
-  for (u32 r = 0; r < R; ++r) deg2 += __popc(S.word(TC_OFF_ADJ, r));
+  // 3. region tree from the cand edges (adj reuses the pending-join slots)
+  for (u32 r = 0; r < R; ++r) S.word(TC_OFF_ADJ, r) = 0;
+  for (u32 l = 1; l < nl; ++l) {
+    const u32 c = S.cand(l) & TC_LOW;
+    if (c == TC_NONE) continue;
+    const u32 a = S.lpar(l), b = S.lpar(c);
+    if (a != b) {
+      S.word(TC_OFF_ADJ, a) |= 1u << b;
+      S.word(TC_OFF_ADJ, b) |= 1u << a;
+    }
+  }
+  u32 deg2 = 0, leaves = 0;
+  for (u32 r = 0; r < R; ++r) {
+    const u32 k = __popc(S.word(TC_OFF_ADJ, r));
+    deg2 += k;
+    if (k == 1 && (int)r != root) leaves |= 1u << r;
+  }
   if (deg2 != 2 * (R - 1)) { err |= TC_ERR_INTERNAL; return 0; }
-  // 4. BFS order from the root, then AHU codes from the leaves up
+  // 4. BFS order from the root, then AHU codes from the leaves up.  A leaf's
+  //    code is '10', the smallest code, so leaves go last among siblings and
+  //    need neither storage nor sorting.
   *S.byte(TC_OFF_ORDER, 0) = (u8)root;
   *S.byte(TC_OFF_TPAR, root) = 0xFFu;
   u32 seen = 1u << root, n = 1;
@@ -176,12 +193,16 @@ __device__ __noinline__ u64 tc_backend(const TcScratch &S, u32 nl, u32 nb, u32 &
     }
   }
   if (n != R) { err |= TC_ERR_INTERNAL; return 0; }
+  const code_t rep10 = (code_t)(0xAAAAAAAAAAAAAAAAull >> (64u - TC_CODE_BITS));
   code_t bits = 0;
   u32 nbits = 0;
   for (int q = (int)n - 1; q >= 0; --q) {
     const u32 x = *S.byte(TC_OFF_ORDER, q);
+    if (leaves & (1u << x)) continue;
     const u32 px = *S.byte(TC_OFF_TPAR, x);
-    u32 kids = S.word(TC_OFF_ADJ, x) & ~(px == 0xFFu ? 0u : (1u << px));
+    const u32 all = S.word(TC_OFF_ADJ, x) & ~(px == 0xFFu ? 0u : (1u << px));
+    u32 kids = all & ~leaves;
+    const u32 nleaf = __popc(all & leaves);
     code_t v = 0;
     u32 len = 0;
     while (kids) {
@@ -195,6 +216,11 @@ __device__ __noinline__ u64 tc_backend(const TcScratch &S, u32 nl, u32 nb, u32 &
       v |= len < TC_CODE_BITS ? (bv >> len) : (code_t)0;
       len += *S.byte(TC_OFF_CLEN, best);
       kids &= ~(1u << best);
+    }
+    if (nleaf) {
+      const code_t pat = rep10 & ~(((code_t)~(code_t)0) >> (2 * nleaf));
+      v |= len < TC_CODE_BITS ? (pat >> len) : (code_t)0;
+      len += 2 * nleaf;
     }
     if (px != 0xFFu) {
       tc_set_code(S, x, ((code_t)1 << (TC_CODE_BITS - 1)) | (v >> 1));
