@@ -32,9 +32,9 @@ const char kDeviceSrc[] =
 constexpr int kJitThreads = 256;
 
 struct Layout {
-  int lbytes, epw, wlab, nb, rmax, code64, wcode, wsmall, pcap;
+  int lbytes, epw, wlab, nb, rmax, code64, wcode, wsmall, pcap, wodd, snapw;
   int off_lpar, off_cand, off_bpair, off_pend, off_adj, off_code, off_clen, off_order, off_tpar,
-      words;
+      off_odd, words;
   int threads, hash;
 };
 
@@ -42,8 +42,10 @@ struct Layout {
 //   [lpar | cand]  one entry per label (at most one label per vertex)
 //   [bpair]        crossed boundary edges (odd d), root detection
 //   [pend]         pending joins; later the region adjacency words
-// The AHU codes and the BFS arrays reuse [lpar | cand] once the region tree
-// is built, or get their own words when they do not fit there.
+//   [odd]          odd-cycle flag per label
+// The AHU codes and the BFS arrays reuse [lpar] once the region tree is
+// built (the block sweep restores lpar from registers for every instance and
+// keeps cand), or get their own words when they do not fit there.
 Layout layout_for(const Diamond &D) {
   Layout L{};
   const int d = D.d, V = D.V;
@@ -58,13 +60,16 @@ Layout layout_for(const Diamond &D) {
   const int wb = (L.rmax + 3) / 4;
   L.wsmall = 3 * wb;
   L.pcap = 2 * d + 24;
+  L.wodd = (V + 31) / 32;
+  L.snapw = (32 + L.epw - 1) / L.epw;  // the block sweep snapshots 32 labels
   L.off_lpar = 0;
   L.off_cand = L.wlab;
   L.off_bpair = 2 * L.wlab;
   L.off_pend = L.off_bpair + L.nb;
   L.off_adj = L.off_pend;
-  int end = L.off_pend + std::max(L.pcap, L.rmax);
-  if (L.wcode + L.wsmall <= 2 * L.wlab) {
+  L.off_odd = L.off_pend + std::max(L.pcap, L.rmax);
+  int end = L.off_odd + L.wodd;
+  if (L.wcode + L.wsmall <= L.wlab) {
     L.off_code = 0;
   } else {
     L.off_code = end;
@@ -159,10 +164,10 @@ std::string jit_compile_uncached(const std::string &src, std::string *log);
 
 struct JitModule {
   CUmodule mod = nullptr;
-  CUfunction real = nullptr, enumerate = nullptr;
+  CUfunction real = nullptr, enumerate = nullptr, blocks = nullptr;
   Layout L{};
   size_t smem_real = 0, smem_enum = 0;
-  int bpsm_real = 0, bpsm_enum = 0;
+  int bpsm_real = 0, bpsm_enum = 0, bpsm_blocks = 0;
   ~JitModule() {
     if (mod && driver().ok) driver().unload(mod);
   }
@@ -179,6 +184,8 @@ std::string jit_source(const Diamond &D) {
     << "\n#define TC_THREADS " << L.threads << "\n#define TC_HASH_SLOTS " << L.hash
     << "\n#define TC_LABEL_BYTES " << L.lbytes << "\n#define TC_CODE64 " << L.code64
     << "\n#define TC_PCAP " << L.pcap << "u\n#define TC_OFF_PEND " << L.off_pend << "u"
+    << "\n#define TC_OFF_ODD " << L.off_odd << "u\n#define TC_WODD " << L.wodd << "u"
+    << "\n#define TC_B " << d + 1 << "u\n#define TC_SNAPW " << L.snapw << "u"
     << "\n#define TC_OFF_LPAR " << L.off_lpar << "u\n#define TC_OFF_CAND " << L.off_cand
     << "u\n#define TC_OFF_BPAIR " << L.off_bpair << "u\n#define TC_OFF_ADJ " << L.off_adj
     << "u\n#define TC_OFF_CODE " << L.off_code << "u\n#define TC_OFF_CLEN " << L.off_clen
@@ -195,51 +202,93 @@ std::string jit_source(const Diamond &D) {
     for (size_t i = 0; i < D.bedge.size(); ++i)
       bedge_at[std::max(D.bedge[i].first, D.bedge[i].second)].push_back((int)i);
 
-  o << "__device__ __forceinline__ u64 tc_classify(u64 sig, const TcScratch &S, u32 &err) {\n"
-    << "  const u32 slo = (u32)sig, shi = (u32)(sig >> 32);\n  u32 nl = 0, nb = 0, np = 0;\n";
-  for (int v = 0; v < V; ++v) {
+  // One vertex of the sweep.  mid_sig: expression of the middle-row mask word
+  // (the block sweep varies it per instance), or empty to read slo/shi.
+  auto emit_vertex = [&](int v, const char *ind, const char *mid_sig) {
     const auto &fan = D.fan[v];
     const auto &lk = D.link[v];
     const int m = (int)fan.size();
-    o << "  // vertex " << v << " (" << D.x[v] << "," << D.y[v] << ")\n";
+    o << ind << "// vertex " << v << " (" << D.x[v] << "," << D.y[v] << ")\n";
     const int pushes = (m >= 2 ? m - 1 : 0) + (int)anti_at[v].size();
-    if (pushes) o << "  if (np > TC_PCAP - " << pushes << "u) { tc_unions(S, np); np = 0; }\n";
-    o << "  const u32 s" << v << " = TC_BIT(" << D.k[v] << ") ^ " << D.c[v] << "u;\n";
-    o << "  u32 L" << v << ";\n";
+    if (pushes) o << ind << "if (np > TC_PCAP - " << pushes << "u) { tc_unions(S, np); np = 0; }\n";
+    if (mid_sig && D.y[v] == 0)
+      o << ind << "const u32 s" << v << " = ((" << mid_sig << " >> " << D.k[v] << ") & 1u) ^ " << D.c[v]
+        << "u;\n";
+    else
+      o << ind << "const u32 s" << v << " = TC_BIT(" << D.k[v] << ") ^ " << D.c[v] << "u;\n";
+    o << ind << "u32 L" << v << ";\n";
     if (m == 0) {
-      o << "  L" << v << " = nl; tc_newlab(S, nl, TC_NONE); ++nl;\n";
+      o << ind << "L" << v << " = nl; tc_newlab(S, nl, TC_NONE); ++nl;\n";
     } else {
-      o << "  {\n";
+      o << ind << "{\n";
       for (int i = 0; i < m; ++i)
-        o << "    const u32 e" << i << " = s" << fan[i] << " ^ s" << v << " ^ 1u;\n";
-      o << "    L" << v << " = ";
+        o << ind << "  const u32 e" << i << " = s" << fan[i] << " ^ s" << v << " ^ 1u;\n";
+      o << ind << "  L" << v << " = ";
       for (int i = 0; i < m; ++i) o << "e" << i << " ? L" << fan[i] << " : ";
-      o << "nl;\n    if (!(";
+      o << "nl;\n" << ind << "  if (!(";
       for (int i = 0; i < m; ++i) o << (i ? " | " : "") << "e" << i;
       o << ")) { tc_newlab(S, nl, L" << fan[0] << "); ++nl; }\n";
       // a same-sign entry that starts a new run after an earlier run: join
       if (m >= 2) {
-        o << "    u32 any = e0;\n";
+        o << ind << "  u32 any = e0;\n";
         for (int i = 1; i < m; ++i) {
-          o << "    { const u32 st = e" << i;
+          o << ind << "  { const u32 st = e" << i;
           if (lk[i]) o << " & (e" << i - 1 << " ^ 1u)";
           o << "; S.word(TC_OFF_PEND, np) = L" << v << " | (L" << fan[i]
             << " << 16); np += st & any; any |= st; }\n";
         }
       }
-      o << "  }\n";
+      o << ind << "}\n";
     }
     for (int i : anti_at[v])
-      o << "  S.word(TC_OFF_PEND, np) = L" << D.anti[i].first << " | (L" << v
+      o << ind << "S.word(TC_OFF_PEND, np) = L" << D.anti[i].first << " | (L" << v
         << " << 16) | 0x80000000u; ++np;\n";
     for (int i : bedge_at[v]) {
       const int a = D.bedge[i].first, b = D.bedge[i].second;
-      o << "  if (s" << a << " ^ s" << b << ") { tc_bpair(S, nb, L" << a << ", L" << b
+      o << ind << "if (s" << a << " ^ s" << b << ") { tc_bpair(S, nb, L" << a << ", L" << b
         << "); ++nb; }\n";
     }
-  }
-  o << "  tc_unions(S, np);\n";
-  o << "  return tc_backend(S, nl, nb, err);\n}\n";
+  };
+  const int Vo = V - (2 * d + 1);  // the middle row comes last in the sweep
+
+  // ---- the whole sweep for one mask ----
+  o << "__device__ __forceinline__ u64 tc_classify(u64 sig, const TcScratch &S, u32 &err) {\n"
+    << "  const u32 slo = (u32)sig, shi = (u32)(sig >> 32);\n  u32 nl = 0, nb = 0, np = 0;\n"
+    << "  tc_clear_odd(S);\n";
+  for (int v = 0; v < V; ++v) emit_vertex(v, "  ", nullptr);
+  o << "  tc_unions(S, np);\n  return tc_backend(S, nl, nb, err);\n}\n\n";
+  o << "__device__ __noinline__ u64 tc_classify_slow(u64 sig, const TcScratch &S, u32 &err) {\n"
+    << "  return tc_classify(sig, S, err);\n}\n\n";
+
+  // ---- block sweep: halves once, middle row per instance ----
+  o << "__device__ __forceinline__ void tc_sweep_amortised(u64 sig_hi, const TcScratch &S, u32 &err,\n"
+    << "    u64 *hkeys, unsigned long long *hcnt, u64 *gkeys, unsigned long long *gcnt, u64 gslots,\n"
+    << "    u32 *gerr, unsigned long long &failed) {\n"
+    << "  const u32 lane = threadIdx.x & 31u;\n"
+    << "  const u32 slo = (u32)sig_hi, shi = (u32)(sig_hi >> 32);\n  u32 nl = 0, nb = 0, np = 0;\n"
+    << "  tc_clear_odd(S);\n";
+  for (int v = 0; v < Vo; ++v) emit_vertex(v, "  ", nullptr);
+  o << "  tc_unions(S, np);\n  np = 0;\n  const u32 nl_o = nl, nb_o = nb;\n"
+    << "  if (nl_o > 32u) {  // snapshot too small (never seen in practice): no reuse\n"
+    << "    for (u32 j = 0; j < (1u << TC_B) / 32u; ++j) {\n"
+    << "      const u64 key = tc_classify_slow(sig_hi | (u64)(lane + 32u * j), S, err);\n"
+    << "      failed += key == 0;\n"
+    << "      tc_hist_add(key, hkeys, hcnt, gkeys, gcnt, gslots, gerr);\n    }\n    return;\n  }\n";
+  for (int w = 0; w < L.snapw; ++w)
+    o << "  const u32 snap" << w << " = S.word(TC_OFF_LPAR, " << w << ");\n";
+  o << "  const u32 osnap = S.word(TC_OFF_ODD, 0);\n";
+  o << "  for (u32 j = 0; j < (1u << TC_B) / 32u; ++j) {\n";
+  for (int w = 0; w < L.snapw; ++w) o << "    S.word(TC_OFF_LPAR, " << w << ") = snap" << w << ";\n";
+  o << "    S.word(TC_OFF_ODD, 0) = osnap;\n"
+    << "    for (u32 w = 1; w < TC_WODD; ++w) S.word(TC_OFF_ODD, w) = 0;\n"
+    << "    nl = nl_o; nb = nb_o; np = 0;\n"
+    << "    const u32 sm = slo | (lane + 32u * j);\n";
+  for (int v = Vo; v < V; ++v) emit_vertex(v, "    ", "sm");
+  o << "    tc_unions(S, np);\n"
+    << "    const u64 key = tc_backend(S, nl, nb, err);\n"
+    << "    failed += key == 0;\n"
+    << "    tc_hist_add(key, hkeys, hcnt, gkeys, gcnt, gslots, gerr);\n  }\n}\n";
+
   o << dev.substr(m);
   return o.str();
 }
@@ -309,7 +358,8 @@ cudaError_t jit_prepare(ts_tri *t) {
   mod->L = layout_for(t->dia);
   if (dr.load(&mod->mod, cubin.data()) != CUDA_SUCCESS) return cudaErrorInvalidKernelImage;
   if (dr.get(&mod->real, mod->mod, "tc_real_schemes") != CUDA_SUCCESS ||
-      dr.get(&mod->enumerate, mod->mod, "tc_enumerate") != CUDA_SUCCESS)
+      dr.get(&mod->enumerate, mod->mod, "tc_enumerate") != CUDA_SUCCESS ||
+      dr.get(&mod->blocks, mod->mod, "tc_enumerate_blocks") != CUDA_SUCCESS)
     return cudaErrorSymbolNotFound;
   const Layout &L = mod->L;
   mod->smem_real = (size_t)L.words * 4 * L.threads;
@@ -317,11 +367,14 @@ cudaError_t jit_prepare(ts_tri *t) {
   if (dr.set_attr(mod->real, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)mod->smem_real) !=
           CUDA_SUCCESS ||
       dr.set_attr(mod->enumerate, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES,
+                  (int)mod->smem_enum) != CUDA_SUCCESS ||
+      dr.set_attr(mod->blocks, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES,
                   (int)mod->smem_enum) != CUDA_SUCCESS)
     return cudaErrorInvalidConfiguration;
   if (dr.occupancy(&mod->bpsm_real, mod->real, L.threads, mod->smem_real) != CUDA_SUCCESS ||
       dr.occupancy(&mod->bpsm_enum, mod->enumerate, L.threads, mod->smem_enum) != CUDA_SUCCESS ||
-      mod->bpsm_real < 1 || mod->bpsm_enum < 1)
+      dr.occupancy(&mod->bpsm_blocks, mod->blocks, L.threads, mod->smem_enum) != CUDA_SUCCESS ||
+      mod->bpsm_real < 1 || mod->bpsm_enum < 1 || mod->bpsm_blocks < 1)
     return cudaErrorInvalidConfiguration;
   t->jit = mod;
   return cudaSuccess;
@@ -347,25 +400,63 @@ cudaError_t launch_real_schemes_jit(ts_tri *t, const uint64_t *signs, uint64_t n
   return cudaSuccess;
 }
 
-cudaError_t launch_enumerate_jit(ts_tri *t, uint64_t lo, uint64_t hi, uint32_t flags, ts_hist *h,
-                                 cudaStream_t st) {
-  cudaError_t e = jit_prepare(t);
-  if (e != cudaSuccess) return e;
-  std::shared_ptr<JitModule> m = t->jit;
+namespace {
+
+// One launch of the per-mask sweep kernel over masks m(k), k in [lo, hi).
+cudaError_t enumerate_range(JitModule &m, ts_hist *h, uint64_t lo, uint64_t hi, uint32_t flags,
+                            cudaStream_t st) {
   const uint64_t total = hi - lo;
-  const uint64_t chunk = (uint64_t)m->L.threads * 16;
+  const uint64_t chunk = (uint64_t)m.L.threads * 16;
   const uint64_t want = (total + chunk - 1) / chunk;
-  const uint64_t cap = (uint64_t)m->bpsm_enum * sm_count_now();
+  const uint64_t cap = (uint64_t)m.bpsm_enum * sm_count_now();
   const unsigned grid = (unsigned)std::min(want, cap);
-  e = cudaMemsetAsync(h->d_work, 0, sizeof(unsigned long long), st);
+  cudaError_t e = cudaMemsetAsync(h->d_work, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
   uint64_t slots = h->slots;
   void *args[] = {(void *)&lo,       (void *)&total,       (void *)&flags,
                   (void *)&h->d_keys, (void *)&h->d_counts, (void *)&slots,
                   (void *)&h->d_err,  (void *)&h->d_failed, (void *)&h->d_work};
-  if (driver().launch(m->enumerate, grid, 1, 1, m->L.threads, 1, 1, (unsigned)m->smem_enum,
+  if (driver().launch(m.enumerate, grid, 1, 1, m.L.threads, 1, 1, (unsigned)m.smem_enum,
                       (CUstream)st, args, nullptr) != CUDA_SUCCESS)
     return cudaErrorLaunchFailure;
+  return cudaSuccess;
+}
+
+// One launch of the block sweep over masks [hi0 << B, (hi0 + n_hi) << B).
+cudaError_t enumerate_blocks(JitModule &m, ts_hist *h, uint64_t hi0, uint64_t n_hi, cudaStream_t st) {
+  const uint64_t warps = m.L.threads / 32;
+  const uint64_t want = (n_hi + warps - 1) / warps;
+  const uint64_t cap = (uint64_t)m.bpsm_blocks * sm_count_now();
+  const unsigned grid = (unsigned)std::min(want, cap);
+  cudaError_t e = cudaMemsetAsync(h->d_work, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  uint64_t slots = h->slots;
+  void *args[] = {(void *)&hi0,       (void *)&n_hi,       (void *)&h->d_keys,
+                  (void *)&h->d_counts, (void *)&slots,    (void *)&h->d_err,
+                  (void *)&h->d_failed, (void *)&h->d_work};
+  if (driver().launch(m.blocks, grid, 1, 1, m.L.threads, 1, 1, (unsigned)m.smem_enum, (CUstream)st,
+                      args, nullptr) != CUDA_SUCCESS)
+    return cudaErrorLaunchFailure;
+  return cudaSuccess;
+}
+
+}  // namespace
+
+// Plain sweeps (no flag) of degree >= 4 run whole middle-row blocks through
+// the block sweep, and the ragged head and tail of the range through the
+// per-mask kernel; flagged sweeps use the per-mask kernel throughout.
+cudaError_t launch_enumerate_jit(ts_tri *t, uint64_t lo, uint64_t hi, uint32_t flags, ts_hist *h,
+                                 cudaStream_t st) {
+  cudaError_t e = jit_prepare(t);
+  if (e != cudaSuccess) return e;
+  std::shared_ptr<JitModule> m = t->jit;
+  const int B = t->d + 1;
+  if (flags != 0 || t->d < 4) return enumerate_range(*m, h, lo, hi, flags, st);
+  const uint64_t a = ((lo + (1ull << B) - 1) >> B) << B, b = (hi >> B) << B;
+  if (a >= b) return enumerate_range(*m, h, lo, hi, 0, st);
+  if (lo < a && (e = enumerate_range(*m, h, lo, a, 0, st)) != cudaSuccess) return e;
+  if ((e = enumerate_blocks(*m, h, a >> B, (b - a) >> B, st)) != cudaSuccess) return e;
+  if (b < hi && (e = enumerate_range(*m, h, b, hi, 0, st)) != cudaSuccess) return e;
   return cudaSuccess;
 }
 

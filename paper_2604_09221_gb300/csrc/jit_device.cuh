@@ -8,7 +8,9 @@
 //   TC_HASH_SLOTS, TC_LABEL_BYTES (1 or 2), TC_CODE64 (0/1), TC_PCAP
 //   (pending-union slots), TC_OFF_LPAR, TC_OFF_CAND, TC_OFF_BPAIR,
 //   TC_OFF_PEND, TC_OFF_ADJ, TC_OFF_CODE, TC_OFF_CLEN, TC_OFF_ORDER,
-//   TC_OFF_TPAR, TC_WORDS (per-thread scratch, in 32-bit words), TC_NPOINTS.
+//   TC_OFF_TPAR, TC_OFF_ODD, TC_WODD, TC_WORDS (per-thread scratch, in
+//   32-bit words), TC_NPOINTS, TC_B (middle-row bits: the lattice points
+//   (i, 0), i <= d, are bits 0..d of a mask).
 //
 // Labels.  The sweep gives a vertex the label of its first same-sign earlier
 // neighbour, or a fresh label when it has none; the fresh label remembers the
@@ -80,23 +82,35 @@ __device__ __forceinline__ u32 tc_find(const TcScratch &S, u32 x, u32 &par) {
   return x;
 }
 
+// Odd-cycle flags of the label sets (valid at set roots), one bit per label.
+__device__ __forceinline__ u32 tc_odd(const TcScratch &S, u32 l) {
+  return (S.word(TC_OFF_ODD, l >> 5) >> (l & 31u)) & 1u;
+}
+__device__ __forceinline__ void tc_set_odd(const TcScratch &S, u32 l) {
+  S.word(TC_OFF_ODD, l >> 5) |= 1u << (l & 31u);
+}
+
 // Join labels a and b with relative orientation parity p.
 __device__ __forceinline__ void tc_unite(const TcScratch &S, u32 a, u32 b, u32 p) {
   u32 pa, pb;
   const u32 ra = tc_find(S, a, pa), rb = tc_find(S, b, pb);
   const u32 q = (pa ^ pb ^ p) & 1u;
   if (ra == rb) {
-    if (q) S.set_cand(ra, S.cand(ra) | TC_TOP);  // odd cycle
+    if (q) tc_set_odd(S, ra);  // odd cycle
     return;
   }
   const u32 lo = ra < rb ? ra : rb, hi = ra < rb ? rb : ra;
-  const u32 odd = S.cand(hi) & TC_TOP;
   S.set_lpar(hi, lo | (q ? TC_TOP : 0u));
-  if (odd) S.set_cand(lo, S.cand(lo) | TC_TOP);
+  if (tc_odd(S, hi)) tc_set_odd(S, lo);
 }
 
 __device__ __forceinline__ void tc_bpair(const TcScratch &S, u32 i, u32 la, u32 lb) {
   S.word(TC_OFF_BPAIR, i) = la | (lb << 16);
+}
+
+__device__ __forceinline__ void tc_clear_odd(const TcScratch &S) {
+#pragma unroll
+  for (u32 w = 0; w < TC_WODD; ++w) S.word(TC_OFF_ODD, w) = 0;
 }
 
 // Pending joins: a | b << 16 | parity << 31.
@@ -135,7 +149,7 @@ __device__ __noinline__ u64 tc_backend(const TcScratch &S, u32 nl, u32 nb, u32 &
     const u32 p = S.lpar(l) & TC_LOW;
     if (p == l) {
       if (R >= TC_RMAX) { err |= TC_ERR_OVERFLOW; return 0; }
-      if (S.cand(l) & TC_TOP) odd |= 1ull << R;
+      if (tc_odd(S, l)) odd |= 1ull << R;
       S.set_lpar(l, R);
       ++R;
     } else {
@@ -234,27 +248,6 @@ __device__ __noinline__ u64 tc_backend(const TcScratch &S, u32 nl, u32 nb, u32 &
   return (1ull << nbits) | (nbits ? (u64)(bits >> (TC_CODE_BITS - nbits)) : 0ull);
 }
 
-#define TC_BIT(k) ((k) < 32 ? ((slo >> ((k) & 31)) & 1u) : ((shi >> ((k) & 31)) & 1u))
-
-__device__ __forceinline__ u64 tc_classify(u64 sig, const TcScratch &S, u32 &err);
-
-//@@SPLICE@@
-
-// ---------------------------------------------------------------- kernels
-
-__device__ __forceinline__ TcScratch tc_scratch(u32 *smem) { return TcScratch{smem + threadIdx.x}; }
-
-extern "C" __global__ void __launch_bounds__(TC_THREADS)
-    tc_real_schemes(const u64 *__restrict__ signs, u64 n, u64 *__restrict__ codes, u32 *err_word) {
-  extern __shared__ __align__(16) u32 tc_smem[];
-  const TcScratch S = tc_scratch(tc_smem);
-  const u64 valid = TC_NPOINTS >= 64 ? ~0ull : ((1ull << (TC_NPOINTS & 63)) - 1);
-  u32 err = 0;
-  for (u64 i = (u64)blockIdx.x * TC_THREADS + threadIdx.x; i < n; i += (u64)gridDim.x * TC_THREADS)
-    codes[i] = tc_classify(signs[i] & valid, S, err);
-  if (err) atomicOr(err_word, err);
-}
-
 __device__ __forceinline__ u32 tc_hash_slot(u64 key, u64 mask) {
   return (u32)(((key * 0x9E3779B97F4A7C15ull) >> 32) & mask);
 }
@@ -276,6 +269,53 @@ __device__ void tc_global_add(u64 *gkeys, unsigned long long *gcnt, u64 gslots, 
   atomicOr(gerr, TC_ERR_OVERFLOW);
 }
 
+// Warp-aggregated insert into the block's hash table (all 32 lanes call it).
+__device__ __forceinline__ void tc_hist_add(u64 key, u64 *hkeys, unsigned long long *hcnt, u64 *gkeys,
+                                            unsigned long long *gcnt, u64 gslots, u32 *gerr) {
+  const u32 lane = threadIdx.x & 31u;
+  const unsigned peers = __match_any_sync(0xffffffffu, key);
+  if (key != 0 && lane == (u32)(__ffs(peers) - 1)) {
+    const unsigned long long cnt = (unsigned long long)__popc(peers);
+    u32 s = tc_hash_slot(key, TC_HASH_SLOTS - 1);
+    for (u32 probe = 0; probe < TC_HASH_SLOTS; ++probe) {
+      unsigned long long *kp = reinterpret_cast<unsigned long long *>(hkeys + s);
+      unsigned long long k = *reinterpret_cast<volatile unsigned long long *>(kp);
+      if (k == 0) k = atomicCAS(kp, 0ull, (unsigned long long)key);
+      if (k == 0 || k == key) {
+        atomicAdd(hcnt + s, cnt);
+        return;
+      }
+      s = (s + 1) & (TC_HASH_SLOTS - 1);
+    }
+    tc_global_add(gkeys, gcnt, gslots, gerr, key, cnt);
+  }
+}
+
+#define TC_BIT(k) ((k) < 32 ? ((slo >> ((k) & 31)) & 1u) : ((shi >> ((k) & 31)) & 1u))
+
+__device__ __forceinline__ u64 tc_classify(u64 sig, const TcScratch &S, u32 &err);
+__device__ __forceinline__ void tc_sweep_amortised(u64 sig_hi, const TcScratch &S, u32 &err,
+                                                   u64 *hkeys, unsigned long long *hcnt,
+                                                   u64 *gkeys, unsigned long long *gcnt, u64 gslots,
+                                                   u32 *gerr, unsigned long long &failed);
+
+//@@SPLICE@@
+
+// ---------------------------------------------------------------- kernels
+
+__device__ __forceinline__ TcScratch tc_scratch(u32 *smem) { return TcScratch{smem + threadIdx.x}; }
+
+extern "C" __global__ void __launch_bounds__(TC_THREADS, 2)
+    tc_real_schemes(const u64 *__restrict__ signs, u64 n, u64 *__restrict__ codes, u32 *err_word) {
+  extern __shared__ __align__(16) u32 tc_smem[];
+  const TcScratch S = tc_scratch(tc_smem);
+  const u64 valid = TC_NPOINTS >= 64 ? ~0ull : ((1ull << (TC_NPOINTS & 63)) - 1);
+  u32 err = 0;
+  for (u64 i = (u64)blockIdx.x * TC_THREADS + threadIdx.x; i < n; i += (u64)gridDim.x * TC_THREADS)
+    codes[i] = tc_classify(signs[i] & valid, S, err);
+  if (err) atomicOr(err_word, err);
+}
+
 __device__ __forceinline__ u64 tc_enum_mask(u64 k, u32 flags) {
   if (flags & 1u) return k << 1;
   if (flags & 2u) return ((k & ((1ull << (TC_D - 1)) - 1)) << 2) | ((k >> (TC_D - 1)) << (TC_D + 2));
@@ -284,7 +324,7 @@ __device__ __forceinline__ u64 tc_enum_mask(u64 k, u32 flags) {
 
 #define TC_CHUNK (TC_THREADS * 16)
 
-extern "C" __global__ void __launch_bounds__(TC_THREADS)
+extern "C" __global__ void __launch_bounds__(TC_THREADS, 2)
     tc_enumerate(u64 lo, u64 total, u32 flags, u64 *gkeys, unsigned long long *gcnt, u64 gslots,
                  u32 *gerr, unsigned long long *gfailed, unsigned long long *work) {
   extern __shared__ __align__(16) u32 tc_smem[];
@@ -297,7 +337,6 @@ extern "C" __global__ void __launch_bounds__(TC_THREADS)
     hcnt[s] = 0;
   }
   __syncthreads();
-  const u32 lane = threadIdx.x & 31u;
   u32 err = 0;
   unsigned long long failed = 0;
   for (;;) {
@@ -313,24 +352,41 @@ extern "C" __global__ void __launch_bounds__(TC_THREADS)
         key = tc_classify(tc_enum_mask(lo + idx, flags), S, err);
         failed += key == 0;
       }
-      const unsigned peers = __match_any_sync(0xffffffffu, key);
-      if (key != 0 && lane == (u32)(__ffs(peers) - 1)) {
-        const unsigned long long cnt = (unsigned long long)__popc(peers);
-        u32 s = tc_hash_slot(key, TC_HASH_SLOTS - 1);
-        bool done = false;
-        for (u32 probe = 0; probe < TC_HASH_SLOTS && !done; ++probe) {
-          unsigned long long *kp = reinterpret_cast<unsigned long long *>(hkeys + s);
-          unsigned long long k = *reinterpret_cast<volatile unsigned long long *>(kp);
-          if (k == 0) k = atomicCAS(kp, 0ull, (unsigned long long)key);
-          if (k == 0 || k == key) {
-            atomicAdd(hcnt + s, cnt);
-            done = true;
-          }
-          s = (s + 1) & (TC_HASH_SLOTS - 1);
-        }
-        if (!done) tc_global_add(gkeys, gcnt, gslots, gerr, key, cnt);
-      }
+      tc_hist_add(key, hkeys, hcnt, gkeys, gcnt, gslots, gerr);
     }
+  }
+  __syncthreads();
+  for (u32 s = threadIdx.x; s < TC_HASH_SLOTS; s += TC_THREADS)
+    if (hkeys[s]) tc_global_add(gkeys, gcnt, gslots, gerr, hkeys[s], hcnt[s]);
+  if (err) atomicOr(gerr, err);
+  if (failed) atomicAdd(gfailed, failed);
+}
+
+// Exhaustive sweep of whole middle-row blocks: masks (h << TC_B) | b for
+// h in [hi0, hi0 + n_hi) and every b < 2^TC_B.  Each warp takes one h at a
+// time; the two half-diamonds depend on h only and are swept once, then every
+// lane classifies 2^TC_B / 32 middle-row patterns (tc_sweep_amortised).
+extern "C" __global__ void __launch_bounds__(TC_THREADS, 2)
+    tc_enumerate_blocks(u64 hi0, u64 n_hi, u64 *gkeys, unsigned long long *gcnt, u64 gslots,
+                        u32 *gerr, unsigned long long *gfailed, unsigned long long *work) {
+  extern __shared__ __align__(16) u32 tc_smem[];
+  u64 *hkeys = reinterpret_cast<u64 *>(tc_smem + TC_WORDS * TC_THREADS);
+  unsigned long long *hcnt = reinterpret_cast<unsigned long long *>(hkeys + TC_HASH_SLOTS);
+  const TcScratch S = tc_scratch(tc_smem);
+  for (u32 s = threadIdx.x; s < TC_HASH_SLOTS; s += TC_THREADS) {
+    hkeys[s] = 0;
+    hcnt[s] = 0;
+  }
+  __syncthreads();
+  const u32 lane = threadIdx.x & 31u;
+  u32 err = 0;
+  unsigned long long failed = 0;
+  for (;;) {
+    unsigned long long h = 0;
+    if (lane == 0) h = atomicAdd(work, 1ull);
+    h = __shfl_sync(0xffffffffu, h, 0);
+    if (h >= n_hi) break;
+    tc_sweep_amortised((hi0 + h) << TC_B, S, err, hkeys, hcnt, gkeys, gcnt, gslots, gerr, failed);
   }
   __syncthreads();
   for (u32 s = threadIdx.x; s < TC_HASH_SLOTS; s += TC_THREADS)
