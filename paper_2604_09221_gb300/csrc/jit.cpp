@@ -34,18 +34,18 @@ constexpr int kJitThreads = 256;
 struct Layout {
   int lbytes, epw, wlab, nb, rmax, code64, wcode, wsmall, pcap, wodd, snapw;
   int off_lpar, off_cand, off_bpair, off_pend, off_adj, off_code, off_clen, off_order, off_tpar,
-      off_odd, words;
+      off_rlab, off_odd, words;
   int threads, hash;
 };
 
 // Per-thread scratch (32-bit words, interleaved across the block):
 //   [lpar | cand]  one entry per label (at most one label per vertex)
 //   [bpair]        crossed boundary edges (odd d), root detection
-//   [pend]         pending joins; later the region adjacency words
+//   [pend]         pending joins; later the region children masks and the
+//                  per-region bytes (smallest label, parent, path, code length)
 //   [odd]          odd-cycle flag per label
-// The AHU codes and the BFS arrays reuse [lpar] once the region tree is
-// built (the block sweep restores lpar from registers for every instance and
-// keeps cand), or get their own words when they do not fit there.
+// The AHU codes reuse [lpar] once the region tree is built (the block sweep
+// restores lpar from registers for every instance and keeps cand).
 Layout layout_for(const Diamond &D) {
   Layout L{};
   const int d = D.d, V = D.V;
@@ -67,18 +67,15 @@ Layout layout_for(const Diamond &D) {
   L.off_bpair = 2 * L.wlab;
   L.off_pend = L.off_bpair + L.nb;
   L.off_adj = L.off_pend;
-  L.off_odd = L.off_pend + std::max(L.pcap, L.rmax);
-  int end = L.off_odd + L.wodd;
-  if (L.wcode + L.wsmall <= L.wlab) {
-    L.off_code = 0;
-  } else {
-    L.off_code = end;
-    end += L.wcode + L.wsmall;
-  }
-  L.off_clen = L.off_code + L.wcode;
-  L.off_order = L.off_clen + wb;
-  L.off_tpar = L.off_order + wb;
-  L.words = end;
+  const int region_words = L.rmax + 4 * wb;  // children masks + 4 byte arrays
+  L.off_rlab = L.off_adj + L.rmax;
+  L.off_tpar = L.off_rlab + wb;
+  L.off_order = L.off_tpar + wb;
+  L.off_clen = L.off_order + wb;
+  L.off_odd = L.off_pend + std::max(L.pcap, region_words);
+  L.off_code = 0;  // over lpar, dead once the region tree is built
+  if (L.wcode > L.wlab) return Layout{};  // never for d <= 9
+  L.words = L.off_odd + L.wodd;
   L.hash = d <= 7 ? 256 : 1024;
   // the largest block (multiple of 32, <= 256 threads) of which two fit per SM
   L.threads = kJitThreads;
@@ -190,6 +187,7 @@ std::string jit_source(const Diamond &D) {
     << "u\n#define TC_OFF_BPAIR " << L.off_bpair << "u\n#define TC_OFF_ADJ " << L.off_adj
     << "u\n#define TC_OFF_CODE " << L.off_code << "u\n#define TC_OFF_CLEN " << L.off_clen
     << "u\n#define TC_OFF_ORDER " << L.off_order << "u\n#define TC_OFF_TPAR " << L.off_tpar
+    << "u\n#define TC_OFF_RLAB " << L.off_rlab
     << "u\n#define TC_WORDS " << L.words << "u\n";
   const std::string dev(kDeviceSrc);
   const size_t m = dev.find("//@@SPLICE@@");

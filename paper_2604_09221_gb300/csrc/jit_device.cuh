@@ -8,7 +8,7 @@
 //   TC_HASH_SLOTS, TC_LABEL_BYTES (1 or 2), TC_CODE64 (0/1), TC_PCAP
 //   (pending-union slots), TC_OFF_LPAR, TC_OFF_CAND, TC_OFF_BPAIR,
 //   TC_OFF_PEND, TC_OFF_ADJ, TC_OFF_CODE, TC_OFF_CLEN, TC_OFF_ORDER,
-//   TC_OFF_TPAR, TC_OFF_ODD, TC_WODD, TC_WORDS (per-thread scratch, in
+//   TC_OFF_TPAR, TC_OFF_RLAB, TC_OFF_ODD, TC_WODD, TC_WORDS (per-thread scratch, in
 //   32-bit words), TC_NPOINTS, TC_B (middle-row bits: the lattice points
 //   (i, 0), i <= d, are bits 0..d of a mask).
 //
@@ -23,9 +23,9 @@
 // warp's lanes stay converged during the sweep.  An
 // inconsistent join marks the set as containing an odd antipodal cycle, i.e.
 // the non-orientable region (Alg. 1 lines 6-7).  The back end turns the sets
-// into regions, the cand edges into the region tree (they connect every
-// component, so their projection is the whole tree), finds the root, and
-// writes the AHU code (Alg. 1 line 11).
+// into regions and builds the region tree from the cand edges of the regions'
+// smallest labels (see tc_backend), finds the root, and writes the AHU code
+// (Alg. 1 line 11).
 //
 // Scratch words are interleaved across the block's threads (word i of thread
 // t at [i * TC_THREADS + t]) so every per-thread access pattern is free of
@@ -140,21 +140,67 @@ __device__ __forceinline__ void tc_set_code(const TcScratch &S, u32 r, code_t v)
 }
 #endif
 
+// Concatenated codes of the regions in `kids`: the non-leaves in descending
+// order of their codes (left-aligned bit strings), then '10' once per leaf
+// (the smallest code, so leaves always come last).
+__device__ __forceinline__ code_t tc_concat(const TcScratch &S, u32 kids, u32 leaves, u32 &len) {
+  const code_t rep10 = (code_t)(0xAAAAAAAAAAAAAAAAull >> (64u - TC_CODE_BITS));
+  u32 big = kids & ~leaves;
+  const u32 nleaf = __popc(kids & leaves);
+  code_t v = 0;
+  len = 0;
+  while (big) {
+    u32 best = __ffs(big) - 1;
+    code_t bv = tc_code(S, best);
+    for (u32 rest = big & (big - 1); rest; rest &= rest - 1) {
+      const u32 y = __ffs(rest) - 1;
+      const code_t cy = tc_code(S, y);
+      if (cy > bv) { bv = cy; best = y; }
+    }
+    v |= len < TC_CODE_BITS ? (bv >> len) : (code_t)0;
+    len += *S.byte(TC_OFF_CLEN, best);
+    big &= ~(1u << best);
+  }
+  if (nleaf) {
+    const code_t pat = rep10 & ~(((code_t)~(code_t)0) >> (2 * nleaf));
+    v |= len < TC_CODE_BITS ? (pat >> len) : (code_t)0;
+    len += 2 * nleaf;
+  }
+  return v;
+}
+
+// enc(region) = '1' . children . '0', stored left-aligned with its length.
+__device__ __forceinline__ void tc_store_node(const TcScratch &S, u32 x, code_t v, u32 len) {
+  tc_set_code(S, x, ((code_t)1 << (TC_CODE_BITS - 1)) | (v >> 1));
+  *S.byte(TC_OFF_CLEN, x) = (u8)(len + 2);
+}
+
 // Regions, region tree, root and canonical code from the label sets.
+//
+// Regions are numbered in the order of their smallest label, which is the
+// root of their label set (joins always keep the smaller root).  The smallest
+// label of a region r > 0 was created at a vertex whose earlier neighbours all
+// have the other sign; its cand label lies in a region with a smaller
+// smallest label, i.e. a region p < r across a crossed edge.  These R - 1
+// edges join every region to region 0, so they span the region adjacency
+// graph; that graph is a tree (each oval separates RP^2), hence they are all
+// of it, already oriented towards region 0.  Re-rooting at the non-orientable
+// region (or the pseudoline's region) reverses the path between the two.
 __device__ __noinline__ u64 tc_backend(const TcScratch &S, u32 nl, u32 nb, u32 &err) {
-  // 1. sets -> region ids (stored over lpar); odd-cycle flags of the roots
+  // 1. region ids over lpar (label order), odd-cycle flags, smallest labels
   u32 R = 0;
   u64 odd = 0;
   for (u32 l = 0; l < nl; ++l) {
     const u32 p = S.lpar(l) & TC_LOW;
-    if (p == l) {
+    const u32 is_root = p == l;
+    const u32 rp = S.lpar(p);  // p < l holds its region id already
+    if (is_root) {
       if (R >= TC_RMAX) { err |= TC_ERR_OVERFLOW; return 0; }
-      if (tc_odd(S, l)) odd |= 1ull << R;
-      S.set_lpar(l, R);
-      ++R;
-    } else {
-      S.set_lpar(l, S.lpar(p));  // p < l already holds its region id
+      odd |= (u64)tc_odd(S, l) << R;
+      *S.byte(TC_OFF_RLAB, R) = (u8)l;
     }
+    S.set_lpar(l, is_root ? R : rp);
+    R += is_root;
   }
   // 2. root: odd antipodal cycle (even d) / both sides of the pseudoline (odd d)
   int root = -1;
@@ -171,74 +217,49 @@ __device__ __noinline__ u64 tc_backend(const TcScratch &S, u32 nl, u32 nb, u32 &
   }
   if (root < 0) { err |= TC_ERR_INTERNAL; return 0; }
 #endif
-  // 3. region tree from the cand edges (adj reuses the pending-join slots)
+  // 3. the tree hanging from region 0: parent(r) = region of cand(smallest label of r)
   for (u32 r = 0; r < R; ++r) S.word(TC_OFF_ADJ, r) = 0;
-  for (u32 l = 1; l < nl; ++l) {
-    const u32 c = S.cand(l) & TC_LOW;
-    if (c == TC_NONE) continue;
-    const u32 a = S.lpar(l), b = S.lpar(c);
-    if (a != b) {
-      S.word(TC_OFF_ADJ, a) |= 1u << b;
-      S.word(TC_OFF_ADJ, b) |= 1u << a;
-    }
+  u32 internal = 0;
+  for (u32 r = 1; r < R; ++r) {
+    const u32 c = S.cand(*S.byte(TC_OFF_RLAB, r)) & TC_LOW;
+    if (c == TC_NONE) { err |= TC_ERR_INTERNAL; return 0; }
+    const u32 p = S.lpar(c);
+    if (p >= r) { err |= TC_ERR_INTERNAL; return 0; }
+    *S.byte(TC_OFF_TPAR, r) = (u8)p;
+    S.word(TC_OFF_ADJ, p) |= 1u << r;
+    internal |= 1u << p;
   }
-  u32 deg2 = 0, leaves = 0;
-  for (u32 r = 0; r < R; ++r) {
-    const u32 k = __popc(S.word(TC_OFF_ADJ, r));
-    deg2 += k;
-    if (k == 1 && (int)r != root) leaves |= 1u << r;
-  }
-  if (deg2 != 2 * (R - 1)) { err |= TC_ERR_INTERNAL; return 0; }
-  // 4. BFS order from the root, then AHU codes from the leaves up.  A leaf's
-  //    code is '10', the smallest code, so leaves go last among siblings and
-  //    need neither storage nor sorting.
+  // 4. the path root -> region 0, reversed by re-rooting
+  u32 k = 0, path = 1u;
   *S.byte(TC_OFF_ORDER, 0) = (u8)root;
-  *S.byte(TC_OFF_TPAR, root) = 0xFFu;
-  u32 seen = 1u << root, n = 1;
-  for (u32 q = 0; q < n; ++q) {
-    const u32 x = *S.byte(TC_OFF_ORDER, q);
-    u32 kids = S.word(TC_OFF_ADJ, x) & ~seen;
-    seen |= kids;
-    while (kids) {
-      const u32 y = __ffs(kids) - 1;
-      kids &= kids - 1;
-      *S.byte(TC_OFF_ORDER, n++) = (u8)y;
-      *S.byte(TC_OFF_TPAR, y) = (u8)x;
-    }
+  for (u32 x = (u32)root; x != 0;) {
+    x = *S.byte(TC_OFF_TPAR, x);
+    *S.byte(TC_OFF_ORDER, ++k) = (u8)x;
+    path |= 1u << x;
   }
-  if (n != R) { err |= TC_ERR_INTERNAL; return 0; }
-  const code_t rep10 = (code_t)(0xAAAAAAAAAAAAAAAAull >> (64u - TC_CODE_BITS));
+  // 5. AHU: internal regions off the path (higher index = deeper first), then
+  //    the path from region 0 up to the root
+  const u32 all = R >= 32 ? ~0u : ((1u << R) - 1);
+  u32 leaves = all & ~internal & ~path;
+  for (u32 todo = internal & ~path; todo;) {
+    const u32 x = 31 - __clz(todo);
+    todo &= ~(1u << x);
+    u32 len;
+    const code_t v = tc_concat(S, S.word(TC_OFF_ADJ, x), leaves, len);
+    tc_store_node(S, x, v, len);
+  }
   code_t bits = 0;
   u32 nbits = 0;
-  for (int q = (int)n - 1; q >= 0; --q) {
-    const u32 x = *S.byte(TC_OFF_ORDER, q);
-    if (leaves & (1u << x)) continue;
-    const u32 px = *S.byte(TC_OFF_TPAR, x);
-    const u32 all = S.word(TC_OFF_ADJ, x) & ~(px == 0xFFu ? 0u : (1u << px));
-    u32 kids = all & ~leaves;
-    const u32 nleaf = __popc(all & leaves);
-    code_t v = 0;
-    u32 len = 0;
-    while (kids) {
-      u32 best = __ffs(kids) - 1;
-      code_t bv = tc_code(S, best);
-      for (u32 rest = kids & (kids - 1); rest; rest &= rest - 1) {
-        const u32 y = __ffs(rest) - 1;
-        const code_t cy = tc_code(S, y);
-        if (cy > bv) { bv = cy; best = y; }
-      }
-      v |= len < TC_CODE_BITS ? (bv >> len) : (code_t)0;
-      len += *S.byte(TC_OFF_CLEN, best);
-      kids &= ~(1u << best);
-    }
-    if (nleaf) {
-      const code_t pat = rep10 & ~(((code_t)~(code_t)0) >> (2 * nleaf));
-      v |= len < TC_CODE_BITS ? (pat >> len) : (code_t)0;
-      len += 2 * nleaf;
-    }
-    if (px != 0xFFu) {
-      tc_set_code(S, x, ((code_t)1 << (TC_CODE_BITS - 1)) | (v >> 1));
-      *S.byte(TC_OFF_CLEN, x) = (u8)(len + 2);
+  for (int i = (int)k; i >= 0; --i) {
+    const u32 x = *S.byte(TC_OFF_ORDER, i);
+    u32 kids = S.word(TC_OFF_ADJ, x);
+    if (i > 0) kids &= ~(1u << *S.byte(TC_OFF_ORDER, i - 1));
+    if (i < (int)k) kids |= 1u << *S.byte(TC_OFF_ORDER, i + 1);
+    if (i > 0 && !kids) { leaves |= 1u << x; continue; }
+    u32 len;
+    const code_t v = tc_concat(S, kids, leaves, len);
+    if (i > 0) {
+      tc_store_node(S, x, v, len);
     } else {
       bits = v;
       nbits = len;
