@@ -167,6 +167,32 @@ ts_status ts_enumerate(const ts_tri *tri, uint64_t lo, uint64_t hi, uint32_t fla
 ts_status ts_hist_read(ts_hist *hist, uint64_t *codes, uint64_t *counts, uint64_t cap,
                        uint64_t *n_out, uint64_t *n_failed, void *stream);
 
+/* Exhaustive sweep that allocates nothing (the paper has no counterpart; it
+ * is an engine facility).  For callers that cannot allocate device memory at
+ * the time they sweep -- code running while a stream is captured into a CUDA
+ * graph, services that reserve all device memory up front and forbid later
+ * allocations, threads that must not enter an allocator.  Same results as
+ * ts_enumerate followed by ts_hist_read, computed by the table-driven sweep
+ * kernel with its hash table, counters and error word in one static device
+ * array of 65 600 bytes that every GPU loading this library keeps until the
+ * process exits.  The caller passes the outputs:
+ *   codes, counts  device, cap uint64 each: the distinct codes (1 word each)
+ *                  and their counts, unsorted
+ *   cap            at most 2048 (the array's table holds 2048 codes);
+ *                  larger values return TS_EINVAL
+ *   n_out          device, 3 uint64: [0] distinct codes found (entries beyond
+ *                  cap are dropped), [1] failed instances, [2] error bits
+ *                  (nonzero: the table overflowed or an instance failed)
+ * Requires d <= 9 and tri loaded on the current device.  Asynchronous on
+ * stream.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture.  Every call reuses the same array and clears it first, so
+ * calls that overlap on the GPU (different streams, or host threads without
+ * ordering) race and corrupt each other's results: serialise them. */
+ts_status ts_enumerate_noalloc(const ts_tri *tri, uint64_t lo, uint64_t hi, uint32_t flags,
+                               uint64_t *codes, uint64_t *counts, uint64_t cap, uint64_t *n_out,
+                               void *stream);
+
 /* Rohlin-Viro notation of a code (Sec. 2): "<0>", "<J>", "<4>", "<1<1>>",
  * "<J + 1<1> + 2>" ('+' stands for the disjoint union); writes at most len
  * bytes including the terminating NUL. */

@@ -73,6 +73,7 @@ def _load():
                 "ts_specialized_log": ([P, ctypes.c_char_p, ctypes.c_size_t], I),
                 "ts_specialized_source": ([I, P, I, I, ctypes.c_char_p, ctypes.c_size_t,
                                            ctypes.POINTER(ctypes.c_size_t)], I),
+                "ts_enumerate_noalloc": ([P, U64, U64, ctypes.c_uint32, P, P, U64, P, P], I),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
