@@ -255,7 +255,9 @@ def main():
 
     # ---- merge of the per-rank histograms (the only exchange step) ----
     if pg:
-        merged = merge_histograms(pg, codes, counts)
+        from paper_2604_09221_gb300 import sweep
+        mine = {eng.code_to_int(c): int(k) for c, k in zip(codes, counts)}
+        merged = sweep.all_gather_histogram(pg, mine, tri.code_words, device="cuda")
         if rank == 0:
             assert sum(merged.values()) == ws * SLICE
 
@@ -308,26 +310,6 @@ def hist_read_bytes(hist):
     while slots < 2 * hist.capacity:
         slots <<= 1
     return int(slots * (8 * hist.code_words + 8) + 4 + 8)
-
-
-def merge_histograms(pg, codes, counts):
-    import torch
-    ws = pg.get_world_size()
-    n = torch.tensor([len(codes)], device="cuda")
-    sizes = [torch.zeros_like(n) for _ in range(ws)]
-    pg.all_gather(sizes, n)
-    m = int(max(s.item() for s in sizes))
-    buf = torch.zeros((m, 2), dtype=torch.int64, device="cuda")
-    buf[:len(codes), 0] = torch.from_numpy(codes[:, 0].view("int64"))
-    buf[:len(codes), 1] = torch.from_numpy(counts.view("int64"))
-    outs = [torch.zeros_like(buf) for _ in range(ws)]
-    pg.all_gather(outs, buf)
-    merged = {}
-    for o in outs:
-        for c, k in o.cpu().tolist():
-            if c:
-                merged[c] = merged.get(c, 0) + k
-    return merged
 
 
 def plain_kernel(eng, tri, ti, stream):

@@ -259,7 +259,8 @@ std::string jit_source(const Diamond &D) {
     << "  return tc_classify(sig, S, err);\n}\n\n";
 
   // ---- block sweep: halves once, middle row per instance ----
-  o << "__device__ __forceinline__ void tc_sweep_amortised(u64 sig_hi, const TcScratch &S, u32 &err,\n"
+  o << "__device__ __forceinline__ void tc_sweep_amortised(u64 sig_hi, u32 ishift, u32 ireps,\n"
+    << "    const TcScratch &S, u32 &err,\n"
     << "    u64 *hkeys, unsigned long long *hcnt, u64 *gkeys, unsigned long long *gcnt, u64 gslots,\n"
     << "    u32 *gerr, unsigned long long &failed) {\n"
     << "  const u32 lane = threadIdx.x & 31u;\n"
@@ -268,19 +269,19 @@ std::string jit_source(const Diamond &D) {
   for (int v = 0; v < Vo; ++v) emit_vertex(v, "  ", nullptr);
   o << "  tc_unions(S, np);\n  np = 0;\n  const u32 nl_o = nl, nb_o = nb;\n"
     << "  if (nl_o > 32u) {  // snapshot too small (never seen in practice): no reuse\n"
-    << "    for (u32 j = 0; j < (1u << TC_B) / 32u; ++j) {\n"
-    << "      const u64 key = tc_classify_slow(sig_hi | (u64)(lane + 32u * j), S, err);\n"
+    << "    for (u32 j = 0; j < ireps; ++j) {\n"
+    << "      const u64 key = tc_classify_slow(sig_hi | ((u64)(lane + 32u * j) << ishift), S, err);\n"
     << "      failed += key == 0;\n"
     << "      tc_hist_add(key, hkeys, hcnt, gkeys, gcnt, gslots, gerr);\n    }\n    return;\n  }\n";
   for (int w = 0; w < L.snapw; ++w)
     o << "  const u32 snap" << w << " = S.word(TC_OFF_LPAR, " << w << ");\n";
   o << "  const u32 osnap = S.word(TC_OFF_ODD, 0);\n";
-  o << "  for (u32 j = 0; j < (1u << TC_B) / 32u; ++j) {\n";
+  o << "  for (u32 j = 0; j < ireps; ++j) {\n";
   for (int w = 0; w < L.snapw; ++w) o << "    S.word(TC_OFF_LPAR, " << w << ") = snap" << w << ";\n";
   o << "    S.word(TC_OFF_ODD, 0) = osnap;\n"
     << "    for (u32 w = 1; w < TC_WODD; ++w) S.word(TC_OFF_ODD, w) = 0;\n"
     << "    nl = nl_o; nb = nb_o; np = 0;\n"
-    << "    const u32 sm = slo | (lane + 32u * j);\n";
+    << "    const u32 sm = slo | ((lane + 32u * j) << ishift);\n";
   for (int v = Vo; v < V; ++v) emit_vertex(v, "    ", "sm");
   o << "    tc_unions(S, np);\n"
     << "    const u64 key = tc_backend(S, nl, nb, err);\n"
@@ -420,8 +421,10 @@ cudaError_t enumerate_range(JitModule &m, ts_hist *h, uint64_t lo, uint64_t hi, 
   return cudaSuccess;
 }
 
-// One launch of the block sweep over masks [hi0 << B, (hi0 + n_hi) << B).
-cudaError_t enumerate_blocks(JitModule &m, ts_hist *h, uint64_t hi0, uint64_t n_hi, cudaStream_t st) {
+// One launch of the block sweep: masks (h << oshift) | (t << ishift) for
+// h in [hi0, hi0 + n_hi) and t < 32 * ireps (all middle-row patterns).
+cudaError_t enumerate_blocks(JitModule &m, ts_hist *h, uint64_t hi0, uint64_t n_hi, uint32_t oshift,
+                             uint32_t ishift, uint32_t ireps, cudaStream_t st) {
   const uint64_t warps = m.L.threads / 32;
   const uint64_t want = (n_hi + warps - 1) / warps;
   const uint64_t cap = (uint64_t)m.bpsm_blocks * sm_count_now();
@@ -429,9 +432,9 @@ cudaError_t enumerate_blocks(JitModule &m, ts_hist *h, uint64_t hi0, uint64_t n_
   cudaError_t e = cudaMemsetAsync(h->d_work, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
   uint64_t slots = h->slots;
-  void *args[] = {(void *)&hi0,       (void *)&n_hi,       (void *)&h->d_keys,
-                  (void *)&h->d_counts, (void *)&slots,    (void *)&h->d_err,
-                  (void *)&h->d_failed, (void *)&h->d_work};
+  void *args[] = {(void *)&hi0,      (void *)&n_hi,       (void *)&oshift,   (void *)&ishift,
+                  (void *)&ireps,    (void *)&h->d_keys,  (void *)&h->d_counts, (void *)&slots,
+                  (void *)&h->d_err, (void *)&h->d_failed, (void *)&h->d_work};
   if (driver().launch(m.blocks, grid, 1, 1, m.L.threads, 1, 1, (unsigned)m.smem_enum, (CUstream)st,
                       args, nullptr) != CUDA_SUCCESS)
     return cudaErrorLaunchFailure;
@@ -440,21 +443,29 @@ cudaError_t enumerate_blocks(JitModule &m, ts_hist *h, uint64_t hi0, uint64_t n_
 
 }  // namespace
 
-// Plain sweeps (no flag) of degree >= 4 run whole middle-row blocks through
-// the block sweep, and the ragged head and tail of the range through the
-// per-mask kernel; flagged sweeps use the per-mask kernel throughout.
+// Sweeps run whole middle-row blocks through the block sweep and the ragged
+// head and tail of the range through the per-mask kernel.  In terms of the
+// sweep index k, the mask m(k) is (h << oshift) | (t << ishift) with
+// t = k mod 2^ib the middle-row pattern (ib free middle-row bits) and
+// h = k >> ib: ib = d + 1 without flags, d with TS_ENUM_FLIP (bit 0 fixed),
+// d - 1 with TS_ENUM_REDUCED (bits 0, 1 and d + 1 fixed).
 cudaError_t launch_enumerate_jit(ts_tri *t, uint64_t lo, uint64_t hi, uint32_t flags, ts_hist *h,
                                  cudaStream_t st) {
   cudaError_t e = jit_prepare(t);
   if (e != cudaSuccess) return e;
   std::shared_ptr<JitModule> m = t->jit;
-  const int B = t->d + 1;
-  if (flags != 0 || t->d < 4) return enumerate_range(*m, h, lo, hi, flags, st);
-  const uint64_t a = ((lo + (1ull << B) - 1) >> B) << B, b = (hi >> B) << B;
-  if (a >= b) return enumerate_range(*m, h, lo, hi, 0, st);
-  if (lo < a && (e = enumerate_range(*m, h, lo, a, 0, st)) != cudaSuccess) return e;
-  if ((e = enumerate_blocks(*m, h, a >> B, (b - a) >> B, st)) != cudaSuccess) return e;
-  if (b < hi && (e = enumerate_range(*m, h, b, hi, 0, st)) != cudaSuccess) return e;
+  const int d = t->d;
+  uint32_t ib = d + 1, ishift = 0, oshift = d + 1;
+  if (flags & TS_ENUM_FLIP) { ib = d; ishift = 1; oshift = d + 1; }
+  if (flags & TS_ENUM_REDUCED) { ib = d - 1; ishift = 2; oshift = d + 2; }
+  if (ib < 5) return enumerate_range(*m, h, lo, hi, flags, st);  // fewer patterns than lanes
+  const uint64_t a = ((lo + (1ull << ib) - 1) >> ib) << ib, b = (hi >> ib) << ib;
+  if (a >= b) return enumerate_range(*m, h, lo, hi, flags, st);
+  if (lo < a && (e = enumerate_range(*m, h, lo, a, flags, st)) != cudaSuccess) return e;
+  if ((e = enumerate_blocks(*m, h, a >> ib, (b - a) >> ib, oshift, ishift, (1u << ib) / 32u, st)) !=
+      cudaSuccess)
+    return e;
+  if (b < hi && (e = enumerate_range(*m, h, b, hi, flags, st)) != cudaSuccess) return e;
   return cudaSuccess;
 }
 

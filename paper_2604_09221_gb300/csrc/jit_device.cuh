@@ -315,7 +315,8 @@ __device__ __forceinline__ void tc_hist_add(u64 key, u64 *hkeys, unsigned long l
 #define TC_BIT(k) ((k) < 32 ? ((slo >> ((k) & 31)) & 1u) : ((shi >> ((k) & 31)) & 1u))
 
 __device__ __forceinline__ u64 tc_classify(u64 sig, const TcScratch &S, u32 &err);
-__device__ __forceinline__ void tc_sweep_amortised(u64 sig_hi, const TcScratch &S, u32 &err,
+__device__ __forceinline__ void tc_sweep_amortised(u64 sig_hi, u32 ishift, u32 ireps,
+                                                   const TcScratch &S, u32 &err,
                                                    u64 *hkeys, unsigned long long *hcnt,
                                                    u64 *gkeys, unsigned long long *gcnt, u64 gslots,
                                                    u32 *gerr, unsigned long long &failed);
@@ -383,12 +384,14 @@ extern "C" __global__ void __launch_bounds__(TC_THREADS, 2)
   if (failed) atomicAdd(gfailed, failed);
 }
 
-// Exhaustive sweep of whole middle-row blocks: masks (h << TC_B) | b for
-// h in [hi0, hi0 + n_hi) and every b < 2^TC_B.  Each warp takes one h at a
-// time; the two half-diamonds depend on h only and are swept once, then every
-// lane classifies 2^TC_B / 32 middle-row patterns (tc_sweep_amortised).
+// Exhaustive sweep of whole middle-row blocks: masks (h << oshift) |
+// (t << ishift) for h in [hi0, hi0 + n_hi) and every t < 32 * ireps.  Each
+// warp takes one h at a time; the two half-diamonds depend on h only and are
+// swept once, then every lane classifies ireps middle-row patterns
+// (tc_sweep_amortised).
 extern "C" __global__ void __launch_bounds__(TC_THREADS, 2)
-    tc_enumerate_blocks(u64 hi0, u64 n_hi, u64 *gkeys, unsigned long long *gcnt, u64 gslots,
+    tc_enumerate_blocks(u64 hi0, u64 n_hi, u32 oshift, u32 ishift, u32 ireps, u64 *gkeys,
+                        unsigned long long *gcnt, u64 gslots,
                         u32 *gerr, unsigned long long *gfailed, unsigned long long *work) {
   extern __shared__ __align__(16) u32 tc_smem[];
   u64 *hkeys = reinterpret_cast<u64 *>(tc_smem + TC_WORDS * TC_THREADS);
@@ -407,7 +410,8 @@ extern "C" __global__ void __launch_bounds__(TC_THREADS, 2)
     if (lane == 0) h = atomicAdd(work, 1ull);
     h = __shfl_sync(0xffffffffu, h, 0);
     if (h >= n_hi) break;
-    tc_sweep_amortised((hi0 + h) << TC_B, S, err, hkeys, hcnt, gkeys, gcnt, gslots, gerr, failed);
+    tc_sweep_amortised((hi0 + h) << oshift, ishift, ireps, S, err, hkeys, hcnt, gkeys, gcnt, gslots,
+                       gerr, failed);
   }
   __syncthreads();
   for (u32 s = threadIdx.x; s < TC_HASH_SLOTS; s += TC_THREADS)
