@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libtcurve.so")
 SOURCES = ["host.cpp", "kernels.cu", "jit.cpp", "noalloc.cu"]
-HEADERS = ["engine.h", "jit_device.cuh", os.path.join("..", "..", "include", "tcurve.h")]
+HEADERS = ["engine.h", "tc_layout.h", "tc_runtime.cuh", "jit_kernels.cuh",
+           os.path.join("..", "..", "include", "tcurve.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -36,16 +37,17 @@ def _stale() -> bool:
     return any(os.path.getmtime(p) > t for p in deps)
 
 
-def embed_device_runtime() -> str:
-    """Write the device runtime of the specialised kernels (jit_device.cuh)
-    as a C++ raw string literal for jit.cpp to splice generated code into."""
-    src = open(os.path.join(CSRC, "jit_device.cuh")).read()
-    out = os.path.join(OUT_DIR, "_jit_device_src.inc")
-    text = 'R"TCJIT(' + src + ')TCJIT"\n'
-    if not os.path.exists(out) or open(out).read() != text:
-        with open(out, "w") as f:
-            f.write(text)
-    return out
+def embed_device_runtime() -> None:
+    """Write the device runtime (tc_runtime.cuh) and the kernels of the
+    specialised sources (jit_kernels.cuh) as C++ raw string literals, which
+    jit.cpp puts around the code it generates for a triangulation."""
+    for name in ("tc_runtime", "jit_kernels"):
+        src = open(os.path.join(CSRC, name + ".cuh")).read()
+        out = os.path.join(OUT_DIR, f"_{name}_src.inc")
+        text = 'R"TCJIT(' + src + ')TCJIT"\n'
+        if not os.path.exists(out) or open(out).read() != text:
+            with open(out, "w") as f:
+                f.write(text)
 
 
 def build(force: bool = False, verbose: bool = False) -> str:

@@ -23,12 +23,12 @@ constexpr int kMaxDegree = 9;  // single-word sign masks, 8-bit vertex ids
 //             bits 16-31 first fan entry
 //   fan[NF]   bits 0-7 neighbour u, bits 8-13 k(u), bit 14 c(u),
 //             bit 15 "u and the previous entry span a triangle with v"
-//   anti[2d]  bits 0-7 x, bits 8-15 -x (antipodal boundary vertices)
-//   bedge[2d] bits 0-7 a, 8-15 b, 16-21 k(a), 22 c(a), 23-28 k(b), 29 c(b):
-//             one boundary edge of each antipodal pair
+//   vext[V]   bits 0-7 the antipodal partner x < v of v (0xFF: none), bits
+//             8-15 and 16-23 the other end b < v of up to two boundary edges
+//             kept for root detection (0xFF: none)
 struct TableLayout {
-  uint32_t V, NF, n_anti, n_bedge;
-  uint32_t off_vdesc, off_fan, off_anti, off_bedge;
+  uint32_t V, NF;
+  uint32_t off_vdesc, off_fan, off_vext;
   uint32_t words;  // padded to a multiple of 4 (16-byte TMA granule)
 };
 

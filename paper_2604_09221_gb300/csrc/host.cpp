@@ -173,12 +173,12 @@ bool build_diamond(int d, const std::vector<std::array<Pt, 3>> &tris, Diamond &D
   return (int)D.anti.size() == 2 * d && (int)D.bedge.size() == 2 * d;
 }
 
-// Pack the diamond into the tables the generic kernels stage into shared
-// memory (layout in engine.h).
+// Pack the diamond into the tables the table-driven kernels stage into
+// shared memory (layout in engine.h).
 bool pack_tables(const Diamond &D, ts_tri *t) {
   const int V = D.V;
   if (V > 255) return false;
-  std::vector<uint32_t> vdesc(V), fan, anti, bedge;
+  std::vector<uint32_t> vdesc(V), fan, vext(V, 0xFFFFFFu);
   for (int v = 0; v < V; ++v) {
     if (D.fan[v].size() > 63 || fan.size() > 65535) return false;
     vdesc[v] = (uint32_t)D.k[v] | ((uint32_t)D.c[v] << 6) | ((uint32_t)D.fan[v].size() << 7) |
@@ -189,27 +189,27 @@ bool pack_tables(const Diamond &D, ts_tri *t) {
                     ((uint32_t)D.link[v][n] << 15));
     }
   }
-  for (auto &p : D.anti) anti.push_back((uint32_t)p.first | ((uint32_t)p.second << 8));
-  for (auto &e : D.bedge) {
-    int a = e.first, b = e.second;
-    bedge.push_back((uint32_t)a | ((uint32_t)b << 8) | ((uint32_t)D.k[a] << 16) |
-                    ((uint32_t)D.c[a] << 22) | ((uint32_t)D.k[b] << 23) | ((uint32_t)D.c[b] << 29));
+  for (auto &p : D.anti) vext[p.second] = (vext[p.second] & ~0xFFu) | (uint32_t)p.first;
+  if (D.d % 2) {
+    for (auto &e : D.bedge) {
+      const int late = std::max(e.first, e.second), early = std::min(e.first, e.second);
+      uint32_t &w = vext[late];
+      if (((w >> 8) & 0xFFu) == 0xFFu) w = (w & ~0xFF00u) | ((uint32_t)early << 8);
+      else if (((w >> 16) & 0xFFu) == 0xFFu) w = (w & ~0xFF0000u) | ((uint32_t)early << 16);
+      else return false;
+    }
   }
   TableLayout L{};
   L.V = V;
   L.NF = (uint32_t)fan.size();
-  L.n_anti = (uint32_t)anti.size();
-  L.n_bedge = (uint32_t)bedge.size();
   L.off_vdesc = 0;
   L.off_fan = L.off_vdesc + V;
-  L.off_anti = L.off_fan + L.NF;
-  L.off_bedge = L.off_anti + L.n_anti;
-  L.words = (L.off_bedge + L.n_bedge + 3) & ~3u;
+  L.off_vext = L.off_fan + L.NF;
+  L.words = (L.off_vext + V + 3) & ~3u;
   std::vector<uint32_t> buf(L.words, 0);
   std::copy(vdesc.begin(), vdesc.end(), buf.begin() + L.off_vdesc);
   std::copy(fan.begin(), fan.end(), buf.begin() + L.off_fan);
-  std::copy(anti.begin(), anti.end(), buf.begin() + L.off_anti);
-  std::copy(bedge.begin(), bedge.end(), buf.begin() + L.off_bedge);
+  std::copy(vext.begin(), vext.end(), buf.begin() + L.off_vext);
   t->lay = L;
   t->host_tables = std::move(buf);
   t->V = V;

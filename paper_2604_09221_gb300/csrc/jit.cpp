@@ -5,11 +5,12 @@
 // order becomes a few integer instructions whose operands (lattice bit
 // positions, Eq. 2 parity constants, fan neighbours, link bits, antipodal
 // partners) are immediates, and the provisional component label of each
-// vertex is a register.  The generated function is spliced into the device
-// runtime of jit_device.cuh (label union-find, region tree, AHU code, hash
-// histogram, kernels), compiled with NVRTC for sm_103a and loaded with the
-// driver API (entry points obtained from the runtime, so the library does not
-// link libcuda or libnvrtc; NVRTC is opened on first use).
+// vertex is a register.  The generated functions sit between the device
+// runtime (tc_runtime.cuh: label union-find, region tree, AHU code, hash
+// histogram) and the kernels (jit_kernels.cuh); the source is compiled with
+// NVRTC for sm_103a and loaded with the driver API (entry points obtained
+// from the runtime, so the library does not link libcuda or libnvrtc; NVRTC
+// is opened on first use).
 #include <cuda.h>
 #include <dlfcn.h>
 #include <nvrtc.h>
@@ -20,70 +21,24 @@
 #include <sstream>
 
 #include "engine.h"
+#include "tc_layout.h"
 
 namespace tcurve {
 
 namespace {
 
-const char kDeviceSrc[] =
-#include "_jit_device_src.inc"
+const char kRuntimeSrc[] =
+#include "_tc_runtime_src.inc"
+    ;
+const char kKernelsSrc[] =
+#include "_jit_kernels_src.inc"
     ;
 
 constexpr int kJitThreads = 256;
 
-struct Layout {
-  int lbytes, epw, wlab, nb, rmax, code64, wcode, wsmall, pcap, wodd, snapw;
-  int off_lpar, off_cand, off_bpair, off_pend, off_adj, off_code, off_clen, off_order, off_tpar,
-      off_rlab, off_odd, words;
-  int threads, hash;
-};
+typedef TcLayout Layout;
 
-// Per-thread scratch (32-bit words, interleaved across the block):
-//   [lpar | cand]  one entry per label (at most one label per vertex)
-//   [bpair]        crossed boundary edges (odd d), root detection
-//   [pend]         pending joins; later the region children masks and the
-//                  per-region bytes (smallest label, parent, path, code length)
-//   [odd]          odd-cycle flag per label
-// The AHU codes reuse [lpar] once the region tree is built (the block sweep
-// restores lpar from registers for every instance and keeps cand).
-Layout layout_for(const Diamond &D) {
-  Layout L{};
-  const int d = D.d, V = D.V;
-  const int M = (d - 1) * (d - 2) / 2 + 1, nmax = (d % 2 == 0) ? M : M - 1;
-  L.lbytes = V <= 126 ? 1 : 2;  // label ids and the "none" value fit 7 / 15 bits
-  L.epw = 4 / L.lbytes;
-  L.wlab = (V + L.epw - 1) / L.epw;
-  L.nb = (d % 2) ? 2 * d : 0;
-  L.rmax = nmax + 1;
-  L.code64 = 2 * nmax > 30 ? 1 : 0;
-  L.wcode = L.rmax * (L.code64 ? 2 : 1);
-  const int wb = (L.rmax + 3) / 4;
-  L.wsmall = 3 * wb;
-  L.pcap = 2 * d + 24;
-  L.wodd = (V + 31) / 32;
-  L.snapw = (32 + L.epw - 1) / L.epw;  // the block sweep snapshots 32 labels
-  L.off_lpar = 0;
-  L.off_cand = L.wlab;
-  L.off_bpair = 2 * L.wlab;
-  L.off_pend = L.off_bpair + L.nb;
-  L.off_adj = L.off_pend;
-  const int region_words = L.rmax + 4 * wb;  // children masks + 4 byte arrays
-  L.off_rlab = L.off_adj + L.rmax;
-  L.off_tpar = L.off_rlab + wb;
-  L.off_order = L.off_tpar + wb;
-  L.off_clen = L.off_order + wb;
-  L.off_odd = L.off_pend + std::max(L.pcap, region_words);
-  L.off_code = 0;  // over lpar, dead once the region tree is built
-  if (L.wcode > L.wlab) return Layout{};  // never for d <= 9
-  L.words = L.off_odd + L.wodd;
-  L.hash = d <= 7 ? 256 : 1024;
-  // the largest block (multiple of 32, <= 256 threads) of which two fit per SM
-  L.threads = kJitThreads;
-  while (L.threads > 32 &&
-         2 * ((size_t)L.words * 4 * L.threads + L.hash * 16 + 16) > 224 * 1024)
-    L.threads -= 32;
-  return L;
-}
+Layout layout_for(const Diamond &D) { return tc_layout(D.d, false, kJitThreads); }
 
 // ---- NVRTC, opened on first use ----
 struct Nvrtc {
@@ -176,23 +131,19 @@ std::string jit_source(const Diamond &D) {
   std::ostringstream o;
   o << "// T-curve real-scheme kernels specialised to one triangulation of " << d
     << "*Delta_2 (generated)\n";
-  o << "#define TC_D " << d << "\n#define TC_V " << V << "\n#define TC_NPOINTS "
-    << (d + 1) * (d + 2) / 2 << "\n#define TC_RMAX " << L.rmax << "\n#define TC_NB " << L.nb
-    << "\n#define TC_THREADS " << L.threads << "\n#define TC_HASH_SLOTS " << L.hash
-    << "\n#define TC_LABEL_BYTES " << L.lbytes << "\n#define TC_CODE64 " << L.code64
-    << "\n#define TC_PCAP " << L.pcap << "u\n#define TC_OFF_PEND " << L.off_pend << "u"
-    << "\n#define TC_OFF_ODD " << L.off_odd << "u\n#define TC_WODD " << L.wodd << "u"
-    << "\n#define TC_B " << d + 1 << "u\n#define TC_SNAPW " << L.snapw << "u"
-    << "\n#define TC_OFF_LPAR " << L.off_lpar << "u\n#define TC_OFF_CAND " << L.off_cand
-    << "u\n#define TC_OFF_BPAIR " << L.off_bpair << "u\n#define TC_OFF_ADJ " << L.off_adj
-    << "u\n#define TC_OFF_CODE " << L.off_code << "u\n#define TC_OFF_CLEN " << L.off_clen
-    << "u\n#define TC_OFF_ORDER " << L.off_order << "u\n#define TC_OFF_TPAR " << L.off_tpar
-    << "u\n#define TC_OFF_RLAB " << L.off_rlab
-    << "u\n#define TC_WORDS " << L.words << "u\n";
-  const std::string dev(kDeviceSrc);
-  const size_t m = dev.find("//@@SPLICE@@");
-  o << dev.substr(0, m);
-
+  o << "struct TcK {\n";
+  auto c = [&](const char *n, long v) { o << "  static constexpr unsigned " << n << " = " << v << "u;\n"; };
+  c("D", d); c("V", V); c("NPOINTS", (d + 1) * (d + 2) / 2); c("RMAX", L.rmax); c("NB", L.nb);
+  c("THREADS", L.threads); c("HASH", L.hash); c("LBYTES", L.lbytes); c("CODE64", L.code64);
+  c("PCAP", L.pcap); c("WODD", L.wodd); c("WORDS", L.words); c("B", d + 1); c("SNAPW", L.snapw);
+  c("OFF_LPAR", L.off_lpar); c("OFF_CAND", L.off_cand); c("OFF_LAB", L.off_lab);
+  c("OFF_BPAIR", L.off_bpair); c("OFF_PEND", L.off_pend); c("OFF_ADJ", L.off_adj);
+  c("OFF_RLAB", L.off_rlab); c("OFF_TPAR", L.off_tpar); c("OFF_ORDER", L.off_order);
+  c("OFF_CLEN", L.off_clen); c("OFF_ODD", L.off_odd); c("OFF_CODE", L.off_code);
+  o << "};\n";
+  o << kRuntimeSrc;
+  o << "#define TC_BIT(k) ((k) < 32 ? ((slo >> ((k) & 31)) & 1u) : ((shi >> ((k) & 31)) & 1u))\n"
+    << "typedef TcScratch<TcK> TcS;\n\n";
   // which antipodal pairs / boundary edges complete at each vertex
   std::vector<std::vector<int>> anti_at(V), bedge_at(V);
   for (size_t i = 0; i < D.anti.size(); ++i) anti_at[D.anti[i].second].push_back((int)i);
@@ -208,7 +159,7 @@ std::string jit_source(const Diamond &D) {
     const int m = (int)fan.size();
     o << ind << "// vertex " << v << " (" << D.x[v] << "," << D.y[v] << ")\n";
     const int pushes = (m >= 2 ? m - 1 : 0) + (int)anti_at[v].size();
-    if (pushes) o << ind << "if (np > TC_PCAP - " << pushes << "u) { tc_unions(S, np); np = 0; }\n";
+    if (pushes) o << ind << "if (np > TcK::PCAP - " << pushes << "u) { tc_unions(S, np); np = 0; }\n";
     if (mid_sig && D.y[v] == 0)
       o << ind << "const u32 s" << v << " = ((" << mid_sig << " >> " << D.k[v] << ") & 1u) ^ " << D.c[v]
         << "u;\n";
@@ -216,7 +167,7 @@ std::string jit_source(const Diamond &D) {
       o << ind << "const u32 s" << v << " = TC_BIT(" << D.k[v] << ") ^ " << D.c[v] << "u;\n";
     o << ind << "u32 L" << v << ";\n";
     if (m == 0) {
-      o << ind << "L" << v << " = nl; tc_newlab(S, nl, TC_NONE); ++nl;\n";
+      o << ind << "L" << v << " = nl; tc_newlab(S, nl, TcS::NONE); ++nl;\n";
     } else {
       o << ind << "{\n";
       for (int i = 0; i < m; ++i)
@@ -232,14 +183,14 @@ std::string jit_source(const Diamond &D) {
         for (int i = 1; i < m; ++i) {
           o << ind << "  { const u32 st = e" << i;
           if (lk[i]) o << " & (e" << i - 1 << " ^ 1u)";
-          o << "; S.word(TC_OFF_PEND, np) = L" << v << " | (L" << fan[i]
+          o << "; S.word(TcK::OFF_PEND, np) = L" << v << " | (L" << fan[i]
             << " << 16); np += st & any; any |= st; }\n";
         }
       }
       o << ind << "}\n";
     }
     for (int i : anti_at[v])
-      o << ind << "S.word(TC_OFF_PEND, np) = L" << D.anti[i].first << " | (L" << v
+      o << ind << "S.word(TcK::OFF_PEND, np) = L" << D.anti[i].first << " | (L" << v
         << " << 16) | 0x80000000u; ++np;\n";
     for (int i : bedge_at[v]) {
       const int a = D.bedge[i].first, b = D.bedge[i].second;
@@ -250,17 +201,17 @@ std::string jit_source(const Diamond &D) {
   const int Vo = V - (2 * d + 1);  // the middle row comes last in the sweep
 
   // ---- the whole sweep for one mask ----
-  o << "__device__ __forceinline__ u64 tc_classify(u64 sig, const TcScratch &S, u32 &err) {\n"
+  o << "__device__ __forceinline__ u64 tc_classify(u64 sig, const TcS &S, u32 &err) {\n"
     << "  const u32 slo = (u32)sig, shi = (u32)(sig >> 32);\n  u32 nl = 0, nb = 0, np = 0;\n"
     << "  tc_clear_odd(S);\n";
   for (int v = 0; v < V; ++v) emit_vertex(v, "  ", nullptr);
   o << "  tc_unions(S, np);\n  return tc_backend(S, nl, nb, err);\n}\n\n";
-  o << "__device__ __noinline__ u64 tc_classify_slow(u64 sig, const TcScratch &S, u32 &err) {\n"
+  o << "__device__ __noinline__ u64 tc_classify_slow(u64 sig, const TcS &S, u32 &err) {\n"
     << "  return tc_classify(sig, S, err);\n}\n\n";
 
   // ---- block sweep: halves once, middle row per instance ----
   o << "__device__ __forceinline__ void tc_sweep_amortised(u64 sig_hi, u32 ishift, u32 ireps,\n"
-    << "    const TcScratch &S, u32 &err,\n"
+    << "    const TcS &S, u32 &err,\n"
     << "    u64 *hkeys, unsigned long long *hcnt, u64 *gkeys, unsigned long long *gcnt, u64 gslots,\n"
     << "    u32 *gerr, unsigned long long &failed) {\n"
     << "  const u32 lane = threadIdx.x & 31u;\n"
@@ -272,23 +223,23 @@ std::string jit_source(const Diamond &D) {
     << "    for (u32 j = 0; j < ireps; ++j) {\n"
     << "      const u64 key = tc_classify_slow(sig_hi | ((u64)(lane + 32u * j) << ishift), S, err);\n"
     << "      failed += key == 0;\n"
-    << "      tc_hist_add(key, hkeys, hcnt, gkeys, gcnt, gslots, gerr);\n    }\n    return;\n  }\n";
+    << "      tc_hist_add<TcK::HASH>(key, hkeys, hcnt, gkeys, gcnt, gslots, gerr);\n    }\n    return;\n  }\n";
   for (int w = 0; w < L.snapw; ++w)
-    o << "  const u32 snap" << w << " = S.word(TC_OFF_LPAR, " << w << ");\n";
-  o << "  const u32 osnap = S.word(TC_OFF_ODD, 0);\n";
+    o << "  const u32 snap" << w << " = S.word(TcK::OFF_LPAR, " << w << ");\n";
+  o << "  const u32 osnap = S.word(TcK::OFF_ODD, 0);\n";
   o << "  for (u32 j = 0; j < ireps; ++j) {\n";
-  for (int w = 0; w < L.snapw; ++w) o << "    S.word(TC_OFF_LPAR, " << w << ") = snap" << w << ";\n";
-  o << "    S.word(TC_OFF_ODD, 0) = osnap;\n"
-    << "    for (u32 w = 1; w < TC_WODD; ++w) S.word(TC_OFF_ODD, w) = 0;\n"
+  for (int w = 0; w < L.snapw; ++w) o << "    S.word(TcK::OFF_LPAR, " << w << ") = snap" << w << ";\n";
+  o << "    S.word(TcK::OFF_ODD, 0) = osnap;\n"
+    << "    for (u32 w = 1; w < TcK::WODD; ++w) S.word(TcK::OFF_ODD, w) = 0;\n"
     << "    nl = nl_o; nb = nb_o; np = 0;\n"
     << "    const u32 sm = slo | ((lane + 32u * j) << ishift);\n";
   for (int v = Vo; v < V; ++v) emit_vertex(v, "    ", "sm");
   o << "    tc_unions(S, np);\n"
     << "    const u64 key = tc_backend(S, nl, nb, err);\n"
     << "    failed += key == 0;\n"
-    << "    tc_hist_add(key, hkeys, hcnt, gkeys, gcnt, gslots, gerr);\n  }\n}\n";
+    << "    tc_hist_add<TcK::HASH>(key, hkeys, hcnt, gkeys, gcnt, gslots, gerr);\n  }\n}\n";
 
-  o << dev.substr(m);
+  o << kKernelsSrc;
   return o.str();
 }
 
