@@ -167,6 +167,38 @@ ts_status ts_enumerate(const ts_tri *tri, uint64_t lo, uint64_t hi, uint32_t fla
 ts_status ts_hist_read(ts_hist *hist, uint64_t *codes, uint64_t *counts, uint64_t cap,
                        uint64_t *n_out, uint64_t *n_failed, void *stream);
 
+/* ---- Batches of mixed-degree triangulations (one graph launch) ----
+ *
+ * A batch holds njobs jobs; job j classifies counts[j] sign vectors of tris[j]
+ * (1 <= d <= 9), vector i being splitmix64(bases[j] + i) with the bits >= |A|
+ * cleared (splitmix64 as published by Steele, Lea and Flood: z = x +
+ * 0x9E3779B97F4A7C15; z = (z ^ z >> 30) * 0xBF58476D1CE4E5B9; z = (z ^ z >> 27)
+ * * 0x94D049BB133111EB; z ^ z >> 31), and adds each code to the job's own
+ * device histogram; if code_outputs is not NULL and code_outputs[j] is not
+ * NULL (device, counts[j] uint64), it also stores every code there.  For each
+ * degree present, one persistent kernel serves all jobs of that degree,
+ * staging a job's tables into shared memory when it moves to that job; the
+ * per-degree kernels run concurrently.  The triangulations must stay loaded
+ * while the batch exists.  Allocates device memory at creation only. */
+typedef struct ts_batch ts_batch;
+ts_status ts_batch_create(int njobs, ts_tri *const *tris, const uint64_t *counts,
+                          const uint64_t *bases, uint64_t *const *code_outputs,
+                          uint64_t hist_capacity, ts_batch **out);
+void ts_batch_free(ts_batch *batch);
+/* Tile of the degree-d kernel: threads per block (multiple of 32, at most 256,
+ * the block's scratch must fit shared memory) and sign vectors per work item
+ * (a multiple of threads).  Returns TS_EINVAL for tiles that do not fit. */
+ts_status ts_batch_set_tile(ts_batch *batch, int d, int threads, int chunk);
+/* Clear the histograms and run every job, asynchronously on stream.  With
+ * use_graph the work (clears, fork, per-degree kernels, join) is captured
+ * into a CUDA graph on the first call (and after a tile change) and the graph
+ * is launched; otherwise the same work is enqueued directly. */
+ts_status ts_batch_run(ts_batch *batch, int use_graph, void *stream);
+/* Histogram of one job, sorted by code, after synchronising stream (same
+ * output conventions as ts_hist_read; n_failed counts the whole batch). */
+ts_status ts_batch_read(ts_batch *batch, int job, uint64_t *codes, uint64_t *counts, uint64_t cap,
+                        uint64_t *n_out, uint64_t *n_failed, void *stream);
+
 /* Exhaustive sweep that allocates nothing (the paper has no counterpart; it
  * is an engine facility).  For callers that cannot allocate device memory at
  * the time they sweep -- code running while a stream is captured into a CUDA

@@ -74,6 +74,11 @@ def _load():
                 "ts_specialized_source": ([I, P, I, I, ctypes.c_char_p, ctypes.c_size_t,
                                            ctypes.POINTER(ctypes.c_size_t)], I),
                 "ts_enumerate_noalloc": ([P, U64, U64, ctypes.c_uint32, P, P, U64, P, P], I),
+                "ts_batch_create": ([I, P, P, P, P, U64, ctypes.POINTER(P)], I),
+                "ts_batch_free": ([P], None),
+                "ts_batch_set_tile": ([P, I, I, I], I),
+                "ts_batch_run": ([P, I, P], I),
+                "ts_batch_read": ([P, I, P, P, U64, ctypes.POINTER(U64), ctypes.POINTER(U64), P], I),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -224,6 +229,59 @@ class Histogram:
                "ts_hist_read")
         k = n.value
         return codes[:k], counts[:k], nf.value
+
+
+class Batch:
+    """Mixed-degree batch (ts_batch): job j classifies counts[j] sign vectors
+    splitmix64(bases[j] + i) of tris[j]; see include/tcurve.h."""
+
+    def __init__(self, tris, counts, bases, code_outputs=None, hist_capacity: int = 1024):
+        n = len(tris)
+        self.tris = list(tris)  # keep the triangulations alive
+        th = (ctypes.c_void_p * n)(*[t.handle.value for t in tris])
+        cnt = np.ascontiguousarray(np.asarray(counts, dtype=np.uint64))
+        bs = np.ascontiguousarray(np.asarray(bases, dtype=np.uint64))
+        outs = None
+        if code_outputs is not None:
+            self._outs = list(code_outputs)
+            outs = (ctypes.c_void_p * n)(*[0 if o is None else o.data_ptr() for o in code_outputs])
+        h = ctypes.c_void_p()
+        _check(_load().ts_batch_create(n, th, cnt.ctypes.data, bs.ctypes.data, outs,
+                                       int(hist_capacity), ctypes.byref(h)), "ts_batch_create")
+        self._h = h
+        self.njobs = n
+        self.counts = cnt
+        self.capacity = int(hist_capacity)
+        self.degrees = sorted({t.d for t in tris})
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.ts_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_tile(self, d: int, threads: int, chunk: int):
+        _check(_lib.ts_batch_set_tile(self._h, int(d), int(threads), int(chunk)), "ts_batch_set_tile")
+
+    def run(self, graph: bool = True, stream=None):
+        _check(_lib.ts_batch_run(self._h, int(bool(graph)), _stream_handle(stream)), "ts_batch_run")
+
+    def read(self, job: int, stream=None):
+        """(codes (n,) uint64, counts (n,) uint64, failed) of one job, sorted by code."""
+        cap = self.capacity
+        codes = np.zeros(cap, dtype=np.uint64)
+        counts = np.zeros(cap, dtype=np.uint64)
+        n = ctypes.c_uint64()
+        nf = ctypes.c_uint64()
+        _check(_lib.ts_batch_read(self._h, int(job), codes.ctypes.data, counts.ctypes.data, cap,
+                                  ctypes.byref(n), ctypes.byref(nf), _stream_handle(stream)),
+               "ts_batch_read")
+        return codes[:n.value], counts[:n.value], nf.value
 
 
 def enumerate_schemes(tri: Triangulation, lo: int, hi: int, hist: Histogram, flags: int = 0,

@@ -1,0 +1,98 @@
+"""Tile autotuner of mixed-degree batches (ts_batch).
+
+For every degree in a batch the persistent kernel has two knobs: threads per
+block and sign vectors per work item.  The tuner times candidate tiles on the
+batch's own jobs of that degree (a sub-batch, so degrees are tuned
+independently), keeps the fastest, and can store the choice in a JSON cache
+keyed by GPU name and degree (path from the argument or the TCURVE_TILE_CACHE
+environment variable).
+"""
+from __future__ import annotations
+
+import json
+import os
+from typing import Dict, Iterable, Optional, Tuple
+
+THREADS = (64, 96, 128, 192, 256)
+CHUNK_PER_THREAD = (4, 16, 64)
+
+
+def _gpu_name() -> str:
+    import torch
+    return torch.cuda.get_device_name()
+
+
+def _time_batch(batch, reps: int) -> float:
+    import torch
+    batch.run(graph=False)
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        batch.run(graph=False)
+        b.record()
+        b.synchronize()
+        best = min(best, a.elapsed_time(b))
+    return best
+
+
+def tune_degree(tris, counts, bases, threads: Iterable[int] = THREADS,
+                chunk_per_thread: Iterable[int] = CHUNK_PER_THREAD, reps: int = 3
+                ) -> Tuple[int, int, float]:
+    """Fastest (threads, chunk, ms) for the jobs (all of one degree)."""
+    from . import Batch, TSError
+    d = tris[0].d
+    assert all(t.d == d for t in tris)
+    sub = Batch(tris, counts, bases, hist_capacity=1024)
+    best = None
+    for t in threads:
+        for c in chunk_per_thread:
+            try:
+                sub.set_tile(d, t, t * c)
+            except TSError:
+                continue  # the block does not fit shared memory
+            ms = _time_batch(sub, reps)
+            if best is None or ms < best[2]:
+                best = (t, t * c, ms)
+    sub.close()
+    if best is None:
+        raise RuntimeError(f"no tile fits degree {d}")
+    return best
+
+
+def autotune(tris, counts, bases, cache: Optional[str] = None, reps: int = 3,
+             threads: Iterable[int] = THREADS, chunk_per_thread: Iterable[int] = CHUNK_PER_THREAD
+             ) -> Dict[int, Tuple[int, int]]:
+    """Tile per degree of the batch {d: (threads, chunk)}; cached choices are
+    reused, new ones stored."""
+    cache = cache or os.environ.get("TCURVE_TILE_CACHE")
+    store = {}
+    if cache and os.path.exists(cache):
+        with open(cache) as f:
+            store = json.load(f)
+    gpu = _gpu_name()
+    tiles: Dict[int, Tuple[int, int]] = {}
+    for d in sorted({t.d for t in tris}):
+        key = f"{gpu}|d={d}"
+        if key in store:
+            tiles[d] = tuple(store[key][:2])
+            continue
+        idx = [i for i, t in enumerate(tris) if t.d == d]
+        t, c, ms = tune_degree([tris[i] for i in idx], [counts[i] for i in idx],
+                               [bases[i] for i in idx], threads, chunk_per_thread, reps)
+        tiles[d] = (t, c)
+        store[key] = [t, c, ms]
+    if cache:
+        tmp = cache + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump(store, f, indent=1, sort_keys=True)
+        os.replace(tmp, cache)
+    return tiles
+
+
+def apply(batch, tiles: Dict[int, Tuple[int, int]]):
+    for d, (t, c) in tiles.items():
+        if d in batch.degrees:
+            batch.set_tile(d, t, c)

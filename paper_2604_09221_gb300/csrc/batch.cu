@@ -1,0 +1,504 @@
+// batch.cu -- many triangulations of mixed degree in one graph launch.
+//
+// A batch is a list of jobs (triangulation, number of sign vectors, splitmix64
+// stream of the sign vectors, optional code output).  For each degree present
+// the batch runs ONE persistent kernel over all jobs of that degree: blocks
+// pull (job, chunk) work items from a counter, re-stage a job's tables into
+// shared memory with cp.async.bulk when the job changes, generate the sign
+// vectors on the device, classify them with the table-driven sweep
+// (Algorithm 1) and add the codes to the job's own device hash histogram
+// (warp-aggregated atomics).  The per-degree kernels run on forked streams
+// inside one CUDA graph that is captured on the first run and replayed after;
+// each degree has its own tile shape (threads per block, instances per work
+// item), which ts_batch_set_tile changes (the autotuner's knob).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "engine.h"
+#include "tc_layout.h"
+#include "tc_runtime.cuh"
+
+namespace tcurve {
+namespace {
+
+constexpr long kWaitIters = 1L << 22;
+
+template <int D_, int T_>
+struct JobK {
+  static constexpr TcLayout L = tc_layout(D_, true, T_);
+  static constexpr u32 D = D_, V = L.V, NPOINTS = (D_ + 1) * (D_ + 2) / 2, RMAX = L.rmax,
+                       NB = L.nb, THREADS = T_, HASH = 1, LBYTES = L.lbytes, CODE64 = L.code64,
+                       PCAP = L.pcap, WODD = L.wodd, WORDS = L.words, OFF_LPAR = L.off_lpar,
+                       OFF_CAND = L.off_cand, OFF_LAB = L.off_lab, OFF_BPAIR = L.off_bpair,
+                       OFF_PEND = L.off_pend, OFF_ADJ = L.off_adj, OFF_RLAB = L.off_rlab,
+                       OFF_TPAR = L.off_tpar, OFF_ORDER = L.off_order, OFF_CLEN = L.off_clen,
+                       OFF_ODD = L.off_odd, OFF_CODE = L.off_code;
+  static constexpr bool fits = L.ok && (size_t)WORDS * 4 * T_ + 4096 + 256 <= 220 * 1024;
+};
+
+struct DevJob {
+  const u32 *tab;
+  u64 n;              // sign vectors
+  u64 base;           // splitmix64 counter base of the sign vectors
+  u64 *codes;         // per-instance codes (or null)
+  u64 *hkeys;         // job histogram (open addressing, 0 = empty)
+  unsigned long long *hcnt;
+  u64 hslots;
+  u64 chunk0;         // first work item of the job
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ u64 splitmix64(u64 x) {
+  u64 z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ u32 sign_bit(u64 sigma, u32 k, u32 c) {
+  return ((u32)(sigma >> k) & 1u) ^ c;
+}
+
+// The table-driven sweep of kernels.cu, over tables in shared memory.
+template <class K>
+__device__ u64 classify_job(u64 sigma, const u32 *__restrict__ tab, u32 off_fan, u32 off_vext,
+                            const TcScratch<K> &S, u32 &err) {
+  const u32 *vdesc = tab;
+  const u32 *fan = tab + off_fan;
+  const u32 *vext = tab + off_vext;
+  u32 nl = 0, nb = 0, np = 0;
+  tc_clear_odd(S);
+  for (u32 v = 0; v < K::V; ++v) {
+    const u32 desc = vdesc[v];
+    const u32 sv = sign_bit(sigma, desc & 63u, (desc >> 6) & 1u);
+    const u32 m = (desc >> 7) & 63u, fs = desc >> 16;
+    if (np + m + 1 > K::PCAP) {
+      tc_unions(S, np);
+      np = 0;
+    }
+    u32 lv = 0, l0 = TcScratch<K>::NONE, any = 0, prev = 0;
+    for (u32 i = 0; i < m; ++i) {
+      const u32 f = fan[fs + i];
+      const u32 lu = *S.lab(K::OFF_LAB, f & 255u);
+      const u32 e = sign_bit(sigma, (f >> 8) & 63u, (f >> 14) & 1u) ^ sv ^ 1u;
+      const u32 st = e & ~(((f >> 15) & 1u) & prev) & 1u;
+      l0 = i == 0 ? lu : l0;
+      S.word(K::OFF_PEND, np) = lv | (lu << 16);
+      np += st & any;
+      lv = any ? lv : (st ? lu : lv);
+      any |= st;
+      prev = e;
+    }
+    if (!any) {
+      lv = nl;
+      tc_newlab(S, nl, l0);
+      ++nl;
+    }
+    *S.lab(K::OFF_LAB, v) = (typename TcScratch<K>::lab_t)lv;
+    const u32 x = vext[v];
+    if ((x & 255u) != 255u) {
+      S.word(K::OFF_PEND, np) = (u32)*S.lab(K::OFF_LAB, x & 255u) | (lv << 16) | 0x80000000u;
+      ++np;
+    }
+    if (K::D % 2) {
+#pragma unroll
+      for (u32 sh = 8; sh <= 16; sh += 8) {
+        const u32 b = (x >> sh) & 255u;
+        if (b == 255u) continue;
+        const u32 db = vdesc[b];
+        if (sign_bit(sigma, db & 63u, (db >> 6) & 1u) != sv) {
+          tc_bpair(S, nb, *S.lab(K::OFF_LAB, b), lv);
+          ++nb;
+        }
+      }
+    }
+  }
+  tc_unions(S, np);
+  return tc_backend(S, nl, nb, err);
+}
+
+template <int D, int T>
+__global__ void __launch_bounds__(T)
+    jobs_kernel(const DevJob *__restrict__ jobs, u32 njobs, u64 total_items, u32 chunk,
+                u32 table_words, u32 off_fan, u32 off_vext, unsigned long long *work, u32 *err_word,
+                unsigned long long *failed_word) {
+  typedef JobK<D, T> K;
+  extern __shared__ __align__(128) uint8_t smem[];
+  u32 *tab = reinterpret_cast<u32 *>(smem);
+  const size_t toff = ((size_t)table_words * 4 + 127) / 128 * 128;
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + toff);
+  unsigned long long *slot = reinterpret_cast<unsigned long long *>(smem + toff + 64);
+  const TcScratch<K> S{reinterpret_cast<u32 *>(smem + toff + 128) + threadIdx.x};
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(1u));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const u32 lane = threadIdx.x & 31u;
+  const u64 valid = K::NPOINTS >= 64 ? ~0ull : ((1ull << (K::NPOINTS & 63)) - 1);
+  u32 cur = 0xFFFFFFFFu, phase = 0, err = 0;
+  unsigned long long failed = 0;
+  for (;;) {
+    if (threadIdx.x == 0) *slot = atomicAdd(work, 1ull);
+    __syncthreads();
+    const u64 c = *slot;
+    __syncthreads();  // also: every thread is done with the previous job's tables
+    if (c >= total_items) break;
+    u32 lo = 0, hi = njobs;  // the job holding item c: last j with chunk0 <= c
+    while (hi - lo > 1) {
+      const u32 mid = (lo + hi) / 2;
+      if (jobs[mid].chunk0 <= c) lo = mid; else hi = mid;
+    }
+    const u32 j = lo;
+    if (j != cur) {  // stage the job's tables (cp.async.bulk, bounded wait)
+      if (threadIdx.x == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                     "r"(table_words * 4u) : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+                "r"(smem_u32(tab)), "l"(jobs[j].tab), "r"(table_words * 4u), "r"(smem_u32(bar))
+            : "memory");
+      }
+      bool ok = false;
+      for (long it = 0; it < kWaitIters && !ok; ++it) {
+        uint32_t r;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(r) : "r"(smem_u32(bar)), "r"(phase) : "memory");
+        ok = r != 0;
+      }
+      if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) atomicOr(err_word, kErrTimeout);
+        for (long it = 0; it < kWaitIters && !ok; ++it) {
+          uint32_t r;
+          asm volatile(
+              "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+              " selp.u32 %0, 1, 0, p;\n}"
+              : "=r"(r) : "r"(smem_u32(bar)), "r"(phase) : "memory");
+          ok = r != 0;
+        }
+        return;
+      }
+      phase ^= 1u;
+      cur = j;
+    }
+    const DevJob J = jobs[j];
+    const u64 first = (c - J.chunk0) * (u64)chunk;
+    for (u32 k = 0; k < chunk; k += T) {
+      const u64 idx = first + k + threadIdx.x;
+      u64 key = 0;
+      if (idx < J.n) {
+        key = classify_job<K>(splitmix64(J.base + idx) & valid, tab, off_fan, off_vext, S, err);
+        failed += key == 0;
+        if (J.codes) J.codes[idx] = key;
+      }
+      const unsigned peers = __match_any_sync(0xffffffffu, key);
+      if (key != 0 && lane == (u32)(__ffs(peers) - 1))
+        tc_global_add(J.hkeys, J.hcnt, J.hslots, err_word, key, (unsigned long long)__popc(peers));
+    }
+  }
+  if (err) atomicOr(err_word, err);
+  if (failed) atomicAdd(failed_word, failed);
+}
+
+// (degree, threads) -> kernel; only instantiations whose block fits.
+typedef void (*JobsFn)(const DevJob *, u32, u64, u32, u32, u32, u32, unsigned long long *, u32 *,
+                       unsigned long long *);
+
+template <int D, int T>
+JobsFn jobs_fn() {
+  if constexpr (JobK<D, T>::fits) return jobs_kernel<D, T>;
+  else return nullptr;
+}
+
+template <int D>
+JobsFn jobs_fn_t(int t) {
+  switch (t) {
+    case 32: return jobs_fn<D, 32>();
+    case 64: return jobs_fn<D, 64>();
+    case 96: return jobs_fn<D, 96>();
+    case 128: return jobs_fn<D, 128>();
+    case 192: return jobs_fn<D, 192>();
+    case 256: return jobs_fn<D, 256>();
+    default: return nullptr;
+  }
+}
+
+JobsFn jobs_fn_dt(int d, int t) {
+  switch (d) {
+    case 1: return jobs_fn_t<1>(t);
+    case 2: return jobs_fn_t<2>(t);
+    case 3: return jobs_fn_t<3>(t);
+    case 4: return jobs_fn_t<4>(t);
+    case 5: return jobs_fn_t<5>(t);
+    case 6: return jobs_fn_t<6>(t);
+    case 7: return jobs_fn_t<7>(t);
+    case 8: return jobs_fn_t<8>(t);
+    case 9: return jobs_fn_t<9>(t);
+    default: return nullptr;
+  }
+}
+
+size_t jobs_smem(int d, int t, uint32_t table_words) {
+  const TcLayout L = tc_layout(d, true, t);
+  return ((size_t)table_words * 4 + 127) / 128 * 128 + 128 + (size_t)L.words * 4 * t;
+}
+
+ts_status cuda_st(cudaError_t e) {
+  if (e == cudaSuccess) return TS_OK;
+  return e == cudaErrorMemoryAllocation ? TS_ENOMEM : TS_ECUDA;
+}
+
+}  // namespace
+}  // namespace tcurve
+
+using namespace tcurve;
+
+struct ts_batch {
+  struct Group {  // all jobs of one degree
+    int d = 0, threads = 64, chunk = 1024;
+    uint32_t table_words = 0, off_fan = 0, off_vext = 0;
+    std::vector<int> jobs;      // indices into the batch's job list
+    DevJob *d_jobs = nullptr;   // device job table (sorted as `jobs`)
+    uint64_t items = 0;
+    unsigned long long *d_work = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+  };
+  std::vector<DevJob> jobs;  // host copies (chunk0 per group)
+  std::vector<int> degree;
+  std::vector<Group> groups;
+  uint64_t hslots = 0;
+  uint64_t *d_keys = nullptr;  // njobs x hslots
+  unsigned long long *d_counts = nullptr;
+  uint32_t *d_err = nullptr;
+  unsigned long long *d_failed = nullptr;
+  cudaEvent_t fork = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int device = 0;
+};
+
+namespace {
+
+cudaError_t upload_group(ts_batch *b, ts_batch::Group &g) {
+  std::vector<DevJob> dj;
+  uint64_t items = 0;
+  for (int j : g.jobs) {
+    DevJob x = b->jobs[j];
+    x.chunk0 = items;
+    items += (x.n + g.chunk - 1) / g.chunk;
+    dj.push_back(x);
+  }
+  g.items = items;
+  if (!g.d_jobs) {
+    cudaError_t e = cudaMalloc(&g.d_jobs, sizeof(DevJob) * dj.size());
+    if (e != cudaSuccess) return e;
+  }
+  return cudaMemcpy(g.d_jobs, dj.data(), sizeof(DevJob) * dj.size(), cudaMemcpyHostToDevice);
+}
+
+cudaError_t launch_group(ts_batch *b, ts_batch::Group &g, cudaStream_t st) {
+  JobsFn fn = jobs_fn_dt(g.d, g.threads);
+  if (!fn) return cudaErrorInvalidConfiguration;
+  const size_t smem = jobs_smem(g.d, g.threads, g.table_words);
+  cudaError_t e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0, sms = 0, dev = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)fn, g.threads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const uint64_t cap = (uint64_t)per_sm * sms;
+  const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(cap, g.items));
+  e = cudaMemsetAsync(g.d_work, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  fn<<<grid, g.threads, smem, st>>>(g.d_jobs, (u32)g.jobs.size(), g.items, (u32)g.chunk,
+                                    g.table_words, g.off_fan, g.off_vext, g.d_work, b->d_err,
+                                    b->d_failed);
+  return cudaGetLastError();
+}
+
+// The whole batch as stream work on `st`: clear, fork, one kernel per degree, join.
+cudaError_t enqueue(ts_batch *b, cudaStream_t st) {
+  const size_t nj = b->jobs.size();
+  cudaError_t e = cudaMemsetAsync(b->d_keys, 0, nj * b->hslots * 8, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counts, 0, nj * b->hslots * 8, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, 4, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_failed, 0, 8, st);
+  if (e == cudaSuccess) e = cudaEventRecord(b->fork, st);
+  for (auto &g : b->groups) {
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(g.stream, b->fork, 0);
+    if (e == cudaSuccess) e = launch_group(b, g, g.stream);
+    if (e == cudaSuccess) e = cudaEventRecord(g.done, g.stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, g.done, 0);
+  }
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+ts_status ts_batch_create(int njobs, ts_tri *const *tris, const uint64_t *counts,
+                          const uint64_t *bases, uint64_t *const *code_outputs,
+                          uint64_t hist_capacity, ts_batch **out) {
+  if (!out || njobs < 1 || !tris || !counts || !bases || hist_capacity == 0 ||
+      hist_capacity > (1u << 20))
+    return TS_EINVAL;
+  *out = nullptr;
+  ts_batch *b = new (std::nothrow) ts_batch();
+  if (!b) return TS_ENOMEM;
+  uint64_t s = 16;
+  while (s < 2 * hist_capacity) s <<= 1;
+  b->hslots = s;
+  cudaError_t e = cudaGetDevice(&b->device);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_keys, (size_t)njobs * s * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_counts, (size_t)njobs * s * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_err, 4);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_failed, 8);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  std::map<int, int> gi;
+  for (int j = 0; j < njobs && e == cudaSuccess; ++j) {
+    const ts_tri *t = tris[j];
+    if (!t || t->cw != 1 || t->np > 64 || t->device != b->device) {
+      ts_batch_free(b);
+      return TS_EINVAL;
+    }
+    DevJob x{};
+    x.tab = t->d_tables;
+    x.n = counts[j];
+    x.base = bases[j];
+    x.codes = code_outputs ? reinterpret_cast<u64 *>(code_outputs[j]) : nullptr;
+    x.hkeys = reinterpret_cast<u64 *>(b->d_keys + (size_t)j * s);
+    x.hcnt = b->d_counts + (size_t)j * s;
+    x.hslots = s;
+    b->jobs.push_back(x);
+    b->degree.push_back(t->d);
+    if (!gi.count(t->d)) {
+      gi[t->d] = (int)b->groups.size();
+      ts_batch::Group g;
+      g.d = t->d;
+      g.table_words = t->lay.words;
+      g.off_fan = t->lay.off_fan;
+      g.off_vext = t->lay.off_vext;
+      g.threads = t->d >= 8 ? 64 : 128;
+      g.chunk = g.threads * 8;
+      b->groups.push_back(g);
+    }
+    b->groups[gi[t->d]].jobs.push_back(j);
+  }
+  for (auto &g : b->groups) {
+    if (e == cudaSuccess) e = cudaMalloc(&g.d_work, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = upload_group(b, g);
+  }
+  if (e != cudaSuccess) {
+    ts_batch_free(b);
+    return cuda_st(e);
+  }
+  *out = b;
+  return TS_OK;
+}
+
+void ts_batch_free(ts_batch *b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (auto &g : b->groups) {
+    if (g.d_jobs) cudaFree(g.d_jobs);
+    if (g.d_work) cudaFree(g.d_work);
+    if (g.stream) cudaStreamDestroy(g.stream);
+    if (g.done) cudaEventDestroy(g.done);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->d_keys) cudaFree(b->d_keys);
+  if (b->d_counts) cudaFree(b->d_counts);
+  if (b->d_err) cudaFree(b->d_err);
+  if (b->d_failed) cudaFree(b->d_failed);
+  delete b;
+}
+
+ts_status ts_batch_set_tile(ts_batch *b, int d, int threads, int chunk) {
+  if (!b || threads < 32 || threads % 32 || chunk < threads || chunk % threads) return TS_EINVAL;
+  for (auto &g : b->groups) {
+    if (g.d != d) continue;
+    if (!jobs_fn_dt(d, threads)) return TS_EINVAL;  // block does not fit shared memory
+    g.threads = threads;
+    g.chunk = chunk;
+    if (b->exec) {
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
+    return cuda_st(upload_group(b, g));
+  }
+  return TS_EINVAL;
+}
+
+ts_status ts_batch_run(ts_batch *b, int use_graph, void *stream) {
+  if (!b) return TS_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!use_graph) return cuda_st(enqueue(b, st));
+  if (!b->exec) {
+    cudaStream_t cap = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    cudaGraph_t graph = nullptr;
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t e2 = enqueue(b, cap);
+      e = cudaStreamEndCapture(cap, &graph);
+      if (e2 != cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (cap) cudaStreamDestroy(cap);
+    if (e != cudaSuccess) return cuda_st(e);
+  }
+  return cuda_st(cudaGraphLaunch(b->exec, st));
+}
+
+ts_status ts_batch_read(ts_batch *b, int job, uint64_t *codes, uint64_t *counts, uint64_t cap,
+                        uint64_t *n_out, uint64_t *n_failed, void *stream) {
+  if (!b || !n_out || job < 0 || job >= (int)b->jobs.size() || (cap && (!codes || !counts)))
+    return TS_EINVAL;
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  std::vector<uint64_t> k(b->hslots);
+  std::vector<unsigned long long> c(b->hslots);
+  uint32_t err = 0;
+  unsigned long long failed = 0;
+  if (e == cudaSuccess)
+    e = cudaMemcpy(k.data(), b->d_keys + (size_t)job * b->hslots, b->hslots * 8, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(c.data(), b->d_counts + (size_t)job * b->hslots, b->hslots * 8,
+                   cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&err, b->d_err, 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&failed, b->d_failed, 8, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_st(e);
+  std::vector<std::pair<uint64_t, uint64_t>> v;
+  for (uint64_t s = 0; s < b->hslots; ++s)
+    if (k[s]) v.push_back({k[s], c[s]});
+  std::sort(v.begin(), v.end());
+  *n_out = v.size();
+  if (n_failed) *n_failed = failed;
+  for (uint64_t i = 0; i < v.size() && i < cap; ++i) {
+    codes[i] = v[i].first;
+    counts[i] = v[i].second;
+  }
+  if (v.size() > cap) return TS_EOVERFLOW;
+  if (err & kErrTimeout) return TS_ETIMEOUT;
+  if (err & kErrOverflow) return TS_EOVERFLOW;
+  if (err & kErrInternal) return TS_EINTERNAL;
+  return TS_OK;
+}
+
+}  // extern "C"
