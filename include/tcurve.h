@@ -59,6 +59,9 @@ typedef enum ts_status {
 #define TS_ENUM_FLIP 1u    /* mask = k << 1: one representative per global sign flip */
 #define TS_ENUM_REDUCED 2u /* zeros inserted at bits 0, 1, d+1 (sigma(0,0) = sigma(1,0) =
                               sigma(0,1) = 0): one representative per (Z/2)^3 class (Sec. 3) */
+#define TS_ENUM_SPLITMIX 4u /* mask = splitmix64(k) with the bits >= |A| cleared: a sampled,
+                               reproducible stream of sign vectors (splitmix64 of
+                               ts_batch_create); no bound on hi */
 
 /* Human-readable name of a status code; never NULL. */
 const char *ts_status_str(int status);
@@ -138,6 +141,11 @@ ts_status ts_real_schemes_host(const ts_tri *tri, const uint64_t *signs_host, ui
  * word (TS_OK if no instance failed since the last call). */
 ts_status ts_sync(const ts_tri *tri, void *stream);
 
+/* Input generation: out[i] = splitmix64(base + i) with the bits >= |A| of
+ * degree d cleared, i < n (device buffer of n uint64; asynchronous).  The same
+ * sign vectors as TS_ENUM_SPLITMIX sweeps and batches use. */
+ts_status ts_splitmix_masks(int d, uint64_t base, uint64_t n, uint64_t *out, void *stream);
+
 /* Device hash histogram of scheme codes with room for `capacity` distinct
  * codes of `code_words` words each (rounded up to a power of two, x2). */
 ts_status ts_hist_create(uint64_t capacity, int code_words, ts_hist **out);
@@ -148,8 +156,9 @@ ts_status ts_hist_clear(ts_hist *hist, void *stream);
 /* Exhaustive sweep (Sec. 3, "check all sign distributions for one or a few
  * triangulations"): adds the scheme of every mask m(k), k in [lo, hi), to
  * `hist`.  m(k) = k by default; k << 1 with TS_ENUM_FLIP; k with zero bits
- * inserted at positions 0, 1 and d+1 with TS_ENUM_REDUCED.  Requires
- * m(hi-1) < 2^|A| and |A| <= 64 (d <= 9).  One persistent launch on
+ * inserted at positions 0, 1 and d+1 with TS_ENUM_REDUCED; splitmix64(k)
+ * (bits >= |A| cleared) with TS_ENUM_SPLITMIX.  Requires |A| <= 64 (d <= 9)
+ * and, except with TS_ENUM_SPLITMIX, m(hi-1) < 2^|A|.  One persistent launch on
  * `stream`; asynchronous.  Failed instances are counted, not inserted, and
  * set the histogram's error word. */
 ts_status ts_enumerate(const ts_tri *tri, uint64_t lo, uint64_t hi, uint32_t flags,

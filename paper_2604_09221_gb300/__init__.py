@@ -19,6 +19,7 @@ from . import build as _build
 
 TS_ENUM_FLIP = 1
 TS_ENUM_REDUCED = 2
+TS_ENUM_SPLITMIX = 4
 TS_KERNEL_AUTO = 0
 TS_KERNEL_TABLE = 1
 TS_KERNEL_SPECIALIZED = 2
@@ -74,6 +75,7 @@ def _load():
                 "ts_specialized_source": ([I, P, I, I, ctypes.c_char_p, ctypes.c_size_t,
                                            ctypes.POINTER(ctypes.c_size_t)], I),
                 "ts_enumerate_noalloc": ([P, U64, U64, ctypes.c_uint32, P, P, U64, P, P], I),
+                "ts_splitmix_masks": ([I, U64, U64, P, P], I),
                 "ts_batch_create": ([I, P, P, P, P, U64, ctypes.POINTER(P)], I),
                 "ts_batch_free": ([P], None),
                 "ts_batch_set_tile": ([P, I, I, I], I),
@@ -306,6 +308,16 @@ def specialized_source(d: int, edges, compile: bool = False) -> str:
     if st != 0:
         raise TSError(st, "ts_specialized_source: " + text[-3000:])
     return text
+
+
+def splitmix_masks(d: int, base: int, n: int, out=None, stream=None):
+    """Device sign vectors splitmix64(base + i) cut to |A| bits (int64 tensor)."""
+    import torch
+    if out is None:
+        out = torch.empty(n, dtype=torch.int64, device="cuda")
+    _check(_load().ts_splitmix_masks(int(d), int(base) & ((1 << 64) - 1), int(n), out.data_ptr(),
+                                     _stream_handle(stream)), "ts_splitmix_masks")
+    return out
 
 
 def scheme_string(d: int, code) -> str:

@@ -56,13 +56,6 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-__device__ __forceinline__ u64 splitmix64(u64 x) {
-  u64 z = x + 0x9E3779B97F4A7C15ull;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
-
 __device__ __forceinline__ u32 sign_bit(u64 sigma, u32 k, u32 c) {
   return ((u32)(sigma >> k) & 1u) ^ c;
 }
@@ -197,7 +190,7 @@ __global__ void __launch_bounds__(T)
       const u64 idx = first + k + threadIdx.x;
       u64 key = 0;
       if (idx < J.n) {
-        key = classify_job<K>(splitmix64(J.base + idx) & valid, tab, off_fan, off_vext, S, err);
+        key = classify_job<K>(tc_splitmix64(J.base + idx) & valid, tab, off_fan, off_vext, S, err);
         failed += key == 0;
         if (J.codes) J.codes[idx] = key;
       }

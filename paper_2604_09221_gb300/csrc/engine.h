@@ -87,6 +87,8 @@ cudaError_t launch_real_schemes(const ts_tri *tri, const uint64_t *signs, uint64
 cudaError_t launch_enumerate(const ts_tri *tri, uint64_t lo, uint64_t hi, uint32_t flags,
                              ts_hist *hist, cudaStream_t stream);
 cudaError_t launch_hist_clear(ts_hist *hist, cudaStream_t stream);
+cudaError_t launch_splitmix_masks(int d, uint64_t base, uint64_t n, uint64_t *out,
+                                  cudaStream_t stream);
 
 // Specialised kernels (jit.cpp).
 std::string jit_source(const Diamond &D);

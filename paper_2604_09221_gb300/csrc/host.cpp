@@ -416,6 +416,13 @@ ts_status ts_real_schemes_host(const ts_tri *t, const uint64_t *signs_host, uint
   return ts_sync(t, 0);
 }
 
+ts_status ts_splitmix_masks(int d, uint64_t base, uint64_t n, uint64_t *out, void *stream) {
+  if (d < 1 || (n && !out)) return TS_EINVAL;
+  if (d > kMaxDegree) return TS_EUNSUPPORTED;
+  if (n == 0) return TS_OK;
+  return cuda_status(launch_splitmix_masks(d, base, n, out, (cudaStream_t)stream));
+}
+
 ts_status ts_hist_create(uint64_t capacity, int code_words, ts_hist **out) {
   if (!out || code_words < 1 || code_words > 4 || capacity == 0 || capacity > (1ull << 30))
     return TS_EINVAL;
@@ -460,13 +467,12 @@ ts_status ts_hist_clear(ts_hist *h, void *stream) {
 
 ts_status ts_enumerate(const ts_tri *t, uint64_t lo, uint64_t hi, uint32_t flags, ts_hist *h,
                        void *stream) {
-  if (!t || !h || hi < lo || (flags & ~(TS_ENUM_FLIP | TS_ENUM_REDUCED)) ||
-      flags == (TS_ENUM_FLIP | TS_ENUM_REDUCED))
-    return TS_EINVAL;
+  const uint32_t kinds = flags & (TS_ENUM_FLIP | TS_ENUM_REDUCED | TS_ENUM_SPLITMIX);
+  if (!t || !h || hi < lo || (flags & ~kinds) || (kinds & (kinds - 1))) return TS_EINVAL;
   if (h->cw != t->cw) return TS_EINVAL;
   if (t->np > 64) return TS_EUNSUPPORTED;
   int free_bits = t->np - ((flags & TS_ENUM_FLIP) ? 1 : 0) - ((flags & TS_ENUM_REDUCED) ? 3 : 0);
-  if (free_bits < 64 && hi > (1ull << free_bits)) return TS_EINVAL;
+  if (!(flags & TS_ENUM_SPLITMIX) && free_bits < 64 && hi > (1ull << free_bits)) return TS_EINVAL;
   if (lo == hi) return TS_OK;
   ts_tri *tm = const_cast<ts_tri *>(t);
   if (want_specialised(tm, hi - lo, true))

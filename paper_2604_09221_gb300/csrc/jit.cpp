@@ -409,7 +409,8 @@ cudaError_t launch_enumerate_jit(ts_tri *t, uint64_t lo, uint64_t hi, uint32_t f
   uint32_t ib = d + 1, ishift = 0, oshift = d + 1;
   if (flags & TS_ENUM_FLIP) { ib = d; ishift = 1; oshift = d + 1; }
   if (flags & TS_ENUM_REDUCED) { ib = d - 1; ishift = 2; oshift = d + 2; }
-  if (ib < 5) return enumerate_range(*m, h, lo, hi, flags, st);  // fewer patterns than lanes
+  if (ib < 5 || (flags & TS_ENUM_SPLITMIX))  // fewer patterns than lanes / sampled masks
+    return enumerate_range(*m, h, lo, hi, flags, st);
   const uint64_t a = ((lo + (1ull << ib) - 1) >> ib) << ib, b = (hi >> ib) << ib;
   if (a >= b) return enumerate_range(*m, h, lo, hi, flags, st);
   if (lo < a && (e = enumerate_range(*m, h, lo, a, flags, st)) != cudaSuccess) return e;

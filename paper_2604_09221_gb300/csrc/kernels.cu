@@ -265,6 +265,14 @@ __global__ void __launch_bounds__(TableK<D>::THREADS)
   if (failed) atomicAdd(h.d_failed, failed);
 }
 
+// Sign vectors splitmix64(base + i), cut to npoints bits (input generation).
+__global__ void splitmix_masks_kernel(uint64_t base, uint64_t n, uint32_t npoints, uint64_t *out) {
+  const uint64_t valid = npoints >= 64 ? ~0ull : ((1ull << npoints) - 1);
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    out[i] = tc_splitmix64(base + i) & valid;
+}
+
 __global__ void hist_clear_kernel(ts_hist h) {
   const uint64_t n = h.slots;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -361,6 +369,13 @@ cudaError_t launch_enumerate(const ts_tri *t, uint64_t lo, uint64_t hi, uint32_t
     case 9: return enumerate_d<9>(t, lo, hi, flags, h, st);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_splitmix_masks(int d, uint64_t base, uint64_t n, uint64_t *out, cudaStream_t st) {
+  const uint64_t blocks = (n + 255) / 256;
+  splitmix_masks_kernel<<<(unsigned)(blocks < 4096 ? (blocks ? blocks : 1) : 4096), 256, 0, st>>>(
+      base, n, (uint32_t)((d + 1) * (d + 2) / 2), out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_hist_clear(ts_hist *h, cudaStream_t st) {

@@ -372,9 +372,20 @@ __device__ __forceinline__ void tc_hist_add(u64 key, u64 *hkeys, unsigned long l
   }
 }
 
-// Enumeration masks (ts_enumerate flags): k, k << 1, or k with zero bits
-// inserted at positions 0, 1 and d + 1.
+__device__ __forceinline__ u64 tc_splitmix64(u64 x) {
+  u64 z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Enumeration masks (ts_enumerate flags): k, k << 1, k with zero bits
+// inserted at positions 0, 1 and d + 1, or splitmix64(k) cut to |A| bits.
 __device__ __forceinline__ u64 tc_enum_mask(u64 k, u32 flags, u32 d) {
+  if (flags & 4u) {
+    const u32 np = (d + 1) * (d + 2) / 2;
+    return tc_splitmix64(k) & (np >= 64 ? ~0ull : ((1ull << np) - 1));
+  }
   if (flags & 1u) return k << 1;
   if (flags & 2u) return ((k & ((1ull << (d - 1)) - 1)) << 2) | ((k >> (d - 1)) << (d + 2));
   return k;
