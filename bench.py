@@ -14,7 +14,17 @@ the enumeration kernel, the CPU oracle on a bounded sample, the plain
 one-launch query kernel (ts_real_schemes on materialised masks) beside the
 persistent sweep, SM clocks sampled during the timed region.
 
+The default line also carries a short serving run (Poisson job stream on the
+continuous-batching server, p50/p99 job latency).  Other workloads:
+
+  --workload mixed    the mixed-degree batch: 32 seeded triangulations for each
+                      d in 5..9, sign-vector counts log-uniform in [2^10, 2^24],
+                      one CUDA-graph launch per step, autotuned tiles
+  --workload serving  a longer Poisson stream: d uniform in 6..9, 2^8..2^22
+                      sign vectors per job, p50/p99 latency and schemes/s
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--workload d7|mixed|serving]
 """
 from __future__ import annotations
 
@@ -165,9 +175,16 @@ def main():
     ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--workload", default="d7", choices=["d7", "mixed", "serving"])
+    ap.add_argument("--serve-seconds", type=float, default=6.0)
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.workload == "mixed":
+        return mixed_workload(args)
+    if args.workload == "serving":
+        return serving_workload(args, seconds=max(args.serve_seconds, 20.0))
 
     import numpy as np
     import torch
@@ -295,6 +312,8 @@ def main():
             "roofline": roofline, "clocks": clk}
     if not args.no_plain:
         line["plain"] = plain_kernel(eng, tri, ti, stream)
+    if not args.no_serving:
+        line["serving"] = serving_run(args.serve_seconds)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(edges)
     print(json.dumps(line), flush=True)
@@ -335,6 +354,137 @@ def plain_kernel(eng, tri, ti, stream):
     return {"value": n / (ms / 1e3), "unit": "schemes/s",
             "kernel": "tc_real_schemes (specialised, one launch over materialised masks)",
             "n": n, "ms": ms, "hbm_bytes": n * 16}
+
+
+def job_base(seed, stream):
+    import tcurve_inputs as ti
+    m = (1 << 64) - 1
+    return ti.splitmix64_int(((seed & m) * 0x100000001B3 + stream) & m)
+
+
+def serving_run(seconds, degrees=(6, 7, 8, 9), per_degree=4, slots=8, seed=2027):
+    """Poisson stream of jobs on the continuous-batching server: d uniform in
+    `degrees`, 2^U(8,22) sign vectors per job (splitmix64 streams), resident
+    triangulations (table-driven kernels, nothing compiled) and histograms.
+    The arrival rate is 70 % of the capacity measured on a closed burst."""
+    import numpy as np
+    import torch
+
+    import paper_2604_09221_gb300 as eng
+    import tcurve_inputs as ti
+    from paper_2604_09221_gb300.serve import GpuExecutor, Job, Server, percentile
+    tris = [eng.Triangulation(d, e) for d in degrees
+            for e in ti.regular_triangulations(d, per_degree, seed=seed + d)]
+    ex = GpuExecutor(tris, slots=slots, kernel=eng.TS_KERNEL_TABLE)
+    rng = np.random.default_rng(seed)
+
+    def draw():
+        return Job(tri=int(rng.integers(0, len(tris))), n=int(2 ** rng.uniform(8, 22)),
+                   base=int(rng.integers(0, 1 << 62)))
+
+    srv = Server(ex, slots=slots, mem_budget=1 << 32)
+    warm = [draw() for _ in range(2 * slots)]
+    for f in [srv.submit(j) for j in warm]:
+        f.result()
+    burst = [draw() for _ in range(64)]
+    t0 = time.perf_counter()
+    for f in [srv.submit(j) for j in burst]:
+        f.result()
+    cap_jobs = len(burst) / (time.perf_counter() - t0)
+    rate = 0.7 * cap_jobs
+    srv.completed.clear()
+    jobs, futs = [], []
+    t_start = time.perf_counter()
+    t_next = t_start
+    while t_next - t_start < seconds:
+        now = time.perf_counter()
+        if now < t_next:
+            time.sleep(min(t_next - now, 0.002))
+            continue
+        j = draw()
+        jobs.append(j)
+        futs.append(srv.submit(j))
+        t_next += rng.exponential(1.0 / rate)
+    res = [f.result() for f in futs]
+    wall = time.perf_counter() - t_start
+    srv.close()
+    torch.cuda.synchronize()
+    lat = [r.latency * 1e3 for r in res]
+    inst = sum(j.n for j in jobs)
+    return {"jobs": len(jobs), "arrival_rate_jobs_per_s": rate, "capacity_jobs_per_s": cap_jobs,
+            "p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99),
+            "mean_queue_ms": 1e3 * sum(r.queued for r in res) / len(res),
+            "schemes_per_s": inst / wall, "slots": slots, "degrees": list(degrees),
+            "sign_vectors_per_job": "2^U(8,22)", "kernel": "table-driven (resident, uncompiled)",
+            "peak_running": srv.peak_running, "seconds": wall}
+
+
+def serving_workload(args, seconds):
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2604_09221_gb300 import build as _b
+    _b.build()
+    r = serving_run(seconds)
+    line = {"metric": "serving: p50/p99 job latency and schemes/s (d in 6..9)",
+            "value": r["p99_ms"], "unit": "ms (p99 job latency)", "n_gpus": 1,
+            "higher_is_better": False, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "serving_poisson", "degrees": r["degrees"],
+                       "sign_vectors_per_job": r["sign_vectors_per_job"]},
+            "serving": r}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def mixed_workload(args, degrees=(5, 6, 7, 8, 9), per_degree=32, seed=31):
+    """The mixed-degree batch as one CUDA-graph launch per step."""
+    import numpy as np
+    import torch
+
+    import paper_2604_09221_gb300 as eng
+    import tcurve_inputs as ti
+    from paper_2604_09221_gb300 import autotune
+    from paper_2604_09221_gb300 import build as _b
+    torch.cuda.set_device(0)
+    _b.build()
+    rng = np.random.default_rng(seed)
+    tris, counts, bases = [], [], []
+    for d in degrees:
+        for k, e in enumerate(ti.regular_triangulations(d, per_degree, seed=seed + d)):
+            tris.append(eng.Triangulation(d, e))
+            counts.append(int(2 ** rng.uniform(10, 24)))
+            bases.append(job_base(seed * 100 + d, k))
+    tiles = autotune.autotune(tris, counts, bases, cache=os.path.join(ROOT, "gpurun_out", "tiles.json")
+                              if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None, reps=1)
+    batch = eng.Batch(tris, counts, bases)
+    autotune.apply(batch, tiles)
+    for _ in range(max(args.warmup, 1)):
+        batch.run(graph=True)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.steps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        batch.run(graph=True)
+        b.record()
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    for j in range(len(tris)):
+        codes, cnt, failed = batch.read(j)
+        assert failed == 0 and int(cnt.sum()) == counts[j]
+    ms = sum(times) / len(times)
+    total = sum(counts)
+    line = {"metric": "mixed-degree batch: schemes/s (one CUDA graph launch per step)",
+            "value": total / (ms / 1e3), "unit": "schemes/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": "mixed_degree_batch", "degrees": list(degrees),
+                       "triangulations_per_degree": per_degree, "jobs": len(tris),
+                       "sign_vectors": total, "counts": "2^U(10,24) per triangulation",
+                       "tiles": {str(d): list(t) for d, t in tiles.items()}},
+            "gpu_launches": len(degrees) * args.steps}
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 if __name__ == "__main__":
