@@ -234,8 +234,9 @@ class Histogram:
 
 
 class Batch:
-    """Mixed-degree batch (ts_batch): job j classifies counts[j] sign vectors
-    splitmix64(bases[j] + i) of tris[j]; see include/tcurve.h."""
+    """Mixed-degree batch (ts_batch): job j classifies the counts[j] sign
+    vectors of splitmix64 counters bases[j] + i of tris[j]; see
+    include/tcurve.h."""
 
     def __init__(self, tris, counts, bases, code_outputs=None, hist_capacity: int = 1024):
         n = len(tris)
@@ -274,9 +275,11 @@ class Batch:
         _check(_lib.ts_batch_run(self._h, int(bool(graph)), _stream_handle(stream)), "ts_batch_run")
 
     def read(self, job: int, stream=None):
-        """(codes (n,) uint64, counts (n,) uint64, failed) of one job, sorted by code."""
+        """(codes, counts (n,) uint64, failed) of one job, sorted by code; codes
+        has shape (n,) for one code word, (n, code_words) otherwise."""
         cap = self.capacity
-        codes = np.zeros(cap, dtype=np.uint64)
+        cw = self.tris[job].code_words
+        codes = np.zeros(cap if cw == 1 else (cap, cw), dtype=np.uint64)
         counts = np.zeros(cap, dtype=np.uint64)
         n = ctypes.c_uint64()
         nf = ctypes.c_uint64()
@@ -311,10 +314,13 @@ def specialized_source(d: int, edges, compile: bool = False) -> str:
 
 
 def splitmix_masks(d: int, base: int, n: int, out=None, stream=None):
-    """Device sign vectors splitmix64(base + i) cut to |A| bits (int64 tensor)."""
+    """Device sign vectors of the splitmix64 counters base .. base+n-1 (word w
+    of counter k is splitmix64(k * W + w), cut to |A| bits): an int64 tensor
+    of shape (n,) for one sign word, (n, W) otherwise."""
     import torch
     if out is None:
-        out = torch.empty(n, dtype=torch.int64, device="cuda")
+        W = ((d + 1) * (d + 2) // 2 + 63) // 64
+        out = torch.empty(n if W == 1 else (n, W), dtype=torch.int64, device="cuda")
     _check(_load().ts_splitmix_masks(int(d), int(base) & ((1 << 64) - 1), int(n), out.data_ptr(),
                                      _stream_handle(stream)), "ts_splitmix_masks")
     return out

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libtcurve.so")
 SOURCES = ["host.cpp", "kernels.cu", "jit.cpp", "noalloc.cu", "batch.cu"]
-HEADERS = ["engine.h", "tc_layout.h", "tc_runtime.cuh", "jit_kernels.cuh",
+HEADERS = ["engine.h", "tc_layout.h", "tc_runtime.cuh", "tc_table_sweep.cuh", "jit_kernels.cuh",
            os.path.join("..", "..", "include", "tcurve.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

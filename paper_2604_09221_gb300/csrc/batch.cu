@@ -21,32 +21,32 @@
 
 #include "engine.h"
 #include "tc_layout.h"
-#include "tc_runtime.cuh"
+#include "tc_table_sweep.cuh"
 
 namespace tcurve {
 namespace {
 
 constexpr long kWaitIters = 1L << 22;
 
+// Largest table of degree d: 2V + |E(T^diamond)| words, V = 2d^2 + 2d + 1 and
+// |E(T^diamond)| = 6d^2 + 2d, padded to 16 bytes.
+constexpr size_t max_table_bytes(int d) {
+  return (size_t)(((10 * d * d + 6 * d + 2) + 3) & ~3) * 4;
+}
+
 template <int D_, int T_>
-struct JobK {
-  static constexpr TcLayout L = tc_layout(D_, true, T_);
-  static constexpr u32 D = D_, V = L.V, NPOINTS = (D_ + 1) * (D_ + 2) / 2, RMAX = L.rmax,
-                       NB = L.nb, THREADS = T_, HASH = 1, LBYTES = L.lbytes, CODE64 = L.code64,
-                       PCAP = L.pcap, WODD = L.wodd, WORDS = L.words, OFF_LPAR = L.off_lpar,
-                       OFF_CAND = L.off_cand, OFF_LAB = L.off_lab, OFF_BPAIR = L.off_bpair,
-                       OFF_PEND = L.off_pend, OFF_ADJ = L.off_adj, OFF_RLAB = L.off_rlab,
-                       OFF_TPAR = L.off_tpar, OFF_ORDER = L.off_order, OFF_CLEN = L.off_clen,
-                       OFF_ODD = L.off_odd, OFF_CODE = L.off_code;
-  static constexpr bool fits = L.ok && (size_t)WORDS * 4 * T_ + 4096 + 256 <= 220 * 1024;
+struct JobK : TcTableK<D_, T_, true> {
+  static constexpr bool fits =
+      JobK::L.ok && (max_table_bytes(D_) + 127) / 128 * 128 + 128 + (size_t)JobK::WORDS * 4 * T_ <=
+                        227 * 1024;
 };
 
 struct DevJob {
   const u32 *tab;
   u64 n;              // sign vectors
   u64 base;           // splitmix64 counter base of the sign vectors
-  u64 *codes;         // per-instance codes (or null)
-  u64 *hkeys;         // job histogram (open addressing, 0 = empty)
+  u64 *codes;         // per-instance codes, code_words each (or null)
+  u64 *hkeys;         // job histogram (open addressing, code_words per key, 0 = empty)
   unsigned long long *hcnt;
   u64 hslots;
   u64 chunk0;         // first work item of the job
@@ -54,68 +54,6 @@ struct DevJob {
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ u32 sign_bit(u64 sigma, u32 k, u32 c) {
-  return ((u32)(sigma >> k) & 1u) ^ c;
-}
-
-// The table-driven sweep of kernels.cu, over tables in shared memory.
-template <class K>
-__device__ u64 classify_job(u64 sigma, const u32 *__restrict__ tab, u32 off_fan, u32 off_vext,
-                            const TcScratch<K> &S, u32 &err) {
-  const u32 *vdesc = tab;
-  const u32 *fan = tab + off_fan;
-  const u32 *vext = tab + off_vext;
-  u32 nl = 0, nb = 0, np = 0;
-  tc_clear_odd(S);
-  for (u32 v = 0; v < K::V; ++v) {
-    const u32 desc = vdesc[v];
-    const u32 sv = sign_bit(sigma, desc & 63u, (desc >> 6) & 1u);
-    const u32 m = (desc >> 7) & 63u, fs = desc >> 16;
-    if (np + m + 1 > K::PCAP) {
-      tc_unions(S, np);
-      np = 0;
-    }
-    u32 lv = 0, l0 = TcScratch<K>::NONE, any = 0, prev = 0;
-    for (u32 i = 0; i < m; ++i) {
-      const u32 f = fan[fs + i];
-      const u32 lu = *S.lab(K::OFF_LAB, f & 255u);
-      const u32 e = sign_bit(sigma, (f >> 8) & 63u, (f >> 14) & 1u) ^ sv ^ 1u;
-      const u32 st = e & ~(((f >> 15) & 1u) & prev) & 1u;
-      l0 = i == 0 ? lu : l0;
-      S.word(K::OFF_PEND, np) = lv | (lu << 16);
-      np += st & any;
-      lv = any ? lv : (st ? lu : lv);
-      any |= st;
-      prev = e;
-    }
-    if (!any) {
-      lv = nl;
-      tc_newlab(S, nl, l0);
-      ++nl;
-    }
-    *S.lab(K::OFF_LAB, v) = (typename TcScratch<K>::lab_t)lv;
-    const u32 x = vext[v];
-    if ((x & 255u) != 255u) {
-      S.word(K::OFF_PEND, np) = (u32)*S.lab(K::OFF_LAB, x & 255u) | (lv << 16) | 0x80000000u;
-      ++np;
-    }
-    if (K::D % 2) {
-#pragma unroll
-      for (u32 sh = 8; sh <= 16; sh += 8) {
-        const u32 b = (x >> sh) & 255u;
-        if (b == 255u) continue;
-        const u32 db = vdesc[b];
-        if (sign_bit(sigma, db & 63u, (db >> 6) & 1u) != sv) {
-          tc_bpair(S, nb, *S.lab(K::OFF_LAB, b), lv);
-          ++nb;
-        }
-      }
-    }
-  }
-  tc_unions(S, np);
-  return tc_backend(S, nl, nb, err);
 }
 
 template <int D, int T>
@@ -136,7 +74,6 @@ __global__ void __launch_bounds__(T)
   }
   __syncthreads();
   const u32 lane = threadIdx.x & 31u;
-  const u64 valid = K::NPOINTS >= 64 ? ~0ull : ((1ull << (K::NPOINTS & 63)) - 1);
   u32 cur = 0xFFFFFFFFu, phase = 0, err = 0;
   unsigned long long failed = 0;
   for (;;) {
@@ -188,15 +125,30 @@ __global__ void __launch_bounds__(T)
     const u64 first = (c - J.chunk0) * (u64)chunk;
     for (u32 k = 0; k < chunk; k += T) {
       const u64 idx = first + k + threadIdx.x;
-      u64 key = 0;
+      TcCodeOut<K> key{};
       if (idx < J.n) {
-        key = classify_job<K>(tc_splitmix64(J.base + idx) & valid, tab, off_fan, off_vext, S, err);
-        failed += key == 0;
-        if (J.codes) J.codes[idx] = key;
+        // the sign vector of counter base + idx, as ts_splitmix_masks writes it
+        TcSig<K::W> sg;
+#pragma unroll
+        for (u32 w = 0; w < K::W; ++w) sg.w[w] = tc_splitmix64((J.base + idx) * K::W + w);
+        sg.w[K::W - 1] &= tc_top_mask(K::NPOINTS, K::W);
+        key = tc_table_classify<K>(sg, tab, off_fan, off_vext, S, err);
+        u64 any = 0;
+#pragma unroll
+        for (u32 w = 0; w < K::CW; ++w) {
+          any |= key.w[w];
+          if (J.codes) J.codes[idx * K::CW + w] = key.w[w];
+        }
+        failed += any == 0;
       }
-      const unsigned peers = __match_any_sync(0xffffffffu, key);
-      if (key != 0 && lane == (u32)(__ffs(peers) - 1))
-        tc_global_add(J.hkeys, J.hcnt, J.hslots, err_word, key, (unsigned long long)__popc(peers));
+      if constexpr (K::CW == 1) {
+        const unsigned peers = __match_any_sync(0xffffffffu, key.w[0]);
+        if (key.w[0] != 0 && lane == (u32)(__ffs(peers) - 1))
+          tc_global_add(J.hkeys, J.hcnt, J.hslots, err_word, key.w[0],
+                        (unsigned long long)__popc(peers));
+      } else {
+        tc_hist_add_wide<K::CW>(key.w, J.hkeys, J.hcnt, J.hslots, err_word);
+      }
     }
   }
   if (err) atomicOr(err_word, err);
@@ -237,6 +189,13 @@ JobsFn jobs_fn_dt(int d, int t) {
     case 7: return jobs_fn_t<7>(t);
     case 8: return jobs_fn_t<8>(t);
     case 9: return jobs_fn_t<9>(t);
+    case 10: return jobs_fn_t<10>(t);
+    case 11: return jobs_fn_t<11>(t);
+    case 12: return jobs_fn_t<12>(t);
+    case 13: return jobs_fn_t<13>(t);
+    case 14: return jobs_fn_t<14>(t);
+    case 15: return jobs_fn_t<15>(t);
+    case 16: return jobs_fn_t<16>(t);
     default: return nullptr;
   }
 }
@@ -268,10 +227,12 @@ struct ts_batch {
     cudaEvent_t done = nullptr;
   };
   std::vector<DevJob> jobs;  // host copies (chunk0 per group)
-  std::vector<int> degree;
+  std::vector<int> degree, cws;       // degree and code words of every job
+  std::vector<size_t> kofs;           // first key word of every job's histogram
+  size_t key_words = 0;
   std::vector<Group> groups;
   uint64_t hslots = 0;
-  uint64_t *d_keys = nullptr;  // njobs x hslots
+  uint64_t *d_keys = nullptr;  // per job: hslots x code_words
   unsigned long long *d_counts = nullptr;
   uint32_t *d_err = nullptr;
   unsigned long long *d_failed = nullptr;
@@ -325,7 +286,7 @@ cudaError_t launch_group(ts_batch *b, ts_batch::Group &g, cudaStream_t st) {
 // The whole batch as stream work on `st`: clear, fork, one kernel per degree, join.
 cudaError_t enqueue(ts_batch *b, cudaStream_t st) {
   const size_t nj = b->jobs.size();
-  cudaError_t e = cudaMemsetAsync(b->d_keys, 0, nj * b->hslots * 8, st);
+  cudaError_t e = cudaMemsetAsync(b->d_keys, 0, b->key_words * 8, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counts, 0, nj * b->hslots * 8, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, 4, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_failed, 0, 8, st);
@@ -356,7 +317,16 @@ ts_status ts_batch_create(int njobs, ts_tri *const *tris, const uint64_t *counts
   while (s < 2 * hist_capacity) s <<= 1;
   b->hslots = s;
   cudaError_t e = cudaGetDevice(&b->device);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_keys, (size_t)njobs * s * 8);
+  for (int j = 0; j < njobs; ++j) {
+    if (!tris[j]) {
+      ts_batch_free(b);
+      return TS_EINVAL;
+    }
+    b->kofs.push_back(b->key_words);
+    b->cws.push_back(tris[j]->cw);
+    b->key_words += s * tris[j]->cw;
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_keys, b->key_words * 8);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_counts, (size_t)njobs * s * 8);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_err, 4);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_failed, 8);
@@ -364,7 +334,7 @@ ts_status ts_batch_create(int njobs, ts_tri *const *tris, const uint64_t *counts
   std::map<int, int> gi;
   for (int j = 0; j < njobs && e == cudaSuccess; ++j) {
     const ts_tri *t = tris[j];
-    if (!t || t->cw != 1 || t->np > 64 || t->device != b->device) {
+    if (t->device != b->device) {
       ts_batch_free(b);
       return TS_EINVAL;
     }
@@ -373,7 +343,7 @@ ts_status ts_batch_create(int njobs, ts_tri *const *tris, const uint64_t *counts
     x.n = counts[j];
     x.base = bases[j];
     x.codes = code_outputs ? reinterpret_cast<u64 *>(code_outputs[j]) : nullptr;
-    x.hkeys = reinterpret_cast<u64 *>(b->d_keys + (size_t)j * s);
+    x.hkeys = reinterpret_cast<u64 *>(b->d_keys + b->kofs[j]);
     x.hcnt = b->d_counts + (size_t)j * s;
     x.hslots = s;
     b->jobs.push_back(x);
@@ -386,6 +356,7 @@ ts_status ts_batch_create(int njobs, ts_tri *const *tris, const uint64_t *counts
       g.off_fan = t->lay.off_fan;
       g.off_vext = t->lay.off_vext;
       g.threads = t->d >= 8 ? 64 : 128;
+      while (g.threads > 32 && !jobs_fn_dt(t->d, g.threads)) g.threads -= 32;
       g.chunk = g.threads * 8;
       b->groups.push_back(g);
     }
@@ -465,29 +436,37 @@ ts_status ts_batch_read(ts_batch *b, int job, uint64_t *codes, uint64_t *counts,
   if (!b || !n_out || job < 0 || job >= (int)b->jobs.size() || (cap && (!codes || !counts)))
     return TS_EINVAL;
   cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
-  std::vector<uint64_t> k(b->hslots);
+  const int cw = b->cws[job];
+  std::vector<uint64_t> k(b->hslots * cw);
   std::vector<unsigned long long> c(b->hslots);
   uint32_t err = 0;
   unsigned long long failed = 0;
   if (e == cudaSuccess)
-    e = cudaMemcpy(k.data(), b->d_keys + (size_t)job * b->hslots, b->hslots * 8, cudaMemcpyDeviceToHost);
+    e = cudaMemcpy(k.data(), b->d_keys + b->kofs[job], k.size() * 8, cudaMemcpyDeviceToHost);
   if (e == cudaSuccess)
     e = cudaMemcpy(c.data(), b->d_counts + (size_t)job * b->hslots, b->hslots * 8,
                    cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemcpy(&err, b->d_err, 4, cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemcpy(&failed, b->d_failed, 8, cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_st(e);
-  std::vector<std::pair<uint64_t, uint64_t>> v;
-  for (uint64_t s = 0; s < b->hslots; ++s)
-    if (k[s]) v.push_back({k[s], c[s]});
-  std::sort(v.begin(), v.end());
-  *n_out = v.size();
-  if (n_failed) *n_failed = failed;
-  for (uint64_t i = 0; i < v.size() && i < cap; ++i) {
-    codes[i] = v[i].first;
-    counts[i] = v[i].second;
+  std::vector<uint64_t> idx;
+  for (uint64_t s = 0; s < b->hslots; ++s) {
+    bool nz = false;
+    for (int w = 0; w < cw; ++w) nz |= k[s * cw + w] != 0;
+    if (nz) idx.push_back(s);
   }
-  if (v.size() > cap) return TS_EOVERFLOW;
+  std::sort(idx.begin(), idx.end(), [&](uint64_t a, uint64_t x) {
+    for (int w = cw - 1; w >= 0; --w)
+      if (k[a * cw + w] != k[x * cw + w]) return k[a * cw + w] < k[x * cw + w];
+    return false;
+  });
+  *n_out = idx.size();
+  if (n_failed) *n_failed = failed;
+  for (uint64_t i = 0; i < idx.size() && i < cap; ++i) {
+    for (int w = 0; w < cw; ++w) codes[i * cw + w] = k[idx[i] * cw + w];
+    counts[i] = c[idx[i]] & kCountMask;
+  }
+  if (idx.size() > cap) return TS_EOVERFLOW;
   if (err & kErrTimeout) return TS_ETIMEOUT;
   if (err & kErrOverflow) return TS_EOVERFLOW;
   if (err & kErrInternal) return TS_EINTERNAL;

@@ -14,18 +14,16 @@
 
 namespace tcurve {
 
-constexpr int kMaxDegree = 9;  // single-word sign masks, 8-bit vertex ids
+constexpr int kMaxDegree = 16;     // |A| <= 153: three sign words, four code words
+constexpr int kMaxSpecialized = 9;  // triangulation-specialised kernels: one sign word
 
-// Table layout (32-bit words, all indices are vertex positions in the sweep
-// order of T^diamond, see host.cpp):
-//   vdesc[V]  bits 0-5 lattice index k(v), bit 6 parity constant c(v)
-//             (sign(v) = sigma_k ^ c, Eq. 2), bits 7-12 fan length m,
-//             bits 16-31 first fan entry
-//   fan[NF]   bits 0-7 neighbour u, bits 8-13 k(u), bit 14 c(u),
-//             bit 15 "u and the previous entry span a triangle with v"
-//   vext[V]   bits 0-7 the antipodal partner x < v of v (0xFF: none), bits
-//             8-15 and 16-23 the other end b < v of up to two boundary edges
-//             kept for root detection (0xFF: none)
+// Count words of multi-word histograms carry two flags in their top bits
+// (slot being written / key published); the count is the rest.
+constexpr uint64_t kCountMask = (1ull << 62) - 1;
+
+// Triangulation tables (32-bit words, format in tc_table_sweep.cuh): vdesc[V],
+// fan[NF], vext[V] at the offsets below, vertex ids in the sweep order of
+// T^diamond (host.cpp).
 struct TableLayout {
   uint32_t V, NF;
   uint32_t off_vdesc, off_fan, off_vext;

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "engine.h"
+#include "tc_layout.h"
 
 using namespace tcurve;
 
@@ -174,28 +175,32 @@ bool build_diamond(int d, const std::vector<std::array<Pt, 3>> &tris, Diamond &D
 }
 
 // Pack the diamond into the tables the table-driven kernels stage into
-// shared memory (layout in engine.h).
+// shared memory (format in tc_table_sweep.cuh).  Returns false if a field
+// does not fit: a vertex id (10 bits), a fan longer than the join list of
+// the kernels takes (tc_pcap), or a fan start beyond 16 bits.
 bool pack_tables(const Diamond &D, ts_tri *t) {
   const int V = D.V;
-  if (V > 255) return false;
-  std::vector<uint32_t> vdesc(V), fan, vext(V, 0xFFFFFFu);
+  constexpr uint32_t kNone = 1023u;
+  if (V > (int)kNone) return false;
+  std::vector<uint32_t> vdesc(V), fan, vext(V, kNone | (kNone << 10) | (kNone << 20));
   for (int v = 0; v < V; ++v) {
-    if (D.fan[v].size() > 63 || fan.size() > 65535) return false;
-    vdesc[v] = (uint32_t)D.k[v] | ((uint32_t)D.c[v] << 6) | ((uint32_t)D.fan[v].size() << 7) |
+    const int m = (int)D.fan[v].size();
+    if (m > 127 || m + 1 > tc_pcap(D.d) || fan.size() > 65535 || D.k[v] > 255) return false;
+    vdesc[v] = (uint32_t)D.k[v] | ((uint32_t)D.c[v] << 8) | ((uint32_t)m << 9) |
                ((uint32_t)fan.size() << 16);
-    for (size_t n = 0; n < D.fan[v].size(); ++n) {
+    for (int n = 0; n < m; ++n) {
       int u = D.fan[v][n];
-      fan.push_back((uint32_t)u | ((uint32_t)D.k[u] << 8) | ((uint32_t)D.c[u] << 14) |
-                    ((uint32_t)D.link[v][n] << 15));
+      fan.push_back((uint32_t)u | ((uint32_t)D.k[u] << 10) | ((uint32_t)D.c[u] << 18) |
+                    ((uint32_t)D.link[v][n] << 19));
     }
   }
-  for (auto &p : D.anti) vext[p.second] = (vext[p.second] & ~0xFFu) | (uint32_t)p.first;
+  for (auto &p : D.anti) vext[p.second] = (vext[p.second] & ~kNone) | (uint32_t)p.first;
   if (D.d % 2) {
     for (auto &e : D.bedge) {
       const int late = std::max(e.first, e.second), early = std::min(e.first, e.second);
       uint32_t &w = vext[late];
-      if (((w >> 8) & 0xFFu) == 0xFFu) w = (w & ~0xFF00u) | ((uint32_t)early << 8);
-      else if (((w >> 16) & 0xFFu) == 0xFFu) w = (w & ~0xFF0000u) | ((uint32_t)early << 16);
+      if (((w >> 10) & kNone) == kNone) w = (w & ~(kNone << 10)) | ((uint32_t)early << 10);
+      else if (((w >> 20) & kNone) == kNone) w = (w & ~(kNone << 20)) | ((uint32_t)early << 20);
       else return false;
     }
   }
@@ -322,7 +327,7 @@ namespace {
 // Kernel choice: the specialised kernel for sweeps and large batches (AUTO),
 // the table-driven kernel otherwise or when specialisation is unavailable.
 bool want_specialised(ts_tri *t, uint64_t n, bool sweep) {
-  if (t->kernel == TS_KERNEL_TABLE) return false;
+  if (t->kernel == TS_KERNEL_TABLE || t->d > kMaxSpecialized) return false;
   if (t->kernel == TS_KERNEL_SPECIALIZED) return true;
   if (!sweep && n < (1u << 16)) return false;
   return jit_prepare(t) == cudaSuccess;
@@ -341,12 +346,14 @@ ts_status ts_real_schemes(const ts_tri *tc, const uint64_t *signs, uint64_t n, u
 
 ts_status ts_set_kernel(ts_tri *t, int kind) {
   if (!t || kind < TS_KERNEL_AUTO || kind > TS_KERNEL_SPECIALIZED) return TS_EINVAL;
+  if (kind == TS_KERNEL_SPECIALIZED && t->d > kMaxSpecialized) return TS_EUNSUPPORTED;
   t->kernel = kind;
   return TS_OK;
 }
 
 ts_status ts_prepare(ts_tri *t) {
   if (!t) return TS_EINVAL;
+  if (t->d > kMaxSpecialized) return TS_EUNSUPPORTED;
   return cuda_status(jit_prepare(t));
 }
 
@@ -362,7 +369,7 @@ ts_status ts_specialized_log(const ts_tri *t, char *buf, size_t len) {
 ts_status ts_specialized_source(int d, const int32_t *edges_ij, int n_edges, int compile, char *buf,
                                 size_t len, size_t *needed) {
   if ((!edges_ij && n_edges > 0) || n_edges < 0 || d < 1 || (len && !buf)) return TS_EINVAL;
-  if (d > kMaxDegree) return TS_EUNSUPPORTED;
+  if (d > kMaxSpecialized) return TS_EUNSUPPORTED;
   std::vector<std::array<Pt, 3>> tris;
   if (!triangles_of(d, edges_ij, n_edges, tris)) return TS_ENOTTRI;
   Diamond D;
@@ -470,7 +477,6 @@ ts_status ts_enumerate(const ts_tri *t, uint64_t lo, uint64_t hi, uint32_t flags
   const uint32_t kinds = flags & (TS_ENUM_FLIP | TS_ENUM_REDUCED | TS_ENUM_SPLITMIX);
   if (!t || !h || hi < lo || (flags & ~kinds) || (kinds & (kinds - 1))) return TS_EINVAL;
   if (h->cw != t->cw) return TS_EINVAL;
-  if (t->np > 64) return TS_EUNSUPPORTED;
   int free_bits = t->np - ((flags & TS_ENUM_FLIP) ? 1 : 0) - ((flags & TS_ENUM_REDUCED) ? 3 : 0);
   if (!(flags & TS_ENUM_SPLITMIX) && free_bits < 64 && hi > (1ull << free_bits)) return TS_EINVAL;
   if (lo == hi) return TS_OK;
@@ -513,7 +519,7 @@ ts_status ts_hist_read(ts_hist *h, uint64_t *codes, uint64_t *counts, uint64_t c
   if (n_failed) *n_failed = failed;
   for (uint64_t r = 0; r < idx.size() && r < cap; ++r) {
     for (int w = 0; w < cw; ++w) codes[r * cw + w] = keys[idx[r] * cw + w];
-    counts[r] = cnt[idx[r]];
+    counts[r] = cnt[idx[r]] & kCountMask;
   }
   if (idx.size() > cap) return TS_EOVERFLOW;
   return err_word_status(err);

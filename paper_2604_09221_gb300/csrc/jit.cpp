@@ -295,6 +295,7 @@ std::string jit_compile_uncached(const std::string &src, std::string *log) {
 }
 
 cudaError_t jit_prepare(ts_tri *t) {
+  if (t->d > kMaxSpecialized) return cudaErrorNotSupported;
   std::lock_guard<std::mutex> g(t->jit_mu);
   if (t->jit) return cudaSuccess;
   Driver &dr = driver();

@@ -25,27 +25,15 @@
 
 #include "engine.h"
 #include "tc_layout.h"
-#include "tc_runtime.cuh"
+#include "tc_table_sweep.cuh"
 
 namespace tcurve {
 namespace {
 
 constexpr long kWaitIters = 1L << 22;  // bounded spin on the table mbarrier
 
-// Traits of the table-driven kernels of degree D (scratch with one label per
-// vertex, since the sweep is not unrolled).
-template <int D_>
-struct TableK {
-  static constexpr TcLayout L = tc_layout(D_, true, 256);
-  static constexpr u32 D = D_, V = L.V, NPOINTS = (D_ + 1) * (D_ + 2) / 2, RMAX = L.rmax,
-                       NB = L.nb, THREADS = L.threads, HASH = L.hash, LBYTES = L.lbytes,
-                       CODE64 = L.code64, PCAP = L.pcap, WODD = L.wodd, WORDS = L.words,
-                       OFF_LPAR = L.off_lpar, OFF_CAND = L.off_cand, OFF_LAB = L.off_lab,
-                       OFF_BPAIR = L.off_bpair, OFF_PEND = L.off_pend, OFF_ADJ = L.off_adj,
-                       OFF_RLAB = L.off_rlab, OFF_TPAR = L.off_tpar, OFF_ORDER = L.off_order,
-                       OFF_CLEN = L.off_clen, OFF_ODD = L.off_odd, OFF_CODE = L.off_code;
-  static_assert(L.ok, "scratch layout");
-};
+template <int D>
+using TableK = TcTableK<D, 256, false>;
 
 // ---------------------------------------------------------------- PTX ----
 
@@ -105,71 +93,6 @@ __device__ bool stage_tables(uint32_t *stab, const uint32_t *gtab, uint32_t byte
   return true;
 }
 
-// ------------------------------------------------------------- sweep ----
-
-__device__ __forceinline__ u32 sign_bit(u64 sigma, u32 k, u32 c) {
-  return ((u32)(sigma >> k) & 1u) ^ c;
-}
-
-// Algorithm 1 for one sign vector; returns the code or 0 (err bits set).
-template <class K>
-__device__ u64 classify(u64 sigma, const u32 *__restrict__ tab, const TableLayout &L,
-                        const TcScratch<K> &S, u32 &err) {
-  const u32 *vdesc = tab + L.off_vdesc;
-  const u32 *fan = tab + L.off_fan;
-  const u32 *vext = tab + L.off_vext;
-  u32 nl = 0, nb = 0, np = 0;
-  tc_clear_odd(S);
-  for (u32 v = 0; v < K::V; ++v) {
-    const u32 desc = vdesc[v];
-    const u32 sv = sign_bit(sigma, desc & 63u, (desc >> 6) & 1u);
-    const u32 m = (desc >> 7) & 63u, fs = desc >> 16;
-    if (np + m + 1 > K::PCAP) {  // at most m - 1 run joins and one antipodal join at v
-      tc_unions(S, np);
-      np = 0;
-    }
-    u32 lv = 0, l0 = TcScratch<K>::NONE, any = 0, prev = 0;
-    for (u32 i = 0; i < m; ++i) {
-      const u32 f = fan[fs + i];
-      const u32 lu = *S.lab(K::OFF_LAB, f & 255u);
-      const u32 e = sign_bit(sigma, (f >> 8) & 63u, (f >> 14) & 1u) ^ sv ^ 1u;
-      const u32 st = e & ~(((f >> 15) & 1u) & prev) & 1u;  // e starts a run of the fan
-      l0 = i == 0 ? lu : l0;
-      // a run after the first: join its label with the vertex's label
-      S.word(K::OFF_PEND, np) = lv | (lu << 16);
-      np += st & any;
-      lv = any ? lv : (st ? lu : lv);
-      any |= st;
-      prev = e;
-    }
-    if (!any) {
-      lv = nl;
-      tc_newlab(S, nl, l0);
-      ++nl;
-    }
-    *S.lab(K::OFF_LAB, v) = (typename TcScratch<K>::lab_t)lv;
-    const u32 x = vext[v];
-    if ((x & 255u) != 255u) {  // the antipodal partner, reached earlier
-      S.word(K::OFF_PEND, np) = (u32)*S.lab(K::OFF_LAB, x & 255u) | (lv << 16) | 0x80000000u;
-      ++np;
-    }
-    if (K::D % 2) {  // crossed boundary edges, for the pseudoline's region
-#pragma unroll
-      for (u32 sh = 8; sh <= 16; sh += 8) {
-        const u32 b = (x >> sh) & 255u;
-        if (b == 255u) continue;
-        const u32 db = vdesc[b];
-        if (sign_bit(sigma, db & 63u, (db >> 6) & 1u) != sv) {
-          tc_bpair(S, nb, *S.lab(K::OFF_LAB, b), lv);
-          ++nb;
-        }
-      }
-    }
-  }
-  tc_unions(S, np);
-  return tc_backend(S, nl, nb, err);
-}
-
 template <class K>
 constexpr size_t smem_bytes(uint32_t table_words, bool with_hash) {
   return ((size_t)table_words * 4 + 127) / 128 * 128 + 128 + (size_t)K::WORDS * 4 * K::THREADS +
@@ -213,11 +136,14 @@ __global__ void __launch_bounds__(TableK<D>::THREADS)
   SmemLayout M = carve<K>(smem, L.words);
   if (!stage_tables(M.tab, gtab, L.words * 4, M.bar, err_word)) return;
   const TcScratch<K> S{M.scratch + threadIdx.x};
-  const uint64_t valid = K::NPOINTS >= 64 ? ~0ull : ((1ull << (K::NPOINTS & 63)) - 1);
+  const u64 *sg = reinterpret_cast<const u64 *>(signs);
   uint32_t err = 0;
   for (uint64_t i = (uint64_t)blockIdx.x * K::THREADS + threadIdx.x; i < n;
-       i += (uint64_t)gridDim.x * K::THREADS)
-    codes[i] = classify<K>(signs[i] & valid, M.tab, L, S, err);
+       i += (uint64_t)gridDim.x * K::THREADS) {
+    const TcCodeOut<K> c = tc_table_classify<K>(tc_load_sig<K>(sg, i), M.tab, L.off_fan, L.off_vext, S, err);
+#pragma unroll
+    for (u32 w = 0; w < K::CW; ++w) codes[i * K::CW + w] = c.w[w];
+  }
   if (err) atomicOr(err_word, err);
 }
 
@@ -247,13 +173,21 @@ __global__ void __launch_bounds__(TableK<D>::THREADS)
     if (base >= total) break;
     for (uint32_t j = 0; j < kChunk; j += K::THREADS) {
       const uint64_t idx = base + j + threadIdx.x;
-      uint64_t key = 0;
+      TcCodeOut<K> key{};
       if (idx < total) {
-        key = classify<K>(tc_enum_mask(lo + idx, flags, D), M.tab, L, S, err);
-        failed += key == 0;
+        key = tc_table_classify<K>(tc_enum_sig<K::W>(lo + idx, flags, D), M.tab, L.off_fan,
+                                   L.off_vext, S, err);
+        u64 any = 0;
+#pragma unroll
+        for (u32 w = 0; w < K::CW; ++w) any |= key.w[w];
+        failed += any == 0;
       }
-      tc_hist_add<K::HASH>(key, M.hkeys, M.hcnt, reinterpret_cast<u64 *>(h.d_keys), h.d_counts,
-                           h.slots, h.d_err);
+      if constexpr (K::CW == 1)
+        tc_hist_add<K::HASH>(key.w[0], M.hkeys, M.hcnt, reinterpret_cast<u64 *>(h.d_keys),
+                             h.d_counts, h.slots, h.d_err);
+      else
+        tc_hist_add_wide<K::CW>(key.w, reinterpret_cast<u64 *>(h.d_keys), h.d_counts, h.slots,
+                                h.d_err);
     }
   }
   __syncthreads();
@@ -265,12 +199,17 @@ __global__ void __launch_bounds__(TableK<D>::THREADS)
   if (failed) atomicAdd(h.d_failed, failed);
 }
 
-// Sign vectors splitmix64(base + i), cut to npoints bits (input generation).
+// Word w of sign vector i is splitmix64((base + i) * W + w); the top word is
+// cut to the |A| - 64 (W - 1) bits that exist.
 __global__ void splitmix_masks_kernel(uint64_t base, uint64_t n, uint32_t npoints, uint64_t *out) {
-  const uint64_t valid = npoints >= 64 ? ~0ull : ((1ull << npoints) - 1);
+  const uint32_t W = (npoints + 63) / 64;
+  const uint64_t top = tc_top_mask(npoints, W);
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (uint64_t)gridDim.x * blockDim.x)
-    out[i] = tc_splitmix64(base + i) & valid;
+    for (uint32_t w = 0; w < W; ++w) {
+      const uint64_t x = tc_splitmix64((base + i) * W + w);
+      out[i * W + w] = w + 1 == W ? x & top : x;
+    }
 }
 
 __global__ void hist_clear_kernel(ts_hist h) {
@@ -351,6 +290,13 @@ cudaError_t launch_real_schemes(const ts_tri *t, const uint64_t *signs, uint64_t
     case 7: return real_schemes_d<7>(t, signs, n, codes, st);
     case 8: return real_schemes_d<8>(t, signs, n, codes, st);
     case 9: return real_schemes_d<9>(t, signs, n, codes, st);
+    case 10: return real_schemes_d<10>(t, signs, n, codes, st);
+    case 11: return real_schemes_d<11>(t, signs, n, codes, st);
+    case 12: return real_schemes_d<12>(t, signs, n, codes, st);
+    case 13: return real_schemes_d<13>(t, signs, n, codes, st);
+    case 14: return real_schemes_d<14>(t, signs, n, codes, st);
+    case 15: return real_schemes_d<15>(t, signs, n, codes, st);
+    case 16: return real_schemes_d<16>(t, signs, n, codes, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -367,6 +313,13 @@ cudaError_t launch_enumerate(const ts_tri *t, uint64_t lo, uint64_t hi, uint32_t
     case 7: return enumerate_d<7>(t, lo, hi, flags, h, st);
     case 8: return enumerate_d<8>(t, lo, hi, flags, h, st);
     case 9: return enumerate_d<9>(t, lo, hi, flags, h, st);
+    case 10: return enumerate_d<10>(t, lo, hi, flags, h, st);
+    case 11: return enumerate_d<11>(t, lo, hi, flags, h, st);
+    case 12: return enumerate_d<12>(t, lo, hi, flags, h, st);
+    case 13: return enumerate_d<13>(t, lo, hi, flags, h, st);
+    case 14: return enumerate_d<14>(t, lo, hi, flags, h, st);
+    case 15: return enumerate_d<15>(t, lo, hi, flags, h, st);
+    case 16: return enumerate_d<16>(t, lo, hi, flags, h, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -41,6 +41,7 @@ struct TcLab<2> {
 
 constexpr u32 TC_ERR_INTERNAL = 1u;
 constexpr u32 TC_ERR_OVERFLOW = 2u;
+constexpr u32 TC_ERR_TIMEOUT = 4u;
 
 template <class K>
 struct TcScratch {
@@ -55,6 +56,9 @@ struct TcScratch {
   }
   __device__ __forceinline__ u8 *byte(u32 off, u32 i) const {
     return reinterpret_cast<u8 *>(w + (off + (i >> 2)) * K::THREADS) + (i & 3u);
+  }
+  __device__ __forceinline__ u16 *half(u32 off, u32 i) const {
+    return reinterpret_cast<u16 *>(w + (off + (i >> 1)) * K::THREADS) + (i & 1u);
   }
   __device__ __forceinline__ u32 &word(u32 off, u32 i) const { return w[(off + i) * K::THREADS]; }
   __device__ __forceinline__ u32 lpar(u32 i) const { return *lab(K::OFF_LPAR, i); }
@@ -324,6 +328,242 @@ __device__ __noinline__ u64 tc_backend(const TcScratch<K> &S, u32 nl, u32 nb, u3
   return (1ull << nbits) | (nbits ? (u64)(bits >> (BITS - nbits)) : 0ull);
 }
 
+// ------------------------------------------------- wide back end (d >= 10) --
+//
+// Up to 107 regions and 213-bit codes.  The region tree is built as in
+// tc_backend, then re-rooted by reversing the parent links on the path from
+// the root to region 0, and stored as first-child / next-sibling bytes.  AHU
+// codes are produced in post order without a stack (parent and sibling links
+// give the next node).  When a node is finished, the codes of its non-leaf
+// children are the most recent entries of a packed bit arena (the codes of
+// disjoint finished subtrees, 2 * (R - 1) bits at most); they are written in
+// descending order behind a '1' into a build area, followed by '10' per leaf
+// child and a '0', and the result replaces them in the arena.  Bit strings
+// are MSB first: string bit p is bit 31 - p % 32 of word p / 32.
+
+template <class K>
+__device__ __forceinline__ u64 tc_get64(const TcScratch<K> &S, u32 off, u32 p) {
+  const u32 w = p >> 5, sh = p & 31u;
+  const u64 hi = ((u64)S.word(off, w) << 32) | S.word(off, w + 1);
+  return sh ? (hi << sh) | (S.word(off, w + 2) >> (32u - sh)) : hi;
+}
+
+// OR the 64-bit MSB-first chunk x into the bit string at position q.
+template <class K>
+__device__ __forceinline__ void tc_or64(const TcScratch<K> &S, u32 off, u32 q, u64 x) {
+  const u32 w = q >> 5, sh = q & 31u;
+  S.word(off, w) |= (u32)(x >> (32u + sh));
+  S.word(off, w + 1) |= (u32)(x >> sh);
+  if (sh) S.word(off, w + 2) |= (u32)(x << (32u - sh));
+}
+
+// Append n bits starting at position p of one string at position q of another.
+template <class K>
+__device__ __forceinline__ void tc_append(const TcScratch<K> &S, u32 src, u32 p, u32 n, u32 dst,
+                                          u32 q) {
+  for (u32 i = 0; i < n; i += 64) {
+    u64 x = tc_get64(S, src, p + i);
+    if (n - i < 64) x &= ~0ull << (64 - (n - i));
+    tc_or64(S, dst, q + i, x);
+  }
+}
+
+// Lexicographic comparison of two codes (prefix-free, so equal over the
+// shorter length means equal).
+template <class K>
+__device__ __forceinline__ int tc_cmp(const TcScratch<K> &S, u32 off, u32 pa, u32 la, u32 pb,
+                                      u32 lb) {
+  const u32 n = la < lb ? la : lb;
+  for (u32 i = 0; i < n; i += 64) {
+    u64 a = tc_get64(S, off, pa + i), b = tc_get64(S, off, pb + i);
+    if (n - i < 64) {
+      const u64 mk = ~0ull << (64 - (n - i));
+      a &= mk;
+      b &= mk;
+    }
+    if (a != b) return a > b ? 1 : -1;
+  }
+  return 0;
+}
+
+template <class K>
+__device__ __noinline__ void tc_backend_wide(const TcScratch<K> &S, u32 nl, u32 nb, u32 &err,
+                                             u64 *code) {
+  constexpr u32 NONE8 = 0xFFu, ENT_CAP = K::RMAX / 2 + 2, ABITS = 32 * (K::WARENA - 3);
+  typedef TcScratch<K> TS;
+#pragma unroll
+  for (u32 w = 0; w < K::CW; ++w) code[w] = 0;
+  // 1. region ids over lpar (label order), root flags, smallest labels
+  u32 R = 0, nodd = 0;
+  int root = -1;
+  for (u32 l = 0; l < nl; ++l) {
+    const u32 p = S.lpar(l) & TS::LOW;
+    const u32 is_root = p == l;
+    const u32 rp = S.lpar(p);
+    if (is_root) {
+      if (R >= K::RMAX) {
+        err |= TC_ERR_OVERFLOW;
+        return;
+      }
+      if (K::D % 2 == 0 && tc_odd(S, l)) {
+        ++nodd;
+        root = (int)R;
+      }
+      *S.half(K::OFF_RLAB, R) = (u16)l;
+    }
+    S.set_lpar(l, is_root ? R : rp);
+    R += is_root;
+  }
+  // 2. root
+  if (K::D % 2 == 0) {
+    if (nodd != 1) {
+      err |= TC_ERR_INTERNAL;
+      return;
+    }
+  } else {
+    for (u32 i = 0; i < nb; ++i) {
+      const u32 e = S.word(K::OFF_BPAIR, i);
+      const u32 ra = S.lpar(e & 0xFFFFu), rb = S.lpar(e >> 16);
+      if (ra != rb) continue;
+      if (root >= 0 && root != (int)ra) {
+        err |= TC_ERR_INTERNAL;
+        return;
+      }
+      root = (int)ra;
+    }
+    if (root < 0) {
+      err |= TC_ERR_INTERNAL;
+      return;
+    }
+  }
+  // 3. the tree hanging from region 0 (parent(r) < r), then re-rooted
+  *S.byte(K::OFF_WPAR, 0) = (u8)NONE8;
+  for (u32 r = 1; r < R; ++r) {
+    const u32 c = S.cand(*S.half(K::OFF_RLAB, r)) & TS::LOW;
+    if (c == TS::NONE) {
+      err |= TC_ERR_INTERNAL;
+      return;
+    }
+    const u32 p = S.lpar(c);
+    if (p >= r) {
+      err |= TC_ERR_INTERNAL;
+      return;
+    }
+    *S.byte(K::OFF_WPAR, r) = (u8)p;
+  }
+  for (u32 x = (u32)root, prev = NONE8, it = 0; it < R; ++it) {
+    const u32 nx = *S.byte(K::OFF_WPAR, x);
+    *S.byte(K::OFF_WPAR, x) = (u8)prev;
+    if (x == 0) break;
+    prev = x;
+    x = nx;
+  }
+  for (u32 r = 0; r < R; ++r) *S.byte(K::OFF_WFC, r) = (u8)NONE8;
+  for (u32 r = 0; r < R; ++r) {
+    const u32 p = *S.byte(K::OFF_WPAR, r);
+    if (p == NONE8) continue;
+    *S.byte(K::OFF_WNS, r) = *S.byte(K::OFF_WFC, p);
+    *S.byte(K::OFF_WFC, p) = (u8)r;
+  }
+  // 4. AHU in post order
+  u32 top = 0, aend = 0, qroot = 0;
+  u32 x = (u32)root;
+  for (u32 it = 0; it < R && *S.byte(K::OFF_WFC, x) != NONE8; ++it) x = *S.byte(K::OFF_WFC, x);
+  for (u32 it = 0; it < R; ++it) {
+    if (*S.byte(K::OFF_WFC, x) != NONE8) {
+      u32 k = 0, nleaf = 0;
+      for (u32 c = *S.byte(K::OFF_WFC, x); c != NONE8; c = *S.byte(K::OFF_WNS, c)) {
+        if (*S.byte(K::OFF_WFC, c) == NONE8) ++nleaf;
+        else ++k;
+      }
+      if (k > top || k > 63) {
+        err |= TC_ERR_INTERNAL;
+        return;
+      }
+      const u32 first = top - k;
+      const u32 start = k ? *S.half(K::OFF_WENT, first) : aend;
+      const bool is_root = x == (u32)root;
+#pragma unroll
+      for (u32 w = 0; w < K::WARENA; ++w) S.word(K::OFF_WTEMP, w) = 0;
+      u32 q = 0;
+      if (!is_root) {
+        tc_or64(S, K::OFF_WTEMP, 0, 1ull << 63);
+        q = 1;
+      }
+      u64 used = 0;
+      for (u32 s = 0; s < k; ++s) {
+        u32 best = 0, bp = 0, bl = 0;
+        bool have = false;
+        for (u32 i = 0; i < k; ++i) {
+          if ((used >> i) & 1ull) continue;
+          const u32 p = *S.half(K::OFF_WENT, first + i);
+          const u32 l = (first + i + 1 < top ? (u32)*S.half(K::OFF_WENT, first + i + 1) : aend) - p;
+          if (!have || tc_cmp(S, K::OFF_WARENA, p, l, bp, bl) > 0) {
+            best = i;
+            bp = p;
+            bl = l;
+            have = true;
+          }
+        }
+        used |= 1ull << best;
+        if (q + bl > ABITS) {
+          err |= TC_ERR_OVERFLOW;
+          return;
+        }
+        tc_append(S, K::OFF_WARENA, bp, bl, K::OFF_WTEMP, q);
+        q += bl;
+      }
+      if (q + 2 * nleaf + 1 > ABITS) {
+        err |= TC_ERR_OVERFLOW;
+        return;
+      }
+      for (u32 i = 0; i < nleaf; i += 32) {
+        const u32 m = nleaf - i < 32 ? nleaf - i : 32;
+        u64 pat = 0xAAAAAAAAAAAAAAAAull;
+        if (m < 32) pat &= ~0ull << (64 - 2 * m);
+        tc_or64(S, K::OFF_WTEMP, q, pat);
+        q += 2 * m;
+      }
+      if (is_root) {
+        qroot = q;
+        break;
+      }
+      q += 1;  // the closing '0'
+      if (start + q > ABITS || first >= ENT_CAP) {
+        err |= TC_ERR_OVERFLOW;
+        return;
+      }
+      // the children's codes are dead: overwrite them with the node's code
+      const u32 w0 = start >> 5, sh = start & 31u;
+      S.word(K::OFF_WARENA, w0) &= sh ? ~(0xFFFFFFFFu >> sh) : 0u;
+      for (u32 w = w0 + 1; w < K::WARENA; ++w) S.word(K::OFF_WARENA, w) = 0;
+      tc_append(S, K::OFF_WTEMP, 0, q, K::OFF_WARENA, start);
+      *S.half(K::OFF_WENT, first) = (u16)start;
+      top = first + 1;
+      aend = start + q;
+    }
+    if (x == (u32)root) break;
+    if (*S.byte(K::OFF_WNS, x) != NONE8) {
+      x = *S.byte(K::OFF_WNS, x);
+      for (u32 j = 0; j < R && *S.byte(K::OFF_WFC, x) != NONE8; ++j) x = *S.byte(K::OFF_WFC, x);
+    } else {
+      x = *S.byte(K::OFF_WPAR, x);
+    }
+  }
+  // 5. code = (1 << nbits) | bits, little-endian words
+  if (qroot != 2 * (R - 1) || qroot + 1 > 64 * K::CW) {
+    err |= TC_ERR_INTERNAL;
+    return;
+  }
+#pragma unroll
+  for (u32 j = 0; j < K::CW; ++j) {
+    const int hiend = (int)qroot - 64 * (int)j;  // end of this word's bits in the string
+    if (hiend >= 64) code[j] = tc_get64(S, K::OFF_WTEMP, (u32)(hiend - 64));
+    else if (hiend > 0) code[j] = tc_get64(S, K::OFF_WTEMP, 0) >> (64 - hiend);
+  }
+  code[qroot >> 6] |= 1ull << (qroot & 63u);
+}
+
 // ------------------------------------------------------------ histogram ----
 
 __device__ __forceinline__ u32 tc_hash_slot(u64 key, u64 mask) {
@@ -379,6 +619,96 @@ __device__ __forceinline__ u64 tc_splitmix64(u64 x) {
   return z ^ (z >> 31);
 }
 
+// Multi-word keys (d >= 10).  A slot's count word carries two flags: BUSY
+// while the inserting thread writes the key, READY once it is published
+// (keys: slots x CW words, zero = empty).
+constexpr u64 TC_SLOT_BUSY = 1ull << 62, TC_SLOT_READY = 1ull << 63;
+
+template <u32 CW>
+__device__ __forceinline__ u64 tc_key_hash(const u64 *key) {
+  u64 h = key[0];
+#pragma unroll
+  for (u32 w = 1; w < CW; ++w) h = (h ^ key[w]) * 0x9E3779B97F4A7C15ull + w;
+  return h;
+}
+
+template <u32 CW>
+__device__ void tc_global_add_wide(u64 *gkeys, unsigned long long *gcnt, u64 gslots, u32 *gerr,
+                                   const u64 *key, unsigned long long cnt) {
+  const u64 mask = gslots - 1;
+  u64 s = tc_hash_slot(tc_key_hash<CW>(key), mask);
+  for (u64 probe = 0; probe < gslots; ++probe) {
+    unsigned long long *cp = gcnt + s;
+    unsigned long long c = *reinterpret_cast<volatile unsigned long long *>(cp);
+    if (c == 0) {
+      c = atomicCAS(cp, 0ull, (unsigned long long)TC_SLOT_BUSY);
+      if (c == 0) {
+#pragma unroll
+        for (u32 w = 0; w < CW; ++w) gkeys[s * CW + w] = key[w];
+        __threadfence();
+        atomicAdd(cp, (unsigned long long)(TC_SLOT_READY - TC_SLOT_BUSY) + cnt);
+        return;
+      }
+    }
+    for (u32 it = 0; !(c & TC_SLOT_READY) && it < (1u << 20); ++it) {  // bounded wait
+      __nanosleep(64);
+      c = *reinterpret_cast<volatile unsigned long long *>(cp);
+    }
+    if (!(c & TC_SLOT_READY)) {
+      atomicOr(gerr, TC_ERR_TIMEOUT);
+      return;
+    }
+    __threadfence();
+    bool eq = true;
+#pragma unroll
+    for (u32 w = 0; w < CW; ++w)
+      eq &= *reinterpret_cast<volatile u64 *>(gkeys + s * CW + w) == key[w];
+    if (eq) {
+      atomicAdd(cp, cnt);
+      return;
+    }
+    s = (s + 1) & mask;
+  }
+  atomicOr(gerr, TC_ERR_OVERFLOW);
+}
+
+// Warp-aggregated insert of multi-word keys (all 32 lanes call it; an
+// all-zero key means "nothing to add").
+template <u32 CW>
+__device__ __forceinline__ void tc_hist_add_wide(const u64 *key, u64 *gkeys, unsigned long long *gcnt,
+                                                 u64 gslots, u32 *gerr) {
+  const u32 lane = threadIdx.x & 31u;
+  unsigned peers = 0xffffffffu;
+  bool nz = false;
+#pragma unroll
+  for (u32 w = 0; w < CW; ++w) {
+    peers &= __match_any_sync(0xffffffffu, key[w]);
+    nz |= key[w] != 0;
+  }
+  if (nz && lane == (u32)(__ffs(peers) - 1))
+    tc_global_add_wide<CW>(gkeys, gcnt, gslots, gerr, key, (unsigned long long)__popc(peers));
+}
+
+// ---------------------------------------------------------- sign vectors ----
+
+// A sign vector of W words (bit k of word k / 64 is sigma at lattice index k).
+template <u32 W>
+struct TcSig {
+  u64 w[W];
+  __device__ __forceinline__ u32 bit(u32 k) const {
+    u64 x = w[0];
+#pragma unroll
+    for (u32 i = 1; i < W; ++i) x = (k >> 6) == i ? w[i] : x;
+    return (u32)(x >> (k & 63u)) & 1u;
+  }
+};
+
+// Mask of the top word of a sign vector of np points.
+__device__ __forceinline__ u64 tc_top_mask(u32 np, u32 W) {
+  const u32 r = np - 64 * (W - 1);
+  return r >= 64 ? ~0ull : ((1ull << r) - 1);
+}
+
 // Enumeration masks (ts_enumerate flags): k, k << 1, k with zero bits
 // inserted at positions 0, 1 and d + 1, or splitmix64(k) cut to |A| bits.
 __device__ __forceinline__ u64 tc_enum_mask(u64 k, u32 flags, u32 d) {
@@ -389,4 +719,32 @@ __device__ __forceinline__ u64 tc_enum_mask(u64 k, u32 flags, u32 d) {
   if (flags & 1u) return k << 1;
   if (flags & 2u) return ((k & ((1ull << (d - 1)) - 1)) << 2) | ((k >> (d - 1)) << (d + 2));
   return k;
+}
+
+// Enumeration sign vectors of W words: as tc_enum_mask, with the bits that
+// leave the first word carried into the second; splitmix64 fills word w of
+// counter k with splitmix64(k * W + w).
+template <u32 W>
+__device__ __forceinline__ TcSig<W> tc_enum_sig(u64 k, u32 flags, u32 d) {
+  TcSig<W> s;
+  const u32 np = (d + 1) * (d + 2) / 2;
+  if (flags & 4u) {
+#pragma unroll
+    for (u32 w = 0; w < W; ++w) s.w[w] = tc_splitmix64(k * W + w);
+    s.w[W - 1] &= tc_top_mask(np, W);
+    return s;
+  }
+  u64 lo = k, hi = 0;
+  if (flags & 1u) {
+    lo = k << 1;
+    hi = k >> 63;
+  } else if (flags & 2u) {
+    const u64 h = k >> (d - 1);
+    lo = ((k & ((1ull << (d - 1)) - 1)) << 2) | (h << (d + 2));
+    hi = h >> (62 - d);
+  }
+  s.w[0] = lo;
+#pragma unroll
+  for (u32 w = 1; w < W; ++w) s.w[w] = w == 1 ? hi : 0ull;
+  return s;
 }

@@ -1,8 +1,8 @@
 """Continuous-batching job server on one GPU.
 
 A job asks for the real schemes of n sign vectors of one resident
-triangulation: the sign vectors are the splitmix64 stream base, base + 1, ...
-(cut to |A| bits).  The result is the job's histogram of schemes and, if the
+triangulation: the sign vectors of the splitmix64 counters base, base + 1, ...
+(word w of counter k is splitmix64(k * W + w), cut to |A| bits).  The result is the job's histogram of schemes and, if the
 job asks for it, the code of every sign vector.
 
 Jobs queue in arrival order.  The scheduler keeps up to ``slots`` jobs on the
@@ -35,13 +35,14 @@ class Job:
     n: int                   # sign vectors
     base: int                # splitmix64 counter of the first sign vector
     want_codes: bool = False
+    words: int = 2           # sign words + code words per sign vector (set by the server)
     submitted: float = 0.0
     admitted: float = 0.0
     finished: float = 0.0
     future: Future = field(default_factory=Future)
 
     def mem_bytes(self) -> int:
-        return 16 * self.n if self.want_codes else 0   # masks + codes, int64 each
+        return 8 * self.words * self.n if self.want_codes else 0   # masks + codes
 
 
 @dataclass
@@ -67,7 +68,9 @@ class GpuExecutor:
             for t in self.tris:
                 t.set_kernel(kernel)
         self.streams = [torch.cuda.Stream() for _ in range(slots)]
-        self.hists = [Histogram(hist_capacity, 1) for _ in range(slots)]
+        # one resident histogram per slot and code width (1 to 4 words)
+        cws = sorted({t.code_words for t in self.tris})
+        self.hists = [{cw: Histogram(hist_capacity, cw) for cw in cws} for _ in range(slots)]
         self.events = [torch.cuda.Event() for _ in range(slots)]
         self.buffers: Dict[int, tuple] = {}
 
@@ -76,17 +79,21 @@ class GpuExecutor:
         torch = self.torch
         st = self.streams[slot]
         tri = self.tris[job.tri]
-        h = self.hists[slot]
+        h = self.hists[slot][tri.code_words]
         with torch.cuda.stream(st):
             h.clear(st)
             enumerate_schemes(tri, job.base, job.base + job.n, h, TS_ENUM_SPLITMIX, stream=st)
             if job.want_codes:
-                masks = torch.empty(job.n, dtype=torch.int64, device="cuda")
-                codes = torch.empty((job.n, 1), dtype=torch.int64, device="cuda")
+                masks = torch.empty((job.n, tri.sign_words), dtype=torch.int64, device="cuda")
+                codes = torch.empty((job.n, tri.code_words), dtype=torch.int64, device="cuda")
                 splitmix_masks(tri.d, job.base, job.n, masks, stream=st)
                 tri.real_schemes(masks, out=codes, stream=st, sync=False)
                 self.buffers[slot] = (masks, codes)
             self.events[slot].record(st)
+
+    def words(self, job: Job) -> int:
+        t = self.tris[job.tri]
+        return t.sign_words + t.code_words
 
     def done(self, slot: int) -> bool:
         return self.events[slot].query()
@@ -94,7 +101,8 @@ class GpuExecutor:
     def result(self, slot: int, job: Job):
         from . import code_to_int
         st = self.streams[slot]
-        codes, counts, failed = self.hists[slot].read(st)
+        tri = self.tris[job.tri]
+        codes, counts, failed = self.hists[slot][tri.code_words].read(st)
         if failed:
             raise RuntimeError(f"{failed} instances failed")
         hist = {code_to_int(c): int(k) for c, k in zip(codes, counts)}
@@ -102,7 +110,9 @@ class GpuExecutor:
         if slot in self.buffers:
             masks, cbuf = self.buffers.pop(slot)
             self.tris[job.tri].sync(st)
-            out = cbuf.cpu().numpy().view("uint64")[:, 0].copy()
+            out = cbuf.cpu().numpy().view("uint64").copy()
+            if out.shape[1] == 1:
+                out = out[:, 0]
             del masks, cbuf
         return hist, out
 
@@ -126,6 +136,8 @@ class Server:
         self.thread.start()
 
     def submit(self, job: Job) -> Future:
+        if hasattr(self.ex, "words"):
+            job.words = self.ex.words(job)
         if job.mem_bytes() > self.mem_budget:
             raise ValueError("job needs more device memory than the server's budget")
         job.submitted = time.perf_counter()

@@ -17,6 +17,11 @@ Generators
   subdivision is not a unimodular triangulation (a point unused, a facet that
   is not a unit triangle, or a degenerate lifting) are rejected and redrawn.
 * ``random_masks(...)``: counter-based splitmix64 sign words.
+* ``splitmix_sign_vectors(d, base, n)``: the sign vectors of splitmix64
+  counters base, base + 1, ...: word w of counter k is splitmix64(k * W + w),
+  the top word cut to |A| bits (one word: splitmix64(k)).  The engine draws
+  the same stream on the device (ts_splitmix_masks, TS_ENUM_SPLITMIX,
+  batches and serving jobs).
 
 Every value is reproducible from (seed, ids) alone.
 """
@@ -231,4 +236,20 @@ def random_masks(n: int, d: int, seed: int, stream: int = 0) -> np.ndarray:
         nb = min(64, npts - 64 * w)
         if nb < 64:
             words[:, w] &= np.uint64((1 << nb) - 1)
+    return words
+
+
+def splitmix_sign_vectors(d: int, base: int, n: int) -> np.ndarray:
+    """(n, W) uint64 sign vectors of the splitmix64 counters base .. base+n-1:
+    word w of counter k is splitmix64(k * W + w) (mod 2^64), bits >= |A|
+    cleared."""
+    W = sign_words(d)
+    npts = num_points(d)
+    with np.errstate(over="ignore"):
+        k = np.uint64(base & _MASK64) + np.arange(n, dtype=np.uint64)
+        ctr = k[:, None] * np.uint64(W) + np.arange(W, dtype=np.uint64)[None, :]
+    words = splitmix64(ctr)
+    nb = npts - 64 * (W - 1)
+    if nb < 64:
+        words[:, W - 1] &= np.uint64((1 << nb) - 1)
     return words

@@ -59,13 +59,21 @@ def test_validation_rejects_bad_triangulations(eng):
     assert load_status(eng, 5, out) == 2
     assert load_status(eng, 4, good) == 2                         # wrong degree
     assert load_status(eng, 0, good) == 1
-    assert load_status(eng, 10, ti.standard_triangulation(10)) == 8
+    assert load_status(eng, 17, ti.standard_triangulation(17)) == 8  # beyond 3 sign words
 
 
-def test_valid_triangulation_needs_a_device(eng):
+@pytest.mark.parametrize("d", [6, 10, 16])
+def test_valid_triangulation_needs_a_device(eng, d):
     import torch
-    rc = load_status(eng, 6, ti.regular_triangulation(6, seed=6))
+    rc = load_status(eng, d, ti.regular_triangulation(d, seed=d))
     assert rc == (0 if torch.cuda.is_available() else 4)
+
+
+def test_degree_limits(eng):
+    assert eng.library().ts_max_degree() == 16
+    with pytest.raises(eng.TSError) as ex:   # specialised kernels: one sign word (d <= 9)
+        eng.specialized_source(10, ti.standard_triangulation(10))
+    assert ex.value.status == 8
 
 
 def test_status_strings(eng):
