@@ -59,18 +59,20 @@ typedef enum ts_status {
 #define TS_ENUM_FLIP 1u    /* mask = k << 1: one representative per global sign flip */
 #define TS_ENUM_REDUCED 2u /* zeros inserted at bits 0, 1, d+1 (sigma(0,0) = sigma(1,0) =
                               sigma(0,1) = 0): one representative per (Z/2)^3 class (Sec. 3) */
-#define TS_ENUM_SPLITMIX 4u /* mask = splitmix64(k) with the bits >= |A| cleared: a sampled,
-                               reproducible stream of sign vectors (splitmix64 of
-                               ts_batch_create); no bound on hi */
+#define TS_ENUM_SPLITMIX 4u /* word w of the mask = splitmix64(k * W + w), W sign words,
+                               bits >= |A| cleared (one word: splitmix64(k)): a sampled,
+                               reproducible stream of sign vectors (the stream of
+                               ts_splitmix_masks and ts_batch_create); no bound on hi */
 
 /* Human-readable name of a status code; never NULL. */
 const char *ts_status_str(int status);
 
-/* Largest degree this build supports. */
+/* Largest degree this build supports (16: |A| <= 153, three sign words,
+ * codes of at most four words). */
 int ts_max_degree(void);
 
-/* Load a triangulation T of d*Delta_2 given by its edge list (Sec. 2: "a
- * triangulation ... represented by its edge list").
+/* Load a triangulation T of d*Delta_2 given by its edge list (the input form
+ * of Sec. 2).
  *   d        degree, 1 <= d <= ts_max_degree()
  *   edges_ij host, n_edges rows of 4 int32 (i1, j1, i2, j2), each a pair of
  *            lattice points of A; order and orientation are free
@@ -107,27 +109,42 @@ ts_status ts_real_schemes(const ts_tri *tri, const uint64_t *signs, uint64_t n,
  *   TS_KERNEL_TABLE: one generic kernel per degree; the triangulation's
  *     tables are staged into shared memory by a bulk copy in every block.
  *   TS_KERNEL_SPECIALIZED: a kernel generated for this triangulation (its
- *     structure compiled into the instruction stream) with NVRTC on first use.
+ *     structure compiled into the instruction stream) with NVRTC on first use;
+ *     d <= 9 only (one sign word), TS_EUNSUPPORTED above.
  *   TS_KERNEL_AUTO (default): specialised for ts_enumerate and for batches of
- *     at least 65536 instances, table-driven otherwise or if the specialised
- *     kernel cannot be built. */
+ *     at least 65536 instances when d <= 9, table-driven otherwise or if the
+ *     specialised kernel cannot be built. */
 #define TS_KERNEL_AUTO 0
 #define TS_KERNEL_TABLE 1
 #define TS_KERNEL_SPECIALIZED 2
 ts_status ts_set_kernel(ts_tri *tri, int kind);
 
+/* Where the table-driven kernels keep their per-instance scratch (labels,
+ * union-find, region tree; 0.1 to 3.7 KB per instance, growing with d).
+ *   TS_SCRATCH_SHARED: shared memory (few resident warps for large d).
+ *   TS_SCRATCH_GLOBAL: device memory, L1/L2-resident, allocated per launch
+ *     with cudaMallocAsync on the launch's stream and freed after it.
+ *   TS_SCRATCH_AUTO (default): global for d >= 10, shared below.
+ * Results are identical. */
+#define TS_SCRATCH_AUTO 0
+#define TS_SCRATCH_SHARED 1
+#define TS_SCRATCH_GLOBAL 2
+ts_status ts_set_scratch(ts_tri *tri, int where);
+
 /* Build the specialised kernels now (NVRTC compile and module load on the
  * current device; about a second).  Call it before capturing launches of
  * this triangulation in a CUDA graph, since the first specialised launch
  * otherwise compiles.  Returns TS_ECUDA if compilation or loading fails
- * (ts_specialized_log then holds the compiler log). */
+ * (ts_specialized_log then holds the compiler log), TS_EUNSUPPORTED for
+ * d > 9. */
 ts_status ts_prepare(ts_tri *tri);
 ts_status ts_specialized_log(const ts_tri *tri, char *buf, size_t len);
 
 /* Host-only helper (no device needed): validate the edge list and write the
  * generated specialised CUDA source into buf (compile = 0), or compile it
  * with NVRTC for sm_103a and write the compiler log (compile = 1; returns
- * TS_ECUDA if it does not compile).  *needed receives the full length + 1. */
+ * TS_ECUDA if it does not compile).  *needed receives the full length + 1.
+ * TS_EUNSUPPORTED for d > 9. */
 ts_status ts_specialized_source(int d, const int32_t *edges_ij, int n_edges, int compile, char *buf,
                                 size_t len, size_t *needed);
 
@@ -141,9 +158,11 @@ ts_status ts_real_schemes_host(const ts_tri *tri, const uint64_t *signs_host, ui
  * word (TS_OK if no instance failed since the last call). */
 ts_status ts_sync(const ts_tri *tri, void *stream);
 
-/* Input generation: out[i] = splitmix64(base + i) with the bits >= |A| of
- * degree d cleared, i < n (device buffer of n uint64; asynchronous).  The same
- * sign vectors as TS_ENUM_SPLITMIX sweeps and batches use. */
+/* Input generation: the sign vectors of counters base .. base+n-1 of degree
+ * d: word w of vector i is splitmix64((base + i) * W + w), W sign words, with
+ * the bits >= |A| cleared (one word: splitmix64(base + i)).  out: device,
+ * n * W uint64; asynchronous.  The same sign vectors as TS_ENUM_SPLITMIX
+ * sweeps and batches use. */
 ts_status ts_splitmix_masks(int d, uint64_t base, uint64_t n, uint64_t *out, void *stream);
 
 /* Device hash histogram of scheme codes with room for `capacity` distinct
@@ -153,14 +172,16 @@ void ts_hist_free(ts_hist *hist);
 /* Reset counts and error state (asynchronous on stream). */
 ts_status ts_hist_clear(ts_hist *hist, void *stream);
 
-/* Exhaustive sweep (Sec. 3, "check all sign distributions for one or a few
- * triangulations"): adds the scheme of every mask m(k), k in [lo, hi), to
- * `hist`.  m(k) = k by default; k << 1 with TS_ENUM_FLIP; k with zero bits
- * inserted at positions 0, 1 and d+1 with TS_ENUM_REDUCED; splitmix64(k)
- * (bits >= |A| cleared) with TS_ENUM_SPLITMIX.  Requires |A| <= 64 (d <= 9)
- * and, except with TS_ENUM_SPLITMIX, m(hi-1) < 2^|A|.  One persistent launch on
- * `stream`; asynchronous.  Failed instances are counted, not inserted, and
- * set the histogram's error word. */
+/* Exhaustive sweep (Sec. 3, an exhaustive check of the sign distributions of
+ * one or a few triangulations): adds the scheme of every mask m(k), k in
+ * [lo, hi), to `hist`, which must have ts_code_words(tri) words per code.
+ * m(k) = k by default; k << 1 with TS_ENUM_FLIP; k with zero bits inserted at
+ * positions 0, 1 and d+1 with TS_ENUM_REDUCED (bits carried past bit 63 go
+ * to the second sign word); the splitmix64 stream with TS_ENUM_SPLITMIX.
+ * Except with TS_ENUM_SPLITMIX, m(hi-1) < 2^|A| (a bound only for d <= 9
+ * and, with TS_ENUM_REDUCED, d = 10).  One persistent launch on `stream`;
+ * asynchronous.  Failed instances are counted, not inserted, and set the
+ * histogram's error word. */
 ts_status ts_enumerate(const ts_tri *tri, uint64_t lo, uint64_t hi, uint32_t flags,
                        ts_hist *hist, void *stream);
 
@@ -179,12 +200,13 @@ ts_status ts_hist_read(ts_hist *hist, uint64_t *codes, uint64_t *counts, uint64_
 /* ---- Batches of mixed-degree triangulations (one graph launch) ----
  *
  * A batch holds njobs jobs; job j classifies counts[j] sign vectors of tris[j]
- * (1 <= d <= 9), vector i being splitmix64(bases[j] + i) with the bits >= |A|
- * cleared (splitmix64 as published by Steele, Lea and Flood: z = x +
- * 0x9E3779B97F4A7C15; z = (z ^ z >> 30) * 0xBF58476D1CE4E5B9; z = (z ^ z >> 27)
- * * 0x94D049BB133111EB; z ^ z >> 31), and adds each code to the job's own
- * device histogram; if code_outputs is not NULL and code_outputs[j] is not
- * NULL (device, counts[j] uint64), it also stores every code there.  For each
+ * (any supported degree), vector i being the splitmix64 sign vector of
+ * counter bases[j] + i (ts_splitmix_masks; splitmix64 as published by Steele,
+ * Lea and Flood: z = x + 0x9E3779B97F4A7C15; z = (z ^ z >> 30) *
+ * 0xBF58476D1CE4E5B9; z = (z ^ z >> 27) * 0x94D049BB133111EB; z ^ z >> 31),
+ * and adds each code to the job's own device histogram; if code_outputs is
+ * not NULL and code_outputs[j] is not NULL (device, counts[j] *
+ * ts_code_words(tris[j]) uint64), it also stores every code there.  For each
  * degree present, one persistent kernel serves all jobs of that degree,
  * staging a job's tables into shared memory when it moves to that job; the
  * per-degree kernels run concurrently.  The triangulations must stay loaded
@@ -194,17 +216,20 @@ ts_status ts_batch_create(int njobs, ts_tri *const *tris, const uint64_t *counts
                           const uint64_t *bases, uint64_t *const *code_outputs,
                           uint64_t hist_capacity, ts_batch **out);
 void ts_batch_free(ts_batch *batch);
-/* Tile of the degree-d kernel: threads per block (multiple of 32, at most 256,
- * the block's scratch must fit shared memory) and sign vectors per work item
- * (a multiple of threads).  Returns TS_EINVAL for tiles that do not fit. */
-ts_status ts_batch_set_tile(ts_batch *batch, int d, int threads, int chunk);
+/* Tile of the degree-d kernel: threads per block (multiple of 32, at most 256;
+ * with shared scratch the block's scratch must fit shared memory), sign
+ * vectors per work item (a multiple of threads) and scratch placement
+ * (TS_SCRATCH_*; global scratch is allocated here, grid x threads x
+ * scratch words).  Returns TS_EINVAL for tiles that do not fit. */
+ts_status ts_batch_set_tile(ts_batch *batch, int d, int threads, int chunk, int scratch);
 /* Clear the histograms and run every job, asynchronously on stream.  With
  * use_graph the work (clears, fork, per-degree kernels, join) is captured
  * into a CUDA graph on the first call (and after a tile change) and the graph
  * is launched; otherwise the same work is enqueued directly. */
 ts_status ts_batch_run(ts_batch *batch, int use_graph, void *stream);
 /* Histogram of one job, sorted by code, after synchronising stream (same
- * output conventions as ts_hist_read; n_failed counts the whole batch). */
+ * output conventions as ts_hist_read with ts_code_words(tris[job]) words per
+ * code; n_failed counts the whole batch). */
 ts_status ts_batch_read(ts_batch *batch, int job, uint64_t *codes, uint64_t *counts, uint64_t cap,
                         uint64_t *n_out, uint64_t *n_failed, void *stream);
 

@@ -23,6 +23,9 @@ TS_ENUM_SPLITMIX = 4
 TS_KERNEL_AUTO = 0
 TS_KERNEL_TABLE = 1
 TS_KERNEL_SPECIALIZED = 2
+TS_SCRATCH_AUTO = 0
+TS_SCRATCH_SHARED = 1
+TS_SCRATCH_GLOBAL = 2
 
 STATUS = {0: "TS_OK", 1: "TS_EINVAL", 2: "TS_ENOTTRI", 3: "TS_ENOMEM", 4: "TS_ECUDA",
           5: "TS_EOVERFLOW", 6: "TS_ETIMEOUT", 7: "TS_EINTERNAL", 8: "TS_EUNSUPPORTED"}
@@ -70,6 +73,7 @@ def _load():
                 "ts_hist_read": ([P, P, P, U64, ctypes.POINTER(U64), ctypes.POINTER(U64), P], I),
                 "ts_scheme_string": ([I, P, I, ctypes.c_char_p, ctypes.c_size_t], I),
                 "ts_set_kernel": ([P, I], I),
+                "ts_set_scratch": ([P, I], I),
                 "ts_prepare": ([P], I),
                 "ts_specialized_log": ([P, ctypes.c_char_p, ctypes.c_size_t], I),
                 "ts_specialized_source": ([I, P, I, I, ctypes.c_char_p, ctypes.c_size_t,
@@ -78,7 +82,7 @@ def _load():
                 "ts_splitmix_masks": ([I, U64, U64, P, P], I),
                 "ts_batch_create": ([I, P, P, P, P, U64, ctypes.POINTER(P)], I),
                 "ts_batch_free": ([P], None),
-                "ts_batch_set_tile": ([P, I, I, I], I),
+                "ts_batch_set_tile": ([P, I, I, I, I], I),
                 "ts_batch_run": ([P, I, P], I),
                 "ts_batch_read": ([P, I, P, P, U64, ctypes.POINTER(U64), ctypes.POINTER(U64), P], I),
             }
@@ -146,6 +150,10 @@ class Triangulation:
     def set_kernel(self, kind: int):
         """TS_KERNEL_AUTO / TS_KERNEL_TABLE / TS_KERNEL_SPECIALIZED."""
         _check(_lib.ts_set_kernel(self._h, int(kind)), "ts_set_kernel")
+
+    def set_scratch(self, where: int):
+        """TS_SCRATCH_AUTO / TS_SCRATCH_SHARED / TS_SCRATCH_GLOBAL (table-driven kernels)."""
+        _check(_lib.ts_set_scratch(self._h, int(where)), "ts_set_scratch")
 
     def prepare(self):
         """Compile and load the specialised kernels now (ts_prepare)."""
@@ -268,8 +276,11 @@ class Batch:
         except Exception:
             pass
 
-    def set_tile(self, d: int, threads: int, chunk: int):
-        _check(_lib.ts_batch_set_tile(self._h, int(d), int(threads), int(chunk)), "ts_batch_set_tile")
+    def set_tile(self, d: int, threads: int, chunk: int, scratch: int = 0):
+        """Tile of the degree-d kernel: threads per block, sign vectors per
+        work item, scratch placement (TS_SCRATCH_*)."""
+        _check(_lib.ts_batch_set_tile(self._h, int(d), int(threads), int(chunk), int(scratch)),
+               "ts_batch_set_tile")
 
     def run(self, graph: bool = True, stream=None):
         _check(_lib.ts_batch_run(self._h, int(bool(graph)), _stream_handle(stream)), "ts_batch_run")

@@ -1,11 +1,13 @@
 """Tile autotuner of mixed-degree batches (ts_batch).
 
-For every degree in a batch the persistent kernel has two knobs: threads per
-block and sign vectors per work item.  The tuner times candidate tiles on the
-batch's own jobs of that degree (a sub-batch, so degrees are tuned
-independently), keeps the fastest, and can store the choice in a JSON cache
-keyed by GPU name and degree (path from the argument or the TCURVE_TILE_CACHE
-environment variable).
+For every degree in a batch the persistent kernel has three knobs: threads
+per block, sign vectors per work item, and where the per-thread scratch
+lives (shared memory, or global memory for the large degrees whose scratch
+leaves few warps per SM).  The tuner times candidate tiles on the batch's own
+jobs of that degree (a sub-batch, so degrees are tuned independently), keeps
+the fastest, and can store the choice in a JSON cache keyed by GPU name and
+degree (path from the argument or the TCURVE_TILE_CACHE environment
+variable).
 """
 from __future__ import annotations
 
@@ -15,6 +17,12 @@ from typing import Dict, Iterable, Optional, Tuple
 
 THREADS = (64, 96, 128, 192, 256)
 CHUNK_PER_THREAD = (4, 16, 64)
+SHARED, GLOBAL = 1, 2            # TS_SCRATCH_SHARED, TS_SCRATCH_GLOBAL
+
+
+def scratch_choices(d: int):
+    """Scratch placements worth timing: shared below d = 8, both above."""
+    return (SHARED,) if d < 8 else (SHARED, GLOBAL)
 
 
 def _gpu_name() -> str:
@@ -39,23 +47,24 @@ def _time_batch(batch, reps: int) -> float:
 
 
 def tune_degree(tris, counts, bases, threads: Iterable[int] = THREADS,
-                chunk_per_thread: Iterable[int] = CHUNK_PER_THREAD, reps: int = 3
-                ) -> Tuple[int, int, float]:
-    """Fastest (threads, chunk, ms) for the jobs (all of one degree)."""
+                chunk_per_thread: Iterable[int] = CHUNK_PER_THREAD, reps: int = 3,
+                scratch: Optional[Iterable[int]] = None) -> Tuple[int, int, int, float]:
+    """Fastest (threads, chunk, scratch, ms) for the jobs (all of one degree)."""
     from . import Batch, TSError
     d = tris[0].d
     assert all(t.d == d for t in tris)
     sub = Batch(tris, counts, bases, hist_capacity=1024)
     best = None
-    for t in threads:
-        for c in chunk_per_thread:
-            try:
-                sub.set_tile(d, t, t * c)
-            except TSError:
-                continue  # the block does not fit shared memory
-            ms = _time_batch(sub, reps)
-            if best is None or ms < best[2]:
-                best = (t, t * c, ms)
+    for s in (scratch_choices(d) if scratch is None else scratch):
+        for t in threads:
+            for c in chunk_per_thread:
+                try:
+                    sub.set_tile(d, t, t * c, s)
+                except TSError:
+                    continue  # the block does not fit shared memory
+                ms = _time_batch(sub, reps)
+                if best is None or ms < best[3]:
+                    best = (t, t * c, s, ms)
     sub.close()
     if best is None:
         raise RuntimeError(f"no tile fits degree {d}")
@@ -64,26 +73,26 @@ def tune_degree(tris, counts, bases, threads: Iterable[int] = THREADS,
 
 def autotune(tris, counts, bases, cache: Optional[str] = None, reps: int = 3,
              threads: Iterable[int] = THREADS, chunk_per_thread: Iterable[int] = CHUNK_PER_THREAD
-             ) -> Dict[int, Tuple[int, int]]:
-    """Tile per degree of the batch {d: (threads, chunk)}; cached choices are
-    reused, new ones stored."""
+             ) -> Dict[int, Tuple[int, int, int]]:
+    """Tile per degree of the batch {d: (threads, chunk, scratch)}; cached
+    choices are reused, new ones stored."""
     cache = cache or os.environ.get("TCURVE_TILE_CACHE")
     store = {}
     if cache and os.path.exists(cache):
         with open(cache) as f:
             store = json.load(f)
     gpu = _gpu_name()
-    tiles: Dict[int, Tuple[int, int]] = {}
+    tiles: Dict[int, Tuple[int, int, int]] = {}
     for d in sorted({t.d for t in tris}):
-        key = f"{gpu}|d={d}"
+        key = f"{gpu}|d={d}|tile3"
         if key in store:
-            tiles[d] = tuple(store[key][:2])
+            tiles[d] = tuple(store[key][:3])
             continue
         idx = [i for i, t in enumerate(tris) if t.d == d]
-        t, c, ms = tune_degree([tris[i] for i in idx], [counts[i] for i in idx],
-                               [bases[i] for i in idx], threads, chunk_per_thread, reps)
-        tiles[d] = (t, c)
-        store[key] = [t, c, ms]
+        t, c, s, ms = tune_degree([tris[i] for i in idx], [counts[i] for i in idx],
+                                  [bases[i] for i in idx], threads, chunk_per_thread, reps)
+        tiles[d] = (t, c, s)
+        store[key] = [t, c, s, ms]
     if cache:
         tmp = cache + ".tmp"
         with open(tmp, "w") as f:
@@ -92,7 +101,7 @@ def autotune(tris, counts, bases, cache: Optional[str] = None, reps: int = 3,
     return tiles
 
 
-def apply(batch, tiles: Dict[int, Tuple[int, int]]):
-    for d, (t, c) in tiles.items():
+def apply(batch, tiles: Dict[int, Tuple[int, ...]]):
+    for d, tile in tiles.items():
         if d in batch.degrees:
-            batch.set_tile(d, t, c)
+            batch.set_tile(d, *tile)

@@ -10,7 +10,8 @@
 // (warp-aggregated atomics).  The per-degree kernels run on forked streams
 // inside one CUDA graph that is captured on the first run and replayed after;
 // each degree has its own tile shape (threads per block, instances per work
-// item), which ts_batch_set_tile changes (the autotuner's knob).
+// item, scratch in shared or global memory), which ts_batch_set_tile
+// changes (the autotuner's knob).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -34,11 +35,13 @@ constexpr size_t max_table_bytes(int d) {
   return (size_t)(((10 * d * d + 6 * d + 2) + 3) & ~3) * 4;
 }
 
-template <int D_, int T_>
+// Degree-D_ kernel with T_ threads per block; per-thread scratch in shared
+// memory, or (G_) in global memory, L1/L2-resident.
+template <int D_, int T_, bool G_>
 struct JobK : TcTableK<D_, T_, true> {
-  static constexpr bool fits =
-      JobK::L.ok && (max_table_bytes(D_) + 127) / 128 * 128 + 128 + (size_t)JobK::WORDS * 4 * T_ <=
-                        227 * 1024;
+  static constexpr bool fits = JobK::L.ok && (max_table_bytes(D_) + 127) / 128 * 128 + 128 +
+                                                     (G_ ? 0 : (size_t)JobK::WORDS * 4 * T_) <=
+                                                 227 * 1024;
 };
 
 struct DevJob {
@@ -56,18 +59,20 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-template <int D, int T>
+template <int D, int T, bool G>
 __global__ void __launch_bounds__(T)
     jobs_kernel(const DevJob *__restrict__ jobs, u32 njobs, u64 total_items, u32 chunk,
                 u32 table_words, u32 off_fan, u32 off_vext, unsigned long long *work, u32 *err_word,
-                unsigned long long *failed_word) {
-  typedef JobK<D, T> K;
+                unsigned long long *failed_word, u32 *gscratch) {
+  typedef JobK<D, T, G> K;
   extern __shared__ __align__(128) uint8_t smem[];
   u32 *tab = reinterpret_cast<u32 *>(smem);
   const size_t toff = ((size_t)table_words * 4 + 127) / 128 * 128;
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + toff);
   unsigned long long *slot = reinterpret_cast<unsigned long long *>(smem + toff + 64);
-  const TcScratch<K> S{reinterpret_cast<u32 *>(smem + toff + 128) + threadIdx.x};
+  const TcScratch<K> S{(G ? gscratch + (size_t)blockIdx.x * K::WORDS * T
+                         : reinterpret_cast<u32 *>(smem + toff + 128)) +
+                        threadIdx.x};
   if (threadIdx.x == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(1u));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -155,55 +160,62 @@ __global__ void __launch_bounds__(T)
   if (failed) atomicAdd(failed_word, failed);
 }
 
-// (degree, threads) -> kernel; only instantiations whose block fits.
+// (degree, threads, scratch) -> kernel; only instantiations whose block fits.
 typedef void (*JobsFn)(const DevJob *, u32, u64, u32, u32, u32, u32, unsigned long long *, u32 *,
-                       unsigned long long *);
+                       unsigned long long *, u32 *);
 
-template <int D, int T>
+template <int D, int T, bool G>
 JobsFn jobs_fn() {
-  if constexpr (JobK<D, T>::fits) return jobs_kernel<D, T>;
+  if constexpr (JobK<D, T, G>::fits) return jobs_kernel<D, T, G>;
   else return nullptr;
 }
 
-template <int D>
-JobsFn jobs_fn_t(int t) {
+template <int D, bool G>
+JobsFn jobs_fn_tg(int t) {
   switch (t) {
-    case 32: return jobs_fn<D, 32>();
-    case 64: return jobs_fn<D, 64>();
-    case 96: return jobs_fn<D, 96>();
-    case 128: return jobs_fn<D, 128>();
-    case 192: return jobs_fn<D, 192>();
-    case 256: return jobs_fn<D, 256>();
+    case 32: return jobs_fn<D, 32, G>();
+    case 64: return jobs_fn<D, 64, G>();
+    case 96: return jobs_fn<D, 96, G>();
+    case 128: return jobs_fn<D, 128, G>();
+    case 192: return jobs_fn<D, 192, G>();
+    case 256: return jobs_fn<D, 256, G>();
     default: return nullptr;
   }
 }
 
-JobsFn jobs_fn_dt(int d, int t) {
+template <int D>
+JobsFn jobs_fn_t(int t, bool g) {
+  return g ? jobs_fn_tg<D, true>(t) : jobs_fn_tg<D, false>(t);
+}
+
+JobsFn jobs_fn_dt(int d, int t, bool g) {
   switch (d) {
-    case 1: return jobs_fn_t<1>(t);
-    case 2: return jobs_fn_t<2>(t);
-    case 3: return jobs_fn_t<3>(t);
-    case 4: return jobs_fn_t<4>(t);
-    case 5: return jobs_fn_t<5>(t);
-    case 6: return jobs_fn_t<6>(t);
-    case 7: return jobs_fn_t<7>(t);
-    case 8: return jobs_fn_t<8>(t);
-    case 9: return jobs_fn_t<9>(t);
-    case 10: return jobs_fn_t<10>(t);
-    case 11: return jobs_fn_t<11>(t);
-    case 12: return jobs_fn_t<12>(t);
-    case 13: return jobs_fn_t<13>(t);
-    case 14: return jobs_fn_t<14>(t);
-    case 15: return jobs_fn_t<15>(t);
-    case 16: return jobs_fn_t<16>(t);
+    case 1: return jobs_fn_t<1>(t, g);
+    case 2: return jobs_fn_t<2>(t, g);
+    case 3: return jobs_fn_t<3>(t, g);
+    case 4: return jobs_fn_t<4>(t, g);
+    case 5: return jobs_fn_t<5>(t, g);
+    case 6: return jobs_fn_t<6>(t, g);
+    case 7: return jobs_fn_t<7>(t, g);
+    case 8: return jobs_fn_t<8>(t, g);
+    case 9: return jobs_fn_t<9>(t, g);
+    case 10: return jobs_fn_t<10>(t, g);
+    case 11: return jobs_fn_t<11>(t, g);
+    case 12: return jobs_fn_t<12>(t, g);
+    case 13: return jobs_fn_t<13>(t, g);
+    case 14: return jobs_fn_t<14>(t, g);
+    case 15: return jobs_fn_t<15>(t, g);
+    case 16: return jobs_fn_t<16>(t, g);
     default: return nullptr;
   }
 }
 
-size_t jobs_smem(int d, int t, uint32_t table_words) {
+size_t jobs_smem(int d, int t, uint32_t table_words, bool g) {
   const TcLayout L = tc_layout(d, true, t);
-  return ((size_t)table_words * 4 + 127) / 128 * 128 + 128 + (size_t)L.words * 4 * t;
+  return ((size_t)table_words * 4 + 127) / 128 * 128 + 128 + (g ? 0 : (size_t)L.words * 4 * t);
 }
+
+size_t scratch_words(int d, int t) { return (size_t)tc_layout(d, true, t).words * t; }
 
 ts_status cuda_st(cudaError_t e) {
   if (e == cudaSuccess) return TS_OK;
@@ -218,6 +230,12 @@ using namespace tcurve;
 struct ts_batch {
   struct Group {  // all jobs of one degree
     int d = 0, threads = 64, chunk = 1024;
+    bool global = false;        // per-thread scratch in global memory
+    JobsFn fn = nullptr;        // the kernel of this tile, its launch shape
+    size_t smem = 0;
+    unsigned grid = 1;
+    u32 *scratch = nullptr;     // global scratch (grid x threads x words)
+    size_t scratch_bytes = 0;
     uint32_t table_words = 0, off_fan = 0, off_vext = 0;
     std::vector<int> jobs;      // indices into the batch's job list
     DevJob *d_jobs = nullptr;   // device job table (sorted as `jobs`)
@@ -260,26 +278,45 @@ cudaError_t upload_group(ts_batch *b, ts_batch::Group &g) {
   return cudaMemcpy(g.d_jobs, dj.data(), sizeof(DevJob) * dj.size(), cudaMemcpyHostToDevice);
 }
 
-cudaError_t launch_group(ts_batch *b, ts_batch::Group &g, cudaStream_t st) {
-  JobsFn fn = jobs_fn_dt(g.d, g.threads);
-  if (!fn) return cudaErrorInvalidConfiguration;
-  const size_t smem = jobs_smem(g.d, g.threads, g.table_words);
-  cudaError_t e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+// Kernel, shared memory, persistent grid and global scratch of the group's
+// tile (host work only: done at creation and on a tile change, never while a
+// stream is being captured).
+cudaError_t prepare_group(ts_batch::Group &g) {
+  g.fn = jobs_fn_dt(g.d, g.threads, g.global);
+  if (!g.fn) return cudaErrorInvalidConfiguration;
+  g.smem = jobs_smem(g.d, g.threads, g.table_words, g.global);
+  cudaError_t e = cudaFuncSetAttribute((const void *)g.fn,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0, sms = 0, dev = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)fn, g.threads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)g.fn, g.threads, g.smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const uint64_t cap = (uint64_t)per_sm * sms;
-  const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(cap, g.items));
-  e = cudaMemsetAsync(g.d_work, 0, sizeof(unsigned long long), st);
+  g.grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(cap, g.items));
+  if (g.global) {
+    const size_t need = (size_t)g.grid * scratch_words(g.d, g.threads) * 4;
+    if (need > g.scratch_bytes) {
+      if (g.scratch) cudaFree(g.scratch);
+      g.scratch = nullptr;
+      g.scratch_bytes = 0;
+      e = cudaMalloc(&g.scratch, need);
+      if (e != cudaSuccess) return e;
+      g.scratch_bytes = need;
+    }
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_group(ts_batch *b, ts_batch::Group &g, cudaStream_t st) {
+  if (!g.fn) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaMemsetAsync(g.d_work, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
-  fn<<<grid, g.threads, smem, st>>>(g.d_jobs, (u32)g.jobs.size(), g.items, (u32)g.chunk,
-                                    g.table_words, g.off_fan, g.off_vext, g.d_work, b->d_err,
-                                    b->d_failed);
+  g.fn<<<g.grid, g.threads, g.smem, st>>>(g.d_jobs, (u32)g.jobs.size(), g.items, (u32)g.chunk,
+                                          g.table_words, g.off_fan, g.off_vext, g.d_work, b->d_err,
+                                          b->d_failed, g.scratch);
   return cudaGetLastError();
 }
 
@@ -355,8 +392,9 @@ ts_status ts_batch_create(int njobs, ts_tri *const *tris, const uint64_t *counts
       g.table_words = t->lay.words;
       g.off_fan = t->lay.off_fan;
       g.off_vext = t->lay.off_vext;
-      g.threads = t->d >= 8 ? 64 : 128;
-      while (g.threads > 32 && !jobs_fn_dt(t->d, g.threads)) g.threads -= 32;
+      g.global = t->d >= kGlobalScratchFrom;
+      g.threads = g.global ? 128 : (t->d >= 8 ? 64 : 128);
+      while (g.threads > 32 && !jobs_fn_dt(t->d, g.threads, g.global)) g.threads -= 32;
       g.chunk = g.threads * 8;
       b->groups.push_back(g);
     }
@@ -367,6 +405,7 @@ ts_status ts_batch_create(int njobs, ts_tri *const *tris, const uint64_t *counts
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = upload_group(b, g);
+    if (e == cudaSuccess) e = prepare_group(g);
   }
   if (e != cudaSuccess) {
     ts_batch_free(b);
@@ -382,6 +421,7 @@ void ts_batch_free(ts_batch *b) {
   for (auto &g : b->groups) {
     if (g.d_jobs) cudaFree(g.d_jobs);
     if (g.d_work) cudaFree(g.d_work);
+    if (g.scratch) cudaFree(g.scratch);
     if (g.stream) cudaStreamDestroy(g.stream);
     if (g.done) cudaEventDestroy(g.done);
   }
@@ -393,18 +433,24 @@ void ts_batch_free(ts_batch *b) {
   delete b;
 }
 
-ts_status ts_batch_set_tile(ts_batch *b, int d, int threads, int chunk) {
-  if (!b || threads < 32 || threads % 32 || chunk < threads || chunk % threads) return TS_EINVAL;
+ts_status ts_batch_set_tile(ts_batch *b, int d, int threads, int chunk, int scratch) {
+  if (!b || threads < 32 || threads % 32 || chunk < threads || chunk % threads ||
+      scratch < TS_SCRATCH_AUTO || scratch > TS_SCRATCH_GLOBAL)
+    return TS_EINVAL;
   for (auto &g : b->groups) {
     if (g.d != d) continue;
-    if (!jobs_fn_dt(d, threads)) return TS_EINVAL;  // block does not fit shared memory
+    const bool global = scratch == TS_SCRATCH_AUTO ? d >= kGlobalScratchFrom : scratch == TS_SCRATCH_GLOBAL;
+    if (!jobs_fn_dt(d, threads, global)) return TS_EINVAL;  // block does not fit shared memory
     g.threads = threads;
     g.chunk = chunk;
+    g.global = global;
     if (b->exec) {
       cudaGraphExecDestroy(b->exec);
       b->exec = nullptr;
     }
-    return cuda_st(upload_group(b, g));
+    cudaError_t e = upload_group(b, g);
+    if (e == cudaSuccess) e = prepare_group(g);
+    return cuda_st(e);
   }
   return TS_EINVAL;
 }

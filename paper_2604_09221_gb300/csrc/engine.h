@@ -16,6 +16,7 @@ namespace tcurve {
 
 constexpr int kMaxDegree = 16;     // |A| <= 153: three sign words, four code words
 constexpr int kMaxSpecialized = 9;  // triangulation-specialised kernels: one sign word
+constexpr int kGlobalScratchFrom = 10;  // TS_SCRATCH_AUTO: global scratch from this degree
 
 // Count words of multi-word histograms carry two flags in their top bits
 // (slot being written / key published); the count is the rest.
@@ -63,6 +64,7 @@ struct ts_tri {
   uint32_t *d_err = nullptr;     // device error word (scratch, owned here)
   tcurve::Diamond dia;
   int kernel = 0;                // TS_KERNEL_*
+  int scratch = 0;               // TS_SCRATCH_* (table-driven kernels)
   std::mutex jit_mu;
   std::shared_ptr<tcurve::JitModule> jit;
   std::string jit_log;
@@ -82,8 +84,9 @@ struct ts_hist {
 namespace tcurve {
 cudaError_t launch_real_schemes(const ts_tri *tri, const uint64_t *signs, uint64_t n,
                                 uint64_t *codes, cudaStream_t stream);
+// allow_global = false keeps the scratch in shared memory (no allocation).
 cudaError_t launch_enumerate(const ts_tri *tri, uint64_t lo, uint64_t hi, uint32_t flags,
-                             ts_hist *hist, cudaStream_t stream);
+                             ts_hist *hist, cudaStream_t stream, bool allow_global = true);
 cudaError_t launch_hist_clear(ts_hist *hist, cudaStream_t stream);
 cudaError_t launch_splitmix_masks(int d, uint64_t base, uint64_t n, uint64_t *out,
                                   cudaStream_t stream);

@@ -351,6 +351,12 @@ ts_status ts_set_kernel(ts_tri *t, int kind) {
   return TS_OK;
 }
 
+ts_status ts_set_scratch(ts_tri *t, int where) {
+  if (!t || where < TS_SCRATCH_AUTO || where > TS_SCRATCH_GLOBAL) return TS_EINVAL;
+  t->scratch = where;
+  return TS_OK;
+}
+
 ts_status ts_prepare(ts_tri *t) {
   if (!t) return TS_EINVAL;
   if (t->d > kMaxSpecialized) return TS_EUNSUPPORTED;

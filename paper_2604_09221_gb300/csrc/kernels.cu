@@ -32,8 +32,12 @@ namespace {
 
 constexpr long kWaitIters = 1L << 22;  // bounded spin on the table mbarrier
 
-template <int D>
-using TableK = TcTableK<D, 256, false>;
+// Scratch placement: shared memory (block size from the layout: the
+// largest of which two blocks fit an SM), or global memory, L1/L2-resident,
+// with 128-thread blocks (more warps per SM for the large degrees, whose
+// per-thread scratch leaves room for one or two warps in shared memory).
+template <int D, bool G>
+using TableK = TcTableK<D, G ? 128 : 256, G>;
 
 // ---------------------------------------------------------------- PTX ----
 
@@ -93,10 +97,10 @@ __device__ bool stage_tables(uint32_t *stab, const uint32_t *gtab, uint32_t byte
   return true;
 }
 
-template <class K>
+template <class K, bool G>
 constexpr size_t smem_bytes(uint32_t table_words, bool with_hash) {
-  return ((size_t)table_words * 4 + 127) / 128 * 128 + 128 + (size_t)K::WORDS * 4 * K::THREADS +
-         (with_hash ? (size_t)K::HASH * 16 : 0);
+  return ((size_t)table_words * 4 + 127) / 128 * 128 + 128 +
+         (G ? 0 : (size_t)K::WORDS * 4 * K::THREADS) + (with_hash ? (size_t)K::HASH * 16 : 0);
 }
 
 struct SmemLayout {
@@ -108,8 +112,8 @@ struct SmemLayout {
   unsigned long long *hcnt;
 };
 
-template <class K>
-__device__ SmemLayout carve(uint8_t *smem, uint32_t table_words) {
+template <class K, bool G>
+__device__ SmemLayout carve(uint8_t *smem, uint32_t table_words, u32 *gscratch) {
   SmemLayout s;
   size_t off = 0;
   s.tab = reinterpret_cast<uint32_t *>(smem);
@@ -117,8 +121,12 @@ __device__ SmemLayout carve(uint8_t *smem, uint32_t table_words) {
   s.bar = reinterpret_cast<uint64_t *>(smem + off);
   s.chunk = reinterpret_cast<unsigned long long *>(smem + off + 64);
   off += 128;
-  s.scratch = reinterpret_cast<u32 *>(smem + off);
-  off += (size_t)K::WORDS * 4 * K::THREADS;
+  if (G) {
+    s.scratch = gscratch + (size_t)blockIdx.x * K::WORDS * K::THREADS;
+  } else {
+    s.scratch = reinterpret_cast<u32 *>(smem + off);
+    off += (size_t)K::WORDS * 4 * K::THREADS;
+  }
   s.hkeys = reinterpret_cast<u64 *>(smem + off);
   s.hcnt = reinterpret_cast<unsigned long long *>(smem + off + K::HASH * 8);
   return s;
@@ -126,14 +134,14 @@ __device__ SmemLayout carve(uint8_t *smem, uint32_t table_words) {
 
 // ----------------------------------------------------- query kernel ----
 
-template <int D>
-__global__ void __launch_bounds__(TableK<D>::THREADS)
+template <int D, bool G>
+__global__ void __launch_bounds__(TableK<D, G>::THREADS)
     real_schemes_kernel(TableLayout L, const uint32_t *__restrict__ gtab,
                         const uint64_t *__restrict__ signs, uint64_t n, uint64_t *codes,
-                        uint32_t *err_word) {
-  typedef TableK<D> K;
+                        uint32_t *err_word, u32 *gscratch) {
+  typedef TableK<D, G> K;
   extern __shared__ __align__(128) uint8_t smem[];
-  SmemLayout M = carve<K>(smem, L.words);
+  SmemLayout M = carve<K, G>(smem, L.words, gscratch);
   if (!stage_tables(M.tab, gtab, L.words * 4, M.bar, err_word)) return;
   const TcScratch<K> S{M.scratch + threadIdx.x};
   const u64 *sg = reinterpret_cast<const u64 *>(signs);
@@ -149,14 +157,14 @@ __global__ void __launch_bounds__(TableK<D>::THREADS)
 
 // ----------------------------------------------- enumeration kernel ----
 
-template <int D>
-__global__ void __launch_bounds__(TableK<D>::THREADS)
+template <int D, bool G>
+__global__ void __launch_bounds__(TableK<D, G>::THREADS)
     enumerate_kernel(TableLayout L, const uint32_t *__restrict__ gtab, uint64_t lo, uint64_t total,
-                     uint32_t flags, ts_hist h) {
-  typedef TableK<D> K;
+                     uint32_t flags, ts_hist h, u32 *gscratch) {
+  typedef TableK<D, G> K;
   constexpr uint32_t kChunk = K::THREADS * 16;
   extern __shared__ __align__(128) uint8_t smem[];
-  SmemLayout M = carve<K>(smem, L.words);
+  SmemLayout M = carve<K, G>(smem, L.words, gscratch);
   for (int s = threadIdx.x; s < (int)K::HASH; s += K::THREADS) {
     M.hkeys[s] = 0;
     M.hcnt[s] = 0;
@@ -234,46 +242,86 @@ int sm_count() {
   return n > 0 ? n : 1;
 }
 
+// Grid of a persistent launch: resident blocks per SM x SMs, at most `want`.
+template <class F>
+cudaError_t persistent_grid(F fn, int threads, size_t smem, uint64_t want, unsigned *grid) {
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const uint64_t cap = (uint64_t)per_sm * sm_count();
+  *grid = (unsigned)(want < cap ? (want ? want : 1) : cap);
+  return cudaSuccess;
+}
+
+// Global scratch of a launch: stream-ordered allocation, freed after it.
+struct GlobalScratch {
+  u32 *p = nullptr;
+  cudaStream_t st;
+  explicit GlobalScratch(cudaStream_t s) : st(s) {}
+  cudaError_t alloc(size_t bytes) { return cudaMallocAsync((void **)&p, bytes, st); }
+  ~GlobalScratch() {
+    if (p) cudaFreeAsync(p, st);
+  }
+};
+
+template <int D, bool G>
+cudaError_t real_schemes_dg(const ts_tri *t, const uint64_t *signs, uint64_t n, uint64_t *codes,
+                            cudaStream_t st) {
+  typedef TableK<D, G> K;
+  const size_t smem = smem_bytes<K, G>(t->lay.words, false);
+  unsigned grid = 0;
+  cudaError_t e = persistent_grid(real_schemes_kernel<D, G>, K::THREADS, smem,
+                                  (n + K::THREADS - 1) / K::THREADS, &grid);
+  if (e != cudaSuccess) return e;
+  GlobalScratch gs(st);
+  if (G && (e = gs.alloc((size_t)grid * K::WORDS * K::THREADS * 4)) != cudaSuccess) return e;
+  real_schemes_kernel<D, G><<<grid, K::THREADS, smem, st>>>(t->lay, t->d_tables, signs, n, codes,
+                                                            t->d_err, gs.p);
+  return cudaGetLastError();
+}
+
+template <int D, bool G>
+cudaError_t enumerate_dg(const ts_tri *t, uint64_t lo, uint64_t hi, uint32_t flags, ts_hist *h,
+                         cudaStream_t st) {
+  typedef TableK<D, G> K;
+  const size_t smem = smem_bytes<K, G>(t->lay.words, true);
+  const uint64_t total = hi - lo;
+  const uint64_t chunk = (uint64_t)K::THREADS * 16;
+  unsigned grid = 0;
+  cudaError_t e = persistent_grid(enumerate_kernel<D, G>, K::THREADS, smem, (total + chunk - 1) / chunk,
+                                  &grid);
+  if (e != cudaSuccess) return e;
+  GlobalScratch gs(st);
+  if (G && (e = gs.alloc((size_t)grid * K::WORDS * K::THREADS * 4)) != cudaSuccess) return e;
+  e = cudaMemsetAsync(h->d_work, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  enumerate_kernel<D, G><<<grid, K::THREADS, smem, st>>>(t->lay, t->d_tables, lo, total, flags, *h,
+                                                         gs.p);
+  return cudaGetLastError();
+}
+
+// Global scratch for d >= 10 unless the triangulation asks otherwise.
+bool global_scratch(const ts_tri *t) {
+  if (t->scratch == TS_SCRATCH_SHARED) return false;
+  if (t->scratch == TS_SCRATCH_GLOBAL) return true;
+  return t->d >= kGlobalScratchFrom;
+}
+
 template <int D>
 cudaError_t real_schemes_d(const ts_tri *t, const uint64_t *signs, uint64_t n, uint64_t *codes,
                            cudaStream_t st) {
-  typedef TableK<D> K;
-  const size_t smem = smem_bytes<K>(t->lay.words, false);
-  cudaError_t e = cudaFuncSetAttribute(real_schemes_kernel<D>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, real_schemes_kernel<D>, K::THREADS, smem);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  uint64_t want = (n + K::THREADS - 1) / K::THREADS;
-  uint64_t cap = (uint64_t)per_sm * sm_count();
-  unsigned grid = (unsigned)(want < cap ? want : cap);
-  real_schemes_kernel<D><<<grid, K::THREADS, smem, st>>>(t->lay, t->d_tables, signs, n, codes, t->d_err);
-  return cudaGetLastError();
+  return global_scratch(t) ? real_schemes_dg<D, true>(t, signs, n, codes, st)
+                           : real_schemes_dg<D, false>(t, signs, n, codes, st);
 }
 
 template <int D>
 cudaError_t enumerate_d(const ts_tri *t, uint64_t lo, uint64_t hi, uint32_t flags, ts_hist *h,
-                        cudaStream_t st) {
-  typedef TableK<D> K;
-  const size_t smem = smem_bytes<K>(t->lay.words, true);
-  cudaError_t e = cudaFuncSetAttribute(enumerate_kernel<D>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, enumerate_kernel<D>, K::THREADS, smem);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  const uint64_t total = hi - lo;
-  const uint64_t chunk = (uint64_t)K::THREADS * 16;
-  uint64_t want = (total + chunk - 1) / chunk;
-  uint64_t cap = (uint64_t)per_sm * sm_count();
-  unsigned grid = (unsigned)(want < cap ? want : cap);
-  e = cudaMemsetAsync(h->d_work, 0, sizeof(unsigned long long), st);
-  if (e != cudaSuccess) return e;
-  enumerate_kernel<D><<<grid, K::THREADS, smem, st>>>(t->lay, t->d_tables, lo, total, flags, *h);
-  return cudaGetLastError();
+                        cudaStream_t st, bool allow_global) {
+  return allow_global && global_scratch(t) ? enumerate_dg<D, true>(t, lo, hi, flags, h, st)
+                                           : enumerate_dg<D, false>(t, lo, hi, flags, h, st);
 }
 
 }  // namespace
@@ -302,24 +350,24 @@ cudaError_t launch_real_schemes(const ts_tri *t, const uint64_t *signs, uint64_t
 }
 
 cudaError_t launch_enumerate(const ts_tri *t, uint64_t lo, uint64_t hi, uint32_t flags, ts_hist *h,
-                             cudaStream_t st) {
+                             cudaStream_t st, bool allow_global) {
   switch (t->d) {
-    case 1: return enumerate_d<1>(t, lo, hi, flags, h, st);
-    case 2: return enumerate_d<2>(t, lo, hi, flags, h, st);
-    case 3: return enumerate_d<3>(t, lo, hi, flags, h, st);
-    case 4: return enumerate_d<4>(t, lo, hi, flags, h, st);
-    case 5: return enumerate_d<5>(t, lo, hi, flags, h, st);
-    case 6: return enumerate_d<6>(t, lo, hi, flags, h, st);
-    case 7: return enumerate_d<7>(t, lo, hi, flags, h, st);
-    case 8: return enumerate_d<8>(t, lo, hi, flags, h, st);
-    case 9: return enumerate_d<9>(t, lo, hi, flags, h, st);
-    case 10: return enumerate_d<10>(t, lo, hi, flags, h, st);
-    case 11: return enumerate_d<11>(t, lo, hi, flags, h, st);
-    case 12: return enumerate_d<12>(t, lo, hi, flags, h, st);
-    case 13: return enumerate_d<13>(t, lo, hi, flags, h, st);
-    case 14: return enumerate_d<14>(t, lo, hi, flags, h, st);
-    case 15: return enumerate_d<15>(t, lo, hi, flags, h, st);
-    case 16: return enumerate_d<16>(t, lo, hi, flags, h, st);
+    case 1: return enumerate_d<1>(t, lo, hi, flags, h, st, allow_global);
+    case 2: return enumerate_d<2>(t, lo, hi, flags, h, st, allow_global);
+    case 3: return enumerate_d<3>(t, lo, hi, flags, h, st, allow_global);
+    case 4: return enumerate_d<4>(t, lo, hi, flags, h, st, allow_global);
+    case 5: return enumerate_d<5>(t, lo, hi, flags, h, st, allow_global);
+    case 6: return enumerate_d<6>(t, lo, hi, flags, h, st, allow_global);
+    case 7: return enumerate_d<7>(t, lo, hi, flags, h, st, allow_global);
+    case 8: return enumerate_d<8>(t, lo, hi, flags, h, st, allow_global);
+    case 9: return enumerate_d<9>(t, lo, hi, flags, h, st, allow_global);
+    case 10: return enumerate_d<10>(t, lo, hi, flags, h, st, allow_global);
+    case 11: return enumerate_d<11>(t, lo, hi, flags, h, st, allow_global);
+    case 12: return enumerate_d<12>(t, lo, hi, flags, h, st, allow_global);
+    case 13: return enumerate_d<13>(t, lo, hi, flags, h, st, allow_global);
+    case 14: return enumerate_d<14>(t, lo, hi, flags, h, st, allow_global);
+    case 15: return enumerate_d<15>(t, lo, hi, flags, h, st, allow_global);
+    case 16: return enumerate_d<16>(t, lo, hi, flags, h, st, allow_global);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -89,7 +89,7 @@ extern "C" ts_status ts_enumerate_noalloc(const ts_tri *t, uint64_t lo, uint64_t
   cudaStream_t st = (cudaStream_t)stream;
   // the array keeps the previous call's contents: start from zero
   if (cudaMemsetAsync(base, 0, kScratchBytes, st) != cudaSuccess) return TS_ECUDA;
-  if (lo < hi && tcurve::launch_enumerate(t, lo, hi, flags, &view, st) != cudaSuccess)
+  if (lo < hi && tcurve::launch_enumerate(t, lo, hi, flags, &view, st, false) != cudaSuccess)
     return TS_ECUDA;
   noalloc_compact<<<1, 256, 0, st>>>(view.d_keys, view.d_counts, view.d_err, view.d_failed, codes,
                                      counts, cap, n_out);

@@ -2,8 +2,8 @@
 
 This module is shared by the CPU oracle side (``oracle/``, ``tests/``) and the
 GPU side (``paper_2604_09221_gb300``, ``bench.py``).  It only *produces* inputs:
-triangulations of d*Delta_2 given as edge lists of lattice points (the input
-format of Sec. 2: "represented by its edge list") and bit-packed sign vectors.
+triangulations of d*Delta_2 given as edge lists of lattice points (Sec. 2
+takes a triangulation as its list of edges) and bit-packed sign vectors.
 It holds none of the method's arithmetic (no sign extension, no crossing test,
 no component or nesting logic).
 

@@ -76,6 +76,10 @@ def test_batch_matches_oracle_alone_and_in_the_mix(eng, orc, jobs):
     batch.set_tile(7, 64, 64 * 4)
     batch.run(graph=True)
     assert [hist_of(batch, j) for j in range(len(jobs))] == got
+    batch.set_tile(8, 128, 128 * 4, eng.TS_SCRATCH_GLOBAL)   # scratch in global memory
+    batch.set_tile(6, 96, 96 * 16, eng.TS_SCRATCH_SHARED)
+    batch.run(graph=True)
+    assert [hist_of(batch, j) for j in range(len(jobs))] == got
     # each job alone
     for j in (0, 5, len(jobs) - 1):
         alone = eng.Batch([tris[j]], [counts[j]], [bases[j]])

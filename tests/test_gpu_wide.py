@@ -62,6 +62,22 @@ def test_random_sign_vectors_wide(eng, orc, d):
         assert bad.size == 0, (d, idx, bad[:5])
 
 
+@pytest.mark.parametrize("d,where", [(7, 2), (9, 2), (10, 1), (13, 1), (16, 1), (16, 2)])
+def test_scratch_placements(eng, orc, d, where):
+    """Shared- and global-memory scratch give the oracle's codes and sweep
+    histograms (TS_SCRATCH_SHARED = 1, TS_SCRATCH_GLOBAL = 2)."""
+    e = ti.regular_triangulation(d, seed=500 + d)
+    tri = eng.Triangulation(d, e)
+    tri.set_kernel(eng.TS_KERNEL_TABLE)
+    tri.set_scratch(where)
+    otri = orc.triangles(d, e)
+    masks = ti.random_masks(3001, d, 5, stream=where)
+    assert (gpu_codes(tri, masks) == orc.real_schemes(d, otri, masks)).all()
+    h = eng.Histogram(8192, tri.code_words)
+    eng.enumerate_schemes(tri, 77, 77 + 2500, h, eng.TS_ENUM_SPLITMIX)
+    assert hist_rows(h) == counter(orc.real_schemes(d, otri, ti.splitmix_sign_vectors(d, 77, 2500)))
+
+
 @pytest.mark.parametrize("d", WIDE)
 def test_special_sign_vectors_wide(eng, orc, d):
     pts = [(i, j) for j in range(d + 1) for i in range(d + 1 - j)]

@@ -12,8 +12,8 @@ mathematics (not to the oracle itself).
   "mod 2 homology" method named in Sec. 2) on small degrees;
 * symmetry: the (Z/2)^3 action on signs and the S_3 action (Sec. 3);
 * Fig. 2: the printed oval-count distributions of three degree-8
-  triangulations, on a uniform sample, and "the bow tie realizes only even
-  oval counts".
+  triangulations, on a uniform sample, and the bow tie's restriction to even
+  oval counts stated beside the figure.
 """
 import collections
 import itertools
