@@ -18,13 +18,17 @@ The default line also carries a short serving run (Poisson job stream on the
 continuous-batching server, p50/p99 job latency).  Other workloads:
 
   --workload mixed    the mixed-degree batch: 32 seeded triangulations for each
-                      d in 5..9, sign-vector counts log-uniform in [2^10, 2^24],
+                      d in 5..10, sign-vector counts log-uniform in [2^10, 2^24],
                       one CUDA-graph launch per step, autotuned tiles
-  --workload serving  a longer Poisson stream: d uniform in 6..9, 2^8..2^22
+  --workload serving  a longer Poisson stream: d uniform in 6..16, 2^8..2^22
                       sign vectors per job, p50/p99 latency and schemes/s
 
+  --workload profile  a small sweep for profiler captures (--degree, --log2n,
+                      --kernel, --scratch, --splitmix); prints its rate, which
+                      is not a bench value
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--workload d7|mixed|serving]
+                  [--workload d7|mixed|serving|profile]
 """
 from __future__ import annotations
 
@@ -176,11 +180,19 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--workload", default="d7", choices=["d7", "mixed", "serving"])
+    ap.add_argument("--workload", default="d7", choices=["d7", "mixed", "serving", "profile"])
     ap.add_argument("--serve-seconds", type=float, default=6.0)
+    # the small case of --workload profile (for ncu captures; not a bench value)
+    ap.add_argument("--degree", type=int, default=D)
+    ap.add_argument("--log2n", type=int, default=26)
+    ap.add_argument("--kernel", default="auto", choices=["auto", "table", "specialized"])
+    ap.add_argument("--scratch", default="auto", choices=["auto", "shared", "global"])
+    ap.add_argument("--splitmix", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.workload == "profile":
+        return profile_case(args)
     if args.workload == "mixed":
         return mixed_workload(args)
     if args.workload == "serving":
@@ -322,6 +334,46 @@ def main():
     return 0
 
 
+def profile_case(args):
+    """A small sweep for profiler captures: masks [0, 2^log2n) of the bench's
+    seeded regular triangulation of the given degree, swept twice (plain masks,
+    or the splitmix64 stream for d >= 10 or with --splitmix)."""
+    import torch
+
+    import paper_2604_09221_gb300 as eng
+    import tcurve_inputs as ti
+    from paper_2604_09221_gb300 import build as _b
+    torch.cuda.set_device(0)
+    _b.build()
+    d = args.degree
+    tri = eng.Triangulation(d, ti.regular_triangulation(d, seed=TRI_SEED if d == D else d))
+    tri.set_kernel({"auto": eng.TS_KERNEL_AUTO, "table": eng.TS_KERNEL_TABLE,
+                    "specialized": eng.TS_KERNEL_SPECIALIZED}[args.kernel])
+    tri.set_scratch({"auto": eng.TS_SCRATCH_AUTO, "shared": eng.TS_SCRATCH_SHARED,
+                     "global": eng.TS_SCRATCH_GLOBAL}[args.scratch])
+    if args.kernel != "table" and d <= 9:
+        tri.prepare()
+    flags = eng.TS_ENUM_SPLITMIX if (args.splitmix or d > 9) else 0
+    n = 1 << args.log2n
+    h = eng.Histogram(1 << 14, tri.code_words)
+    ms = []
+    for _ in range(2):
+        h.clear()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        eng.enumerate_schemes(tri, 0, n, h, flags)
+        b.record()
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    codes, counts, failed = h.read()
+    assert failed == 0 and int(counts.sum()) == n
+    print(json.dumps({"profile_case": True, "degree": d, "n": n, "kernel": args.kernel,
+                      "scratch": args.scratch, "splitmix": bool(flags), "ms": ms,
+                      "schemes_per_s": n / (min(ms) / 1e3), "distinct": len(counts)}), flush=True)
+    return 0
+
+
 def hist_read_bytes(hist):
     """Bytes ts_hist_read copies to the host: the whole device table (keys and
     counts), the error word and the failure counter."""
@@ -362,7 +414,7 @@ def job_base(seed, stream):
     return ti.splitmix64_int(((seed & m) * 0x100000001B3 + stream) & m)
 
 
-def serving_run(seconds, degrees=(6, 7, 8, 9), per_degree=4, slots=8, seed=2027):
+def serving_run(seconds, degrees=tuple(range(6, 17)), per_degree=4, slots=8, seed=2027):
     """Poisson stream of jobs on the continuous-batching server: d uniform in
     `degrees`, 2^U(8,22) sign vectors per job (splitmix64 streams), resident
     triangulations (table-driven kernels, nothing compiled) and histograms.
@@ -415,7 +467,8 @@ def serving_run(seconds, degrees=(6, 7, 8, 9), per_degree=4, slots=8, seed=2027)
             "p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99),
             "mean_queue_ms": 1e3 * sum(r.queued for r in res) / len(res),
             "schemes_per_s": inst / wall, "slots": slots, "degrees": list(degrees),
-            "sign_vectors_per_job": "2^U(8,22)", "kernel": "table-driven (resident, uncompiled)",
+            "sign_vectors_per_job": "2^U(8,22)",
+            "kernel": "table-driven (resident, uncompiled; global scratch for d >= 10)",
             "peak_running": srv.peak_running, "seconds": wall}
 
 
@@ -425,7 +478,7 @@ def serving_workload(args, seconds):
     from paper_2604_09221_gb300 import build as _b
     _b.build()
     r = serving_run(seconds)
-    line = {"metric": "serving: p50/p99 job latency and schemes/s (d in 6..9)",
+    line = {"metric": "serving: p50/p99 job latency and schemes/s (d in 6..16)",
             "value": r["p99_ms"], "unit": "ms (p99 job latency)", "n_gpus": 1,
             "higher_is_better": False, "dtype": "u64", "data": "synthetic",
             "config": {"workload": "serving_poisson", "degrees": r["degrees"],
@@ -435,7 +488,7 @@ def serving_workload(args, seconds):
     return 0
 
 
-def mixed_workload(args, degrees=(5, 6, 7, 8, 9), per_degree=32, seed=31):
+def mixed_workload(args, degrees=(5, 6, 7, 8, 9, 10), per_degree=32, seed=31):
     """The mixed-degree batch as one CUDA-graph launch per step."""
     import numpy as np
     import torch

@@ -23,6 +23,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "engine.h"
 #include "tc_layout.h"
 #include "tc_table_sweep.cuh"
@@ -256,12 +258,27 @@ cudaError_t persistent_grid(F fn, int threads, size_t smem, uint64_t want, unsig
   return cudaSuccess;
 }
 
-// Global scratch of a launch: stream-ordered allocation, freed after it.
+// Global scratch of a launch: stream-ordered allocation, freed after it.  The
+// device's default pool is told to keep freed memory (release threshold at
+// its maximum), so repeated launches reuse it instead of mapping it again.
 struct GlobalScratch {
   u32 *p = nullptr;
   cudaStream_t st;
   explicit GlobalScratch(cudaStream_t s) : st(s) {}
-  cudaError_t alloc(size_t bytes) { return cudaMallocAsync((void **)&p, bytes, st); }
+  cudaError_t alloc(size_t bytes) {
+    static std::once_flag once[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64)
+      std::call_once(once[dev], [dev] {
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+          uint64_t keep = ~0ull;
+          cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+      });
+    return cudaMallocAsync((void **)&p, bytes, st);
+  }
   ~GlobalScratch() {
     if (p) cudaFreeAsync(p, st);
   }
