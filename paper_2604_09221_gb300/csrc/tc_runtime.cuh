@@ -282,6 +282,13 @@ __device__ __noinline__ u64 tc_backend(const TcScratch<K> &S, u32 nl, u32 nb, u3
     S.word(K::OFF_ADJ, p) |= 1u << r;
     internal |= 1u << p;
   }
+  // a star around the root (every oval outermost; nine in ten random sign
+  // vectors at d = 7): the code is '10' once per oval, no AHU needed
+  if (!(internal & ~(1u | (1u << root))) &&
+      (root == 0 || S.word(K::OFF_ADJ, 0) == (1u << root))) {
+    const u32 nb2 = 2 * (R - 1);
+    return (1ull << nb2) | (0xAAAAAAAAAAAAAAAAull & ((1ull << nb2) - 1));
+  }
   // 4. the path root -> region 0, reversed by re-rooting
   u32 k = 0, path = 1u;
   *S.byte(K::OFF_ORDER, 0) = (u8)root;
@@ -464,6 +471,20 @@ __device__ __noinline__ void tc_backend_wide(const TcScratch<K> &S, u32 nl, u32 
     if (p == NONE8) continue;
     *S.byte(K::OFF_WNS, r) = *S.byte(K::OFF_WFC, p);
     *S.byte(K::OFF_WFC, p) = (u8)r;
+  }
+  // a star around the root (every oval outermost): '10' once per oval
+  bool star = true;
+  for (u32 r = 0; r < R; ++r) star &= r == (u32)root || *S.byte(K::OFF_WFC, r) == NONE8;
+  if (star) {
+    const u32 q = 2 * (R - 1);
+#pragma unroll
+    for (u32 j = 0; j < K::CW; ++j) {
+      const int left = (int)q - 64 * (int)j;  // pattern bits in this word
+      code[j] = left >= 64 ? 0xAAAAAAAAAAAAAAAAull
+                           : (left > 0 ? 0xAAAAAAAAAAAAAAAAull & ((1ull << left) - 1) : 0ull);
+    }
+    code[q >> 6] |= 1ull << (q & 63u);
+    return;
   }
   // 4. AHU in post order
   u32 top = 0, aend = 0, qroot = 0;
