@@ -219,6 +219,7 @@ std::string jit_source(const Diamond &D) {
     << "  tc_clear_odd(S);\n";
   for (int v = 0; v < Vo; ++v) emit_vertex(v, "  ", nullptr);
   o << "  tc_unions(S, np);\n  np = 0;\n  const u32 nl_o = nl, nb_o = nb;\n"
+    << "  tc_flatten(S, nl_o);  // every instance of the warp then finds a half's root in one hop\n"
     << "  if (nl_o > 32u) {  // snapshot too small (never seen in practice): no reuse\n"
     << "    for (u32 j = 0; j < ireps; ++j) {\n"
     << "      const u64 key = tc_classify_slow(sig_hi | ((u64)(lane + 32u * j) << ishift), S, err);\n"

@@ -115,6 +115,18 @@ __device__ __forceinline__ void tc_unite(const TcScratch<K> &S, u32 a, u32 b, u3
   if (tc_odd(S, hi)) tc_set_odd(S, lo);
 }
 
+// Point every label straight at the root of its set, with the parity of the
+// whole path (one pass in label order: a parent is smaller than its child,
+// so it is already flat when the child is visited; roots keep themselves).
+template <class K>
+__device__ __forceinline__ void tc_flatten(const TcScratch<K> &S, u32 nl) {
+  for (u32 l = 0; l < nl; ++l) {
+    const u32 e = S.lpar(l);
+    const u32 pe = S.lpar(e & TcScratch<K>::LOW);
+    S.set_lpar(l, (pe & TcScratch<K>::LOW) | ((e ^ pe) & TcScratch<K>::TOP));
+  }
+}
+
 template <class K>
 __device__ __forceinline__ void tc_bpair(const TcScratch<K> &S, u32 i, u32 la, u32 lb) {
   S.word(K::OFF_BPAIR, i) = la | (lb << 16);
