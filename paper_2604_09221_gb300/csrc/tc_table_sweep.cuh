@@ -75,7 +75,8 @@ __device__ __forceinline__ TcCodeOut<K> tc_table_classify(const TcSig<K::W> &sig
       const u32 st = e & ~(((f >> 19) & 1u) & prev) & 1u;  // e starts a run of the fan
       l0 = i == 0 ? lu : l0;
       // a run after the first: join its label with the vertex's label
-      S.word(K::OFF_PEND, np) = lv | (lu << 16);
+      // (a predicated store: no branch, and no write when nothing joins)
+      if (st & any) S.word(K::OFF_PEND, np) = lv | (lu << 16);
       np += st & any;
       lv = any ? lv : (st ? lu : lv);
       any |= st;
