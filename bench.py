@@ -275,7 +275,7 @@ def main():
         eng.enumerate_schemes(tri, lo, lo + SLICE, hist, stream=stream)
         hist.read(stream)
         e2e_times.append(time.perf_counter() - t0)
-    d2h = hist_read_bytes(hist)
+    d2h = hist_read_bytes(hist, len(codes))
     e2e_ms = 1e3 * sum(e2e_times) / len(e2e_times)
     if pg:
         t = torch.tensor([e2e_ms], device="cuda")
@@ -374,13 +374,10 @@ def profile_case(args):
     return 0
 
 
-def hist_read_bytes(hist):
-    """Bytes ts_hist_read copies to the host: the whole device table (keys and
-    counts), the error word and the failure counter."""
-    slots = 16
-    while slots < 2 * hist.capacity:
-        slots <<= 1
-    return int(slots * (8 * hist.code_words + 8) + 4 + 8)
+def hist_read_bytes(hist, n_codes):
+    """Bytes ts_hist_read copies to the host: the number of packed entries,
+    the error word, the failure counter, then the packed codes and counts."""
+    return int(8 + 4 + 8 + n_codes * (8 * hist.code_words + 8))
 
 
 def plain_kernel(eng, tri, ti, stream):

@@ -204,7 +204,8 @@ ts_status ts_hist_read(ts_hist *hist, uint64_t *codes, uint64_t *counts, uint64_
  * counter bases[j] + i (ts_splitmix_masks; splitmix64 as published by Steele,
  * Lea and Flood: z = x + 0x9E3779B97F4A7C15; z = (z ^ z >> 30) *
  * 0xBF58476D1CE4E5B9; z = (z ^ z >> 27) * 0x94D049BB133111EB; z ^ z >> 31),
- * and adds each code to the job's own device histogram; if code_outputs is
+ * and adds each code to the job's own device histogram (room for
+ * min(hist_capacity, counts[j]) distinct codes, hist_capacity <= 2^20); if code_outputs is
  * not NULL and code_outputs[j] is not NULL (device, counts[j] *
  * ts_code_words(tris[j]) uint64), it also stores every code there.  For each
  * degree present, one persistent kernel serves all jobs of that degree,

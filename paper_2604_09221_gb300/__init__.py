@@ -208,6 +208,10 @@ class Histogram:
         self._h = h
         self.code_words = int(code_words)
         self.capacity = int(capacity)
+        slots = 16
+        while slots < 2 * self.capacity:
+            slots <<= 1
+        self.slots = slots  # the table holds up to this many distinct codes
 
     @property
     def handle(self):
@@ -228,8 +232,10 @@ class Histogram:
         _check(_lib.ts_hist_clear(self._h, _stream_handle(stream)), "ts_hist_clear")
 
     def read(self, stream=None, cap: int | None = None):
-        """(codes (n, code_words) uint64, counts (n,) uint64, n_failed), sorted by code."""
-        cap = self.capacity if cap is None else int(cap)
+        """(codes (n, code_words) uint64, counts (n,) uint64, n_failed), sorted by code.
+        Raises TSError(TS_EOVERFLOW) if more than ``cap`` codes (default: the
+        table's slots) are present or the device table overflowed."""
+        cap = self.slots if cap is None else int(cap)
         codes = np.zeros((max(cap, 1), self.code_words), dtype=np.uint64)
         counts = np.zeros(max(cap, 1), dtype=np.uint64)
         n = ctypes.c_uint64()
@@ -246,7 +252,7 @@ class Batch:
     vectors of splitmix64 counters bases[j] + i of tris[j]; see
     include/tcurve.h."""
 
-    def __init__(self, tris, counts, bases, code_outputs=None, hist_capacity: int = 1024):
+    def __init__(self, tris, counts, bases, code_outputs=None, hist_capacity: int = 1 << 16):
         n = len(tris)
         self.tris = list(tris)  # keep the triangulations alive
         th = (ctypes.c_void_p * n)(*[t.handle.value for t in tris])
@@ -264,6 +270,12 @@ class Batch:
         self.counts = cnt
         self.capacity = int(hist_capacity)
         self.degrees = sorted({t.d for t in tris})
+        self.read_cap = []  # codes a read of job j accepts: its table's slots
+        for n in self.counts:
+            cap, slots = min(self.capacity, max(int(n), 1)), 16
+            while slots < 2 * cap:
+                slots <<= 1
+            self.read_cap.append(slots)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -288,7 +300,7 @@ class Batch:
     def read(self, job: int, stream=None):
         """(codes, counts (n,) uint64, failed) of one job, sorted by code; codes
         has shape (n,) for one code word, (n, code_words) otherwise."""
-        cap = self.capacity
+        cap = self.read_cap[job]
         cw = self.tris[job].code_words
         codes = np.zeros(cap if cw == 1 else (cap, cw), dtype=np.uint64)
         counts = np.zeros(cap, dtype=np.uint64)

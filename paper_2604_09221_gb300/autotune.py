@@ -53,7 +53,7 @@ def tune_degree(tris, counts, bases, threads: Iterable[int] = THREADS,
     from . import Batch, TSError
     d = tris[0].d
     assert all(t.d == d for t in tris)
-    sub = Batch(tris, counts, bases, hist_capacity=1024)
+    sub = Batch(tris, counts, bases)
     best = None
     for s in (scratch_choices(d) if scratch is None else scratch):
         for t in threads:

@@ -247,10 +247,11 @@ struct ts_batch {
   std::vector<DevJob> jobs;  // host copies (chunk0 per group)
   std::vector<int> degree, cws;       // degree and code words of every job
   std::vector<size_t> kofs;           // first key word of every job's histogram
-  size_t key_words = 0;
+  std::vector<size_t> cofs;           // first count of every job's histogram
+  std::vector<uint64_t> jslots;       // slots of every job's histogram
+  size_t key_words = 0, count_words = 0;
   std::vector<Group> groups;
-  uint64_t hslots = 0;
-  uint64_t *d_keys = nullptr;  // per job: hslots x code_words
+  uint64_t *d_keys = nullptr;  // per job: slots x code_words
   unsigned long long *d_counts = nullptr;
   uint32_t *d_err = nullptr;
   unsigned long long *d_failed = nullptr;
@@ -324,7 +325,7 @@ cudaError_t launch_group(ts_batch *b, ts_batch::Group &g, cudaStream_t st) {
 cudaError_t enqueue(ts_batch *b, cudaStream_t st) {
   const size_t nj = b->jobs.size();
   cudaError_t e = cudaMemsetAsync(b->d_keys, 0, b->key_words * 8, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counts, 0, nj * b->hslots * 8, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counts, 0, b->count_words * 8, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, 4, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_failed, 0, 8, st);
   if (e == cudaSuccess) e = cudaEventRecord(b->fork, st);
@@ -350,21 +351,25 @@ ts_status ts_batch_create(int njobs, ts_tri *const *tris, const uint64_t *counts
   *out = nullptr;
   ts_batch *b = new (std::nothrow) ts_batch();
   if (!b) return TS_ENOMEM;
-  uint64_t s = 16;
-  while (s < 2 * hist_capacity) s <<= 1;
-  b->hslots = s;
   cudaError_t e = cudaGetDevice(&b->device);
   for (int j = 0; j < njobs; ++j) {
     if (!tris[j]) {
       ts_batch_free(b);
       return TS_EINVAL;
     }
+    // a job of n sign vectors has at most n distinct schemes
+    const uint64_t cap = std::min<uint64_t>(hist_capacity, std::max<uint64_t>(counts[j], 1));
+    uint64_t s = 16;
+    while (s < 2 * cap) s <<= 1;
+    b->jslots.push_back(s);
     b->kofs.push_back(b->key_words);
+    b->cofs.push_back(b->count_words);
     b->cws.push_back(tris[j]->cw);
     b->key_words += s * tris[j]->cw;
+    b->count_words += s;
   }
   if (e == cudaSuccess) e = cudaMalloc(&b->d_keys, b->key_words * 8);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_counts, (size_t)njobs * s * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_counts, b->count_words * 8);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_err, 4);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_failed, 8);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
@@ -381,8 +386,8 @@ ts_status ts_batch_create(int njobs, ts_tri *const *tris, const uint64_t *counts
     x.base = bases[j];
     x.codes = code_outputs ? reinterpret_cast<u64 *>(code_outputs[j]) : nullptr;
     x.hkeys = reinterpret_cast<u64 *>(b->d_keys + b->kofs[j]);
-    x.hcnt = b->d_counts + (size_t)j * s;
-    x.hslots = s;
+    x.hcnt = b->d_counts + b->cofs[j];
+    x.hslots = b->jslots[j];
     b->jobs.push_back(x);
     b->degree.push_back(t->d);
     if (!gi.count(t->d)) {
@@ -483,20 +488,21 @@ ts_status ts_batch_read(ts_batch *b, int job, uint64_t *codes, uint64_t *counts,
     return TS_EINVAL;
   cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
   const int cw = b->cws[job];
-  std::vector<uint64_t> k(b->hslots * cw);
-  std::vector<unsigned long long> c(b->hslots);
+  const uint64_t hs = b->jslots[job];
+  std::vector<uint64_t> k(hs * cw);
+  std::vector<unsigned long long> c(hs);
   uint32_t err = 0;
   unsigned long long failed = 0;
   if (e == cudaSuccess)
     e = cudaMemcpy(k.data(), b->d_keys + b->kofs[job], k.size() * 8, cudaMemcpyDeviceToHost);
   if (e == cudaSuccess)
-    e = cudaMemcpy(c.data(), b->d_counts + (size_t)job * b->hslots, b->hslots * 8,
+    e = cudaMemcpy(c.data(), b->d_counts + b->cofs[job], hs * 8,
                    cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemcpy(&err, b->d_err, 4, cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemcpy(&failed, b->d_failed, 8, cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_st(e);
   std::vector<uint64_t> idx;
-  for (uint64_t s = 0; s < b->hslots; ++s) {
+  for (uint64_t s = 0; s < hs; ++s) {
     bool nz = false;
     for (int w = 0; w < cw; ++w) nz |= k[s * cw + w] != 0;
     if (nz) idx.push_back(s);

@@ -78,6 +78,10 @@ struct ts_hist {
   uint32_t *d_err = nullptr;          // device error word
   unsigned long long *d_failed = nullptr;
   unsigned long long *d_work = nullptr;  // work counter of the persistent sweep
+  // compaction buffers of ts_hist_read: the occupied slots, packed
+  uint64_t *d_ckeys = nullptr;        // slots * cw words
+  unsigned long long *d_ccnt = nullptr;  // slots counts
+  unsigned long long *d_cn = nullptr;    // number of packed entries
   int device = 0;
 };
 
@@ -88,6 +92,9 @@ cudaError_t launch_real_schemes(const ts_tri *tri, const uint64_t *signs, uint64
 cudaError_t launch_enumerate(const ts_tri *tri, uint64_t lo, uint64_t hi, uint32_t flags,
                              ts_hist *hist, cudaStream_t stream, bool allow_global = true);
 cudaError_t launch_hist_clear(ts_hist *hist, cudaStream_t stream);
+// Pack the occupied slots of the table into d_ckeys / d_ccnt (count flags
+// removed) and their number into d_cn.
+cudaError_t launch_hist_compact(ts_hist *hist, cudaStream_t stream);
 cudaError_t launch_splitmix_masks(int d, uint64_t base, uint64_t n, uint64_t *out,
                                   cudaStream_t stream);
 

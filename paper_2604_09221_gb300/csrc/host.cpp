@@ -452,6 +452,9 @@ ts_status ts_hist_create(uint64_t capacity, int code_words, ts_hist **out) {
   if (e == cudaSuccess) e = cudaMalloc(&h->d_err, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&h->d_failed, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMalloc(&h->d_work, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_ckeys, s * code_words * sizeof(uint64_t));
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_ccnt, s * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_cn, sizeof(unsigned long long));
   if (e == cudaSuccess) e = launch_hist_clear(h, 0);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
@@ -470,6 +473,9 @@ void ts_hist_free(ts_hist *h) {
   if (h->d_err) cudaFree(h->d_err);
   if (h->d_failed) cudaFree(h->d_failed);
   if (h->d_work) cudaFree(h->d_work);
+  if (h->d_ckeys) cudaFree(h->d_ckeys);
+  if (h->d_ccnt) cudaFree(h->d_ccnt);
+  if (h->d_cn) cudaFree(h->d_cn);
   delete h;
 }
 
@@ -495,39 +501,43 @@ ts_status ts_enumerate(const ts_tri *t, uint64_t lo, uint64_t hi, uint32_t flags
 ts_status ts_hist_read(ts_hist *h, uint64_t *codes, uint64_t *counts, uint64_t cap,
                        uint64_t *n_out, uint64_t *n_failed, void *stream) {
   if (!h || !n_out || (cap && (!codes || !counts))) return TS_EINVAL;
-  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
-  std::vector<uint64_t> keys(h->slots * h->cw);
-  std::vector<unsigned long long> cnt(h->slots);
+  cudaStream_t st = (cudaStream_t)stream;
+  // pack the occupied slots on the device; only those cross to the host
+  cudaError_t e = launch_hist_compact(h, st);
+  unsigned long long n = 0, failed = 0;
   uint32_t err = 0;
-  unsigned long long failed = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&n, h->d_cn, sizeof(n), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&err, h->d_err, sizeof(err), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess)
-    e = cudaMemcpy(keys.data(), h->d_keys, keys.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(cnt.data(), h->d_counts, cnt.size() * sizeof(unsigned long long),
-                   cudaMemcpyDeviceToHost);
-  if (e == cudaSuccess) e = cudaMemcpy(&err, h->d_err, sizeof(err), cudaMemcpyDeviceToHost);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(&failed, h->d_failed, sizeof(failed), cudaMemcpyDeviceToHost);
+    e = cudaMemcpyAsync(&failed, h->d_failed, sizeof(failed), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_status(e);
   const int cw = h->cw;
-  std::vector<uint64_t> idx;
-  for (uint64_t s = 0; s < h->slots; ++s) {
-    bool nz = false;
-    for (int w = 0; w < cw; ++w) nz |= keys[s * cw + w] != 0;
-    if (nz) idx.push_back(s);
+  std::vector<uint64_t> keys(n * cw);
+  std::vector<unsigned long long> cnt(n);
+  if (n) {
+    e = cudaMemcpyAsync(keys.data(), h->d_ckeys, keys.size() * sizeof(uint64_t),
+                        cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(cnt.data(), h->d_ccnt, n * sizeof(unsigned long long),
+                          cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(e);
   }
+  std::vector<uint64_t> idx(n);
+  for (uint64_t i = 0; i < n; ++i) idx[i] = i;
   std::sort(idx.begin(), idx.end(), [&](uint64_t a, uint64_t b) {
     for (int w = cw - 1; w >= 0; --w)
       if (keys[a * cw + w] != keys[b * cw + w]) return keys[a * cw + w] < keys[b * cw + w];
     return false;
   });
-  *n_out = idx.size();
+  *n_out = n;
   if (n_failed) *n_failed = failed;
-  for (uint64_t r = 0; r < idx.size() && r < cap; ++r) {
+  for (uint64_t r = 0; r < n && r < cap; ++r) {
     for (int w = 0; w < cw; ++w) codes[r * cw + w] = keys[idx[r] * cw + w];
-    counts[r] = cnt[idx[r]] & kCountMask;
+    counts[r] = cnt[idx[r]];
   }
-  if (idx.size() > cap) return TS_EOVERFLOW;
+  if (n > cap) return TS_EOVERFLOW;
   return err_word_status(err);
 }
 

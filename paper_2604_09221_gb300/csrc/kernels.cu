@@ -235,6 +235,29 @@ __global__ void hist_clear_kernel(ts_hist h) {
   }
 }
 
+// Pack occupied slots (a nonzero key word) into the compaction buffers: one
+// atomic per warp, lanes ranked by a ballot.
+__global__ void hist_compact_kernel(ts_hist h) {
+  const uint64_t n = h.slots;
+  const u32 lane = threadIdx.x & 31u;
+  for (uint64_t base = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~31ull; base < n;
+       base += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t s = base + lane;
+    bool nz = false;
+    if (s < n)
+      for (int w = 0; w < h.cw; ++w) nz |= h.d_keys[s * h.cw + w] != 0;
+    const unsigned ball = __ballot_sync(0xffffffffu, nz);
+    unsigned long long first = 0;
+    if (lane == 0 && ball) first = atomicAdd(h.d_cn, (unsigned long long)__popc(ball));
+    first = __shfl_sync(0xffffffffu, first, 0);
+    if (nz) {
+      const uint64_t o = first + __popc(ball & ((1u << lane) - 1u));
+      for (int w = 0; w < h.cw; ++w) h.d_ckeys[o * h.cw + w] = h.d_keys[s * h.cw + w];
+      h.d_ccnt[o] = h.d_counts[s] & ((1ull << 62) - 1);
+    }
+  }
+}
+
 // ----------------------------------------------------------- launch ----
 
 int sm_count() {
@@ -393,6 +416,14 @@ cudaError_t launch_splitmix_masks(int d, uint64_t base, uint64_t n, uint64_t *ou
   const uint64_t blocks = (n + 255) / 256;
   splitmix_masks_kernel<<<(unsigned)(blocks < 4096 ? (blocks ? blocks : 1) : 4096), 256, 0, st>>>(
       base, n, (uint32_t)((d + 1) * (d + 2) / 2), out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hist_compact(ts_hist *h, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(h->d_cn, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  const uint64_t blocks = (h->slots + 255) / 256;
+  hist_compact_kernel<<<(unsigned)(blocks < 2048 ? blocks : 2048), 256, 0, st>>>(*h);
   return cudaGetLastError();
 }
 

@@ -58,28 +58,40 @@ class GpuExecutor:
     the slot's resident histogram, plus ts_splitmix_masks and ts_real_schemes
     when the job wants codes."""
 
-    def __init__(self, tris, slots: int, hist_capacity: int = 4096, kernel: Optional[int] = None):
-        import torch
+    # histogram size classes: a job of n sign vectors has at most n distinct
+    # schemes; the class is the smallest >= n, capped (random sign vectors of
+    # degree <= 16 give some 10^4 schemes per 2^22 vectors; a job that still
+    # overflows is re-run with a table of its own size)
+    CLASSES = (1 << 10, 1 << 14, 1 << 18)
 
-        from . import Histogram
+    def __init__(self, tris, slots: int, kernel: Optional[int] = None):
+        import torch
         self.torch = torch
         self.tris = list(tris)
         if kernel is not None:
             for t in self.tris:
                 t.set_kernel(kernel)
         self.streams = [torch.cuda.Stream() for _ in range(slots)]
-        # one resident histogram per slot and code width (1 to 4 words)
-        cws = sorted({t.code_words for t in self.tris})
-        self.hists = [{cw: Histogram(hist_capacity, cw) for cw in cws} for _ in range(slots)]
+        # resident histograms per slot, by (code words, size class), made on first use
+        self.hists: List[Dict[tuple, object]] = [{} for _ in range(slots)]
+        self.cur: Dict[int, object] = {}
         self.events = [torch.cuda.Event() for _ in range(slots)]
         self.buffers: Dict[int, tuple] = {}
+
+    def _hist(self, slot: int, cw: int, n: int):
+        from . import Histogram
+        cap = next((c for c in self.CLASSES if c >= n), self.CLASSES[-1])
+        h = self.hists[slot].get((cw, cap))
+        if h is None:
+            h = self.hists[slot][(cw, cap)] = Histogram(cap, cw)
+        return h
 
     def start(self, slot: int, job: Job):
         from . import TS_ENUM_SPLITMIX, enumerate_schemes, splitmix_masks
         torch = self.torch
         st = self.streams[slot]
         tri = self.tris[job.tri]
-        h = self.hists[slot][tri.code_words]
+        h = self.cur[slot] = self._hist(slot, tri.code_words, job.n)
         with torch.cuda.stream(st):
             h.clear(st)
             enumerate_schemes(tri, job.base, job.base + job.n, h, TS_ENUM_SPLITMIX, stream=st)
@@ -99,10 +111,18 @@ class GpuExecutor:
         return self.events[slot].query()
 
     def result(self, slot: int, job: Job):
-        from . import code_to_int
+        from . import TS_ENUM_SPLITMIX, Histogram, TSError, code_to_int, enumerate_schemes
         st = self.streams[slot]
         tri = self.tris[job.tri]
-        codes, counts, failed = self.hists[slot][tri.code_words].read(st)
+        try:
+            codes, counts, failed = self.cur[slot].read(st)
+        except TSError as e:
+            if e.status != 5:  # TS_EOVERFLOW: more schemes than the class holds
+                raise
+            big = Histogram(job.n, tri.code_words)
+            enumerate_schemes(tri, job.base, job.base + job.n, big, TS_ENUM_SPLITMIX, stream=st)
+            codes, counts, failed = big.read(st)
+            big.close()
         if failed:
             raise RuntimeError(f"{failed} instances failed")
         hist = {code_to_int(c): int(k) for c, k in zip(codes, counts)}
