@@ -188,6 +188,7 @@ def main():
     ap.add_argument("--kernel", default="auto", choices=["auto", "table", "specialized"])
     ap.add_argument("--scratch", default="auto", choices=["auto", "shared", "global"])
     ap.add_argument("--splitmix", action="store_true")
+    ap.add_argument("--occupancy", type=int, default=0)
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -351,6 +352,7 @@ def profile_case(args):
                     "specialized": eng.TS_KERNEL_SPECIALIZED}[args.kernel])
     tri.set_scratch({"auto": eng.TS_SCRATCH_AUTO, "shared": eng.TS_SCRATCH_SHARED,
                      "global": eng.TS_SCRATCH_GLOBAL}[args.scratch])
+    tri.set_occupancy(args.occupancy)
     if args.kernel != "table" and d <= 9:
         tri.prepare()
     flags = eng.TS_ENUM_SPLITMIX if (args.splitmix or d > 9) else 0
@@ -369,7 +371,8 @@ def profile_case(args):
     codes, counts, failed = h.read()
     assert failed == 0 and int(counts.sum()) == n
     print(json.dumps({"profile_case": True, "degree": d, "n": n, "kernel": args.kernel,
-                      "scratch": args.scratch, "splitmix": bool(flags), "ms": ms,
+                      "scratch": args.scratch, "occupancy": args.occupancy,
+                      "splitmix": bool(flags), "ms": ms,
                       "schemes_per_s": n / (min(ms) / 1e3), "distinct": len(counts)}), flush=True)
     return 0
 
@@ -465,7 +468,7 @@ def serving_run(seconds, degrees=tuple(range(6, 17)), per_degree=4, slots=8, see
             "mean_queue_ms": 1e3 * sum(r.queued for r in res) / len(res),
             "schemes_per_s": inst / wall, "slots": slots, "degrees": list(degrees),
             "sign_vectors_per_job": "2^U(8,22)",
-            "kernel": "table-driven (resident, uncompiled; global scratch for d >= 10)",
+            "kernel": "table-driven (resident, uncompiled; global scratch from d = 7)",
             "peak_running": srv.peak_running, "seconds": wall}
 
 

@@ -119,17 +119,25 @@ ts_status ts_real_schemes(const ts_tri *tri, const uint64_t *signs, uint64_t n,
 #define TS_KERNEL_SPECIALIZED 2
 ts_status ts_set_kernel(ts_tri *tri, int kind);
 
-/* Where the table-driven kernels keep their per-instance scratch (labels,
- * union-find, region tree; 0.1 to 3.7 KB per instance, growing with d).
+/* Where the kernels keep their per-instance scratch (labels, union-find,
+ * region tree; 0.1 to 3.7 KB per instance, growing with d).
  *   TS_SCRATCH_SHARED: shared memory (few resident warps for large d).
  *   TS_SCRATCH_GLOBAL: device memory, L1/L2-resident, allocated per launch
- *     with cudaMallocAsync on the launch's stream and freed after it.
- *   TS_SCRATCH_AUTO (default): global for d >= 10, shared below.
- * Results are identical. */
+ *     with cudaMallocAsync on the launch's stream and freed after it (the
+ *     device's default memory pool is set to keep freed memory).
+ *   TS_SCRATCH_AUTO (default): for the table-driven kernels global from
+ *     d = 7, shared below; shared for the specialised kernels.
+ * Changing it drops the specialised kernels already built for tri (they are
+ * rebuilt on next use).  Results are identical. */
 #define TS_SCRATCH_AUTO 0
 #define TS_SCRATCH_SHARED 1
 #define TS_SCRATCH_GLOBAL 2
 ts_status ts_set_scratch(ts_tri *tri, int where);
+
+/* Resident blocks per SM the specialised kernels are compiled for (their
+ * register budget): 1..16, or 0 for the default (2 with shared scratch, 4
+ * with global scratch).  Drops kernels already built for tri. */
+ts_status ts_set_occupancy(ts_tri *tri, int blocks_per_sm);
 
 /* Build the specialised kernels now (NVRTC compile and module load on the
  * current device; about a second).  Call it before capturing launches of

@@ -74,6 +74,7 @@ def _load():
                 "ts_scheme_string": ([I, P, I, ctypes.c_char_p, ctypes.c_size_t], I),
                 "ts_set_kernel": ([P, I], I),
                 "ts_set_scratch": ([P, I], I),
+                "ts_set_occupancy": ([P, I], I),
                 "ts_prepare": ([P], I),
                 "ts_specialized_log": ([P, ctypes.c_char_p, ctypes.c_size_t], I),
                 "ts_specialized_source": ([I, P, I, I, ctypes.c_char_p, ctypes.c_size_t,
@@ -152,8 +153,12 @@ class Triangulation:
         _check(_lib.ts_set_kernel(self._h, int(kind)), "ts_set_kernel")
 
     def set_scratch(self, where: int):
-        """TS_SCRATCH_AUTO / TS_SCRATCH_SHARED / TS_SCRATCH_GLOBAL (table-driven kernels)."""
+        """TS_SCRATCH_AUTO / TS_SCRATCH_SHARED / TS_SCRATCH_GLOBAL."""
         _check(_lib.ts_set_scratch(self._h, int(where)), "ts_set_scratch")
+
+    def set_occupancy(self, blocks_per_sm: int):
+        """Blocks per SM the specialised kernels are compiled for (0: default)."""
+        _check(_lib.ts_set_occupancy(self._h, int(blocks_per_sm)), "ts_set_occupancy")
 
     def prepare(self):
         """Compile and load the specialised kernels now (ts_prepare)."""

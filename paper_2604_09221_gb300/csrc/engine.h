@@ -16,7 +16,7 @@ namespace tcurve {
 
 constexpr int kMaxDegree = 16;     // |A| <= 153: three sign words, four code words
 constexpr int kMaxSpecialized = 9;  // triangulation-specialised kernels: one sign word
-constexpr int kGlobalScratchFrom = 10;  // TS_SCRATCH_AUTO: global scratch from this degree
+constexpr int kGlobalScratchFrom = 7;  // TS_SCRATCH_AUTO: table kernels use global scratch from here
 
 // Count words of multi-word histograms carry two flags in their top bits
 // (slot being written / key published); the count is the rest.
@@ -64,7 +64,8 @@ struct ts_tri {
   uint32_t *d_err = nullptr;     // device error word (scratch, owned here)
   tcurve::Diamond dia;
   int kernel = 0;                // TS_KERNEL_*
-  int scratch = 0;               // TS_SCRATCH_* (table-driven kernels)
+  int scratch = 0;               // TS_SCRATCH_* (both kernel families)
+  int occupancy = 0;             // target blocks per SM of the specialised kernels (0: default)
   std::mutex jit_mu;
   std::shared_ptr<tcurve::JitModule> jit;
   std::string jit_log;
@@ -98,8 +99,13 @@ cudaError_t launch_hist_compact(ts_hist *hist, cudaStream_t stream);
 cudaError_t launch_splitmix_masks(int d, uint64_t base, uint64_t n, uint64_t *out,
                                   cudaStream_t stream);
 
-// Specialised kernels (jit.cpp).
-std::string jit_source(const Diamond &D);
+// Stream-ordered device allocation for per-launch global scratch (the
+// device's default pool keeps freed memory); free with cudaFreeAsync.
+cudaError_t scratch_alloc(void **p, size_t bytes, cudaStream_t stream);
+
+// Specialised kernels (jit.cpp).  global: per-thread scratch in global memory
+// (128-thread blocks); min_blocks: blocks per SM the register budget is set for.
+std::string jit_source(const Diamond &D, bool global = false, int min_blocks = 2);
 // Compile the generated source with NVRTC for sm_103a; returns the cubin (or
 // an empty string and the log in *log).
 std::string jit_compile_cubin(const std::string &src, std::string *log);

@@ -353,7 +353,15 @@ ts_status ts_set_kernel(ts_tri *t, int kind) {
 
 ts_status ts_set_scratch(ts_tri *t, int where) {
   if (!t || where < TS_SCRATCH_AUTO || where > TS_SCRATCH_GLOBAL) return TS_EINVAL;
+  if (where != t->scratch) jit_release(t);  // the specialised kernels are rebuilt for it
   t->scratch = where;
+  return TS_OK;
+}
+
+ts_status ts_set_occupancy(ts_tri *t, int blocks_per_sm) {
+  if (!t || blocks_per_sm < 0 || blocks_per_sm > 16) return TS_EINVAL;
+  if (blocks_per_sm != t->occupancy) jit_release(t);
+  t->occupancy = blocks_per_sm;
   return TS_OK;
 }
 

@@ -38,7 +38,13 @@ constexpr int kJitThreads = 256;
 
 typedef TcLayout Layout;
 
-Layout layout_for(const Diamond &D) { return tc_layout(D.d, false, kJitThreads); }
+// Scratch layout of the specialised kernels: 256-thread blocks (fewer if two
+// do not fit shared memory) with shared scratch, 128 with global scratch.
+Layout layout_for(const Diamond &D, bool global) {
+  Layout L = tc_layout(D.d, false, global ? 128 : kJitThreads);
+  if (global) L.threads = 128;
+  return L;
+}
 
 // ---- NVRTC, opened on first use ----
 struct Nvrtc {
@@ -118,6 +124,7 @@ struct JitModule {
   CUmodule mod = nullptr;
   CUfunction real = nullptr, enumerate = nullptr, blocks = nullptr;
   Layout L{};
+  bool global = false;  // per-thread scratch in global memory
   size_t smem_real = 0, smem_enum = 0;
   int bpsm_real = 0, bpsm_enum = 0, bpsm_blocks = 0;
   ~JitModule() {
@@ -125,8 +132,8 @@ struct JitModule {
   }
 };
 
-std::string jit_source(const Diamond &D) {
-  const Layout L = layout_for(D);
+std::string jit_source(const Diamond &D, bool global, int min_blocks) {
+  const Layout L = layout_for(D, global);
   const int d = D.d, V = D.V;
   std::ostringstream o;
   o << "// T-curve real-scheme kernels specialised to one triangulation of " << d
@@ -136,6 +143,7 @@ std::string jit_source(const Diamond &D) {
   c("D", d); c("V", V); c("NPOINTS", (d + 1) * (d + 2) / 2); c("RMAX", L.rmax); c("NB", L.nb);
   c("THREADS", L.threads); c("HASH", L.hash); c("LBYTES", L.lbytes); c("CODE64", L.code64);
   c("PCAP", L.pcap); c("WODD", L.wodd); c("WORDS", L.words); c("B", d + 1); c("SNAPW", L.snapw);
+  c("GSCR", global ? 1 : 0); c("MINB", min_blocks);
   c("OFF_LPAR", L.off_lpar); c("OFF_CAND", L.off_cand); c("OFF_LAB", L.off_lab);
   c("OFF_BPAIR", L.off_bpair); c("OFF_PEND", L.off_pend); c("OFF_ADJ", L.off_adj);
   c("OFF_RLAB", L.off_rlab); c("OFF_TPAR", L.off_tpar); c("OFF_ORDER", L.off_order);
@@ -153,13 +161,21 @@ std::string jit_source(const Diamond &D) {
 
   // One vertex of the sweep.  mid_sig: expression of the middle-row mask word
   // (the block sweep varies it per instance), or empty to read slo/shi.
-  auto emit_vertex = [&](int v, const char *ind, const char *mid_sig) {
+  // check_flush: emit the test that applies the pending joins when the list
+  // might overflow (left out where the joins pushed since the last flush
+  // provably fit).
+  auto pushes_at = [&](int v) {
+    const int m = (int)D.fan[v].size();
+    return (m >= 2 ? m - 1 : 0) + (int)anti_at[v].size();
+  };
+  auto emit_vertex = [&](int v, const char *ind, const char *mid_sig, bool check_flush) {
     const auto &fan = D.fan[v];
     const auto &lk = D.link[v];
     const int m = (int)fan.size();
     o << ind << "// vertex " << v << " (" << D.x[v] << "," << D.y[v] << ")\n";
-    const int pushes = (m >= 2 ? m - 1 : 0) + (int)anti_at[v].size();
-    if (pushes) o << ind << "if (np > TcK::PCAP - " << pushes << "u) { tc_unions(S, np); np = 0; }\n";
+    const int pushes = pushes_at(v);
+    if (pushes && check_flush)
+      o << ind << "if (np > TcK::PCAP - " << pushes << "u) { tc_unions(S, np); np = 0; }\n";
     if (mid_sig && D.y[v] == 0)
       o << ind << "const u32 s" << v << " = ((" << mid_sig << " >> " << D.k[v] << ") & 1u) ^ " << D.c[v]
         << "u;\n";
@@ -183,7 +199,7 @@ std::string jit_source(const Diamond &D) {
         for (int i = 1; i < m; ++i) {
           o << ind << "  { const u32 st = e" << i;
           if (lk[i]) o << " & (e" << i - 1 << " ^ 1u)";
-          o << "; S.word(TcK::OFF_PEND, np) = L" << v << " | (L" << fan[i]
+          o << "; if (st & any) S.word(TcK::OFF_PEND, np) = L" << v << " | (L" << fan[i]
             << " << 16); np += st & any; any |= st; }\n";
         }
       }
@@ -204,7 +220,7 @@ std::string jit_source(const Diamond &D) {
   o << "__device__ __forceinline__ u64 tc_classify(u64 sig, const TcS &S, u32 &err) {\n"
     << "  const u32 slo = (u32)sig, shi = (u32)(sig >> 32);\n  u32 nl = 0, nb = 0, np = 0;\n"
     << "  tc_clear_odd(S);\n";
-  for (int v = 0; v < V; ++v) emit_vertex(v, "  ", nullptr);
+  for (int v = 0; v < V; ++v) emit_vertex(v, "  ", nullptr, true);
   o << "  tc_unions(S, np);\n  return tc_backend(S, nl, nb, err);\n}\n\n";
   o << "__device__ __noinline__ u64 tc_classify_slow(u64 sig, const TcS &S, u32 &err) {\n"
     << "  return tc_classify(sig, S, err);\n}\n\n";
@@ -217,7 +233,7 @@ std::string jit_source(const Diamond &D) {
     << "  const u32 lane = threadIdx.x & 31u;\n"
     << "  const u32 slo = (u32)sig_hi, shi = (u32)(sig_hi >> 32);\n  u32 nl = 0, nb = 0, np = 0;\n"
     << "  tc_clear_odd(S);\n";
-  for (int v = 0; v < Vo; ++v) emit_vertex(v, "  ", nullptr);
+  for (int v = 0; v < Vo; ++v) emit_vertex(v, "  ", nullptr, true);
   o << "  tc_unions(S, np);\n  np = 0;\n  const u32 nl_o = nl, nb_o = nb;\n"
     << "  tc_flatten(S, nl_o);  // every instance of the warp then finds a half's root in one hop\n"
     << "  if (nl_o > 32u) {  // snapshot too small (never seen in practice): no reuse\n"
@@ -234,7 +250,11 @@ std::string jit_source(const Diamond &D) {
     << "    for (u32 w = 1; w < TcK::WODD; ++w) S.word(TcK::OFF_ODD, w) = 0;\n"
     << "    nl = nl_o; nb = nb_o; np = 0;\n"
     << "    const u32 sm = slo | ((lane + 32u * j) << ishift);\n";
-  for (int v = Vo; v < V; ++v) emit_vertex(v, "    ", "sm");
+  // the middle row starts from an empty join list: its flush tests are
+  // needed only if all of its joins might not fit
+  int mid_pushes = 0;
+  for (int v = Vo; v < V; ++v) mid_pushes += pushes_at(v);
+  for (int v = Vo; v < V; ++v) emit_vertex(v, "    ", "sm", mid_pushes > L.pcap);
   o << "    tc_unions(S, np);\n"
     << "    const u64 key = tc_backend(S, nl, nb, err);\n"
     << "    failed += key == 0;\n"
@@ -295,6 +315,14 @@ std::string jit_compile_uncached(const std::string &src, std::string *log) {
   return out;
 }
 
+// Configuration of the specialised kernels of a triangulation: scratch in
+// global memory when asked for (TS_SCRATCH_GLOBAL), blocks per SM from
+// ts_set_occupancy (default 2 with shared scratch, 4 with global scratch).
+void jit_config(const ts_tri *t, bool *global, int *min_blocks) {
+  *global = t->scratch == TS_SCRATCH_GLOBAL;
+  *min_blocks = t->occupancy > 0 ? t->occupancy : (*global ? 4 : 2);
+}
+
 cudaError_t jit_prepare(ts_tri *t) {
   if (t->d > kMaxSpecialized) return cudaErrorNotSupported;
   std::lock_guard<std::mutex> g(t->jit_mu);
@@ -303,18 +331,22 @@ cudaError_t jit_prepare(ts_tri *t) {
   if (!dr.ok) return cudaErrorNotSupported;
   cudaError_t e = cudaFree(0);  // make the primary context current
   if (e != cudaSuccess) return e;
-  const std::string src = jit_source(t->dia);
+  bool global = false;
+  int minb = 2;
+  jit_config(t, &global, &minb);
+  const std::string src = jit_source(t->dia, global, minb);
   const std::string cubin = jit_compile_cubin(src, &t->jit_log);
   if (cubin.empty()) return cudaErrorInvalidSource;
   auto mod = std::make_shared<JitModule>();
-  mod->L = layout_for(t->dia);
+  mod->L = layout_for(t->dia, global);
+  mod->global = global;
   if (dr.load(&mod->mod, cubin.data()) != CUDA_SUCCESS) return cudaErrorInvalidKernelImage;
   if (dr.get(&mod->real, mod->mod, "tc_real_schemes") != CUDA_SUCCESS ||
       dr.get(&mod->enumerate, mod->mod, "tc_enumerate") != CUDA_SUCCESS ||
       dr.get(&mod->blocks, mod->mod, "tc_enumerate_blocks") != CUDA_SUCCESS)
     return cudaErrorSymbolNotFound;
   const Layout &L = mod->L;
-  mod->smem_real = (size_t)L.words * 4 * L.threads;
+  mod->smem_real = global ? 0 : (size_t)L.words * 4 * L.threads;
   mod->smem_enum = mod->smem_real + (size_t)L.hash * 16 + 16;
   if (dr.set_attr(mod->real, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)mod->smem_real) !=
           CUDA_SUCCESS ||
@@ -337,6 +369,23 @@ void jit_release(ts_tri *t) {
   t->jit.reset();
 }
 
+// Global scratch of one launch of a module that keeps it in global memory
+// (grid x threads x words, stream-ordered; nothing for shared scratch).
+struct JitScratch {
+  const JitModule &m;
+  unsigned grid;
+  cudaStream_t st;
+  uint32_t *p = nullptr;
+  JitScratch(const JitModule &mm, unsigned g, cudaStream_t s) : m(mm), grid(g), st(s) {}
+  cudaError_t alloc() {
+    if (!m.global) return cudaSuccess;
+    return scratch_alloc((void **)&p, (size_t)grid * m.L.words * m.L.threads * 4, st);
+  }
+  ~JitScratch() {
+    if (p) cudaFreeAsync(p, st);
+  }
+};
+
 cudaError_t launch_real_schemes_jit(ts_tri *t, const uint64_t *signs, uint64_t n, uint64_t *codes,
                                     cudaStream_t st) {
   cudaError_t e = jit_prepare(t);
@@ -345,7 +394,9 @@ cudaError_t launch_real_schemes_jit(ts_tri *t, const uint64_t *signs, uint64_t n
   const uint64_t want = (n + m->L.threads - 1) / m->L.threads;
   const uint64_t cap = (uint64_t)m->bpsm_real * sm_count_now();
   const unsigned grid = (unsigned)std::min(want, cap);
-  void *args[] = {(void *)&signs, (void *)&n, (void *)&codes, (void *)&t->d_err};
+  JitScratch gs(*m, grid, st);
+  if ((e = gs.alloc()) != cudaSuccess) return e;
+  void *args[] = {(void *)&signs, (void *)&n, (void *)&codes, (void *)&t->d_err, (void *)&gs.p};
   if (driver().launch(m->real, grid, 1, 1, m->L.threads, 1, 1, (unsigned)m->smem_real, (CUstream)st,
                       args, nullptr) != CUDA_SUCCESS)
     return cudaErrorLaunchFailure;
@@ -364,10 +415,13 @@ cudaError_t enumerate_range(JitModule &m, ts_hist *h, uint64_t lo, uint64_t hi, 
   const unsigned grid = (unsigned)std::min(want, cap);
   cudaError_t e = cudaMemsetAsync(h->d_work, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
+  JitScratch gs(m, grid, st);
+  if ((e = gs.alloc()) != cudaSuccess) return e;
   uint64_t slots = h->slots;
   void *args[] = {(void *)&lo,       (void *)&total,       (void *)&flags,
                   (void *)&h->d_keys, (void *)&h->d_counts, (void *)&slots,
-                  (void *)&h->d_err,  (void *)&h->d_failed, (void *)&h->d_work};
+                  (void *)&h->d_err,  (void *)&h->d_failed, (void *)&h->d_work,
+                  (void *)&gs.p};
   if (driver().launch(m.enumerate, grid, 1, 1, m.L.threads, 1, 1, (unsigned)m.smem_enum,
                       (CUstream)st, args, nullptr) != CUDA_SUCCESS)
     return cudaErrorLaunchFailure;
@@ -384,10 +438,12 @@ cudaError_t enumerate_blocks(JitModule &m, ts_hist *h, uint64_t hi0, uint64_t n_
   const unsigned grid = (unsigned)std::min(want, cap);
   cudaError_t e = cudaMemsetAsync(h->d_work, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
+  JitScratch gs(m, grid, st);
+  if ((e = gs.alloc()) != cudaSuccess) return e;
   uint64_t slots = h->slots;
   void *args[] = {(void *)&hi0,      (void *)&n_hi,       (void *)&oshift,   (void *)&ishift,
                   (void *)&ireps,    (void *)&h->d_keys,  (void *)&h->d_counts, (void *)&slots,
-                  (void *)&h->d_err, (void *)&h->d_failed, (void *)&h->d_work};
+                  (void *)&h->d_err, (void *)&h->d_failed, (void *)&h->d_work, (void *)&gs.p};
   if (driver().launch(m.blocks, grid, 1, 1, m.L.threads, 1, 1, (unsigned)m.smem_enum, (CUstream)st,
                       args, nullptr) != CUDA_SUCCESS)
     return cudaErrorLaunchFailure;

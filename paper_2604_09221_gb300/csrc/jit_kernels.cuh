@@ -5,15 +5,22 @@
 // tc_classify (one mask) and tc_sweep_amortised (a block of masks that share
 // their high bits), then this file.
 
-__device__ __forceinline__ TcScratch<TcK> tc_scratch(u32 *smem) {
-  return TcScratch<TcK>{smem + threadIdx.x};
+// Per-thread scratch: in shared memory, or (TcK::GSCR) in the launch's
+// global buffer, one slab of WORDS x THREADS words per block.
+__device__ __forceinline__ TcScratch<TcK> tc_scratch(u32 *smem, u32 *gscr) {
+  return TcScratch<TcK>{(TcK::GSCR ? gscr + (u64)blockIdx.x * TcK::WORDS * TcK::THREADS : smem) +
+                        threadIdx.x};
 }
 
+// Shared words in front of the block's hash table (the scratch, unless global).
+#define TC_SMEM_SCRATCH (TcK::GSCR ? 0u : TcK::WORDS * TcK::THREADS)
+
 // Codes of n sign vectors (one word each), grid-stride.
-extern "C" __global__ void __launch_bounds__(TcK::THREADS, 2)
-    tc_real_schemes(const u64 *__restrict__ signs, u64 n, u64 *__restrict__ codes, u32 *err_word) {
+extern "C" __global__ void __launch_bounds__(TcK::THREADS, TcK::MINB)
+    tc_real_schemes(const u64 *__restrict__ signs, u64 n, u64 *__restrict__ codes, u32 *err_word,
+                    u32 *gscr) {
   extern __shared__ __align__(16) u32 tc_smem[];
-  const TcScratch<TcK> S = tc_scratch(tc_smem);
+  const TcScratch<TcK> S = tc_scratch(tc_smem, gscr);
   const u64 valid = TcK::NPOINTS >= 64 ? ~0ull : ((1ull << (TcK::NPOINTS & 63)) - 1);
   u32 err = 0;
   for (u64 i = (u64)blockIdx.x * TcK::THREADS + threadIdx.x; i < n;
@@ -25,14 +32,14 @@ extern "C" __global__ void __launch_bounds__(TcK::THREADS, 2)
 #define TC_CHUNK (TcK::THREADS * 16)
 
 // Sweep of masks m(lo + i), i < total, in chunks pulled from a work counter.
-extern "C" __global__ void __launch_bounds__(TcK::THREADS, 2)
+extern "C" __global__ void __launch_bounds__(TcK::THREADS, TcK::MINB)
     tc_enumerate(u64 lo, u64 total, u32 flags, u64 *gkeys, unsigned long long *gcnt, u64 gslots,
-                 u32 *gerr, unsigned long long *gfailed, unsigned long long *work) {
+                 u32 *gerr, unsigned long long *gfailed, unsigned long long *work, u32 *gscr) {
   extern __shared__ __align__(16) u32 tc_smem[];
-  u64 *hkeys = reinterpret_cast<u64 *>(tc_smem + TcK::WORDS * TcK::THREADS);
+  u64 *hkeys = reinterpret_cast<u64 *>(tc_smem + TC_SMEM_SCRATCH);
   unsigned long long *hcnt = reinterpret_cast<unsigned long long *>(hkeys + TcK::HASH);
   unsigned long long *chunk = hcnt + TcK::HASH;
-  const TcScratch<TcK> S = tc_scratch(tc_smem);
+  const TcScratch<TcK> S = tc_scratch(tc_smem, gscr);
   for (u32 s = threadIdx.x; s < TcK::HASH; s += TcK::THREADS) {
     hkeys[s] = 0;
     hcnt[s] = 0;
@@ -68,14 +75,14 @@ extern "C" __global__ void __launch_bounds__(TcK::THREADS, 2)
 // warp takes one h at a time; the two half-diamonds depend on h only and are
 // swept once, then every lane classifies ireps middle-row patterns
 // (tc_sweep_amortised).
-extern "C" __global__ void __launch_bounds__(TcK::THREADS, 2)
+extern "C" __global__ void __launch_bounds__(TcK::THREADS, TcK::MINB)
     tc_enumerate_blocks(u64 hi0, u64 n_hi, u32 oshift, u32 ishift, u32 ireps, u64 *gkeys,
                         unsigned long long *gcnt, u64 gslots, u32 *gerr,
-                        unsigned long long *gfailed, unsigned long long *work) {
+                        unsigned long long *gfailed, unsigned long long *work, u32 *gscr) {
   extern __shared__ __align__(16) u32 tc_smem[];
-  u64 *hkeys = reinterpret_cast<u64 *>(tc_smem + TcK::WORDS * TcK::THREADS);
+  u64 *hkeys = reinterpret_cast<u64 *>(tc_smem + TC_SMEM_SCRATCH);
   unsigned long long *hcnt = reinterpret_cast<unsigned long long *>(hkeys + TcK::HASH);
-  const TcScratch<TcK> S = tc_scratch(tc_smem);
+  const TcScratch<TcK> S = tc_scratch(tc_smem, gscr);
   for (u32 s = threadIdx.x; s < TcK::HASH; s += TcK::THREADS) {
     hkeys[s] = 0;
     hcnt[s] = 0;

@@ -281,27 +281,12 @@ cudaError_t persistent_grid(F fn, int threads, size_t smem, uint64_t want, unsig
   return cudaSuccess;
 }
 
-// Global scratch of a launch: stream-ordered allocation, freed after it.  The
-// device's default pool is told to keep freed memory (release threshold at
-// its maximum), so repeated launches reuse it instead of mapping it again.
+// Global scratch of a launch: stream-ordered allocation, freed after it.
 struct GlobalScratch {
   u32 *p = nullptr;
   cudaStream_t st;
   explicit GlobalScratch(cudaStream_t s) : st(s) {}
-  cudaError_t alloc(size_t bytes) {
-    static std::once_flag once[64];
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev >= 0 && dev < 64)
-      std::call_once(once[dev], [dev] {
-        cudaMemPool_t pool;
-        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
-          uint64_t keep = ~0ull;
-          cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
-        }
-      });
-    return cudaMallocAsync((void **)&p, bytes, st);
-  }
+  cudaError_t alloc(size_t bytes) { return scratch_alloc((void **)&p, bytes, st); }
   ~GlobalScratch() {
     if (p) cudaFreeAsync(p, st);
   }
@@ -343,7 +328,7 @@ cudaError_t enumerate_dg(const ts_tri *t, uint64_t lo, uint64_t hi, uint32_t fla
   return cudaGetLastError();
 }
 
-// Global scratch for d >= 10 unless the triangulation asks otherwise.
+// Global scratch from d = 7 unless the triangulation asks otherwise.
 bool global_scratch(const ts_tri *t) {
   if (t->scratch == TS_SCRATCH_SHARED) return false;
   if (t->scratch == TS_SCRATCH_GLOBAL) return true;
@@ -365,6 +350,23 @@ cudaError_t enumerate_d(const ts_tri *t, uint64_t lo, uint64_t hi, uint32_t flag
 }
 
 }  // namespace
+
+// The device's default pool is told to keep freed memory (release threshold
+// at its maximum), so repeated launches reuse it instead of mapping it again.
+cudaError_t scratch_alloc(void **p, size_t bytes, cudaStream_t st) {
+  static std::once_flag once[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64)
+    std::call_once(once[dev], [dev] {
+      cudaMemPool_t pool;
+      if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+      }
+    });
+  return cudaMallocAsync(p, bytes, st);
+}
 
 cudaError_t launch_real_schemes(const ts_tri *t, const uint64_t *signs, uint64_t n, uint64_t *codes,
                                 cudaStream_t st) {

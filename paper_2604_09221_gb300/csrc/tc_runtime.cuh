@@ -655,7 +655,8 @@ __device__ __forceinline__ u64 tc_splitmix64(u64 x) {
 // Multi-word keys (d >= 10).  A slot's count word carries two flags: BUSY
 // while the inserting thread writes the key, READY once it is published
 // (keys: slots x CW words, zero = empty).
-constexpr u64 TC_SLOT_BUSY = 1ull << 62, TC_SLOT_READY = 1ull << 63;
+#define TC_SLOT_BUSY (1ull << 62)
+#define TC_SLOT_READY (1ull << 63)
 
 template <u32 CW>
 __device__ __forceinline__ u64 tc_key_hash(const u64 *key) {

@@ -62,7 +62,7 @@ def test_random_sign_vectors_wide(eng, orc, d):
         assert bad.size == 0, (d, idx, bad[:5])
 
 
-@pytest.mark.parametrize("d,where", [(7, 2), (9, 2), (10, 1), (13, 1), (16, 1), (16, 2)])
+@pytest.mark.parametrize("d,where", [(5, 2), (7, 1), (7, 2), (9, 1), (9, 2), (10, 1), (13, 1), (16, 1), (16, 2)])
 def test_scratch_placements(eng, orc, d, where):
     """Shared- and global-memory scratch give the oracle's codes and sweep
     histograms (TS_SCRATCH_SHARED = 1, TS_SCRATCH_GLOBAL = 2)."""
