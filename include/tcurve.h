@@ -125,8 +125,7 @@ ts_status ts_set_kernel(ts_tri *tri, int kind);
  *   TS_SCRATCH_GLOBAL: device memory, L1/L2-resident, allocated per launch
  *     with cudaMallocAsync on the launch's stream and freed after it (the
  *     device's default memory pool is set to keep freed memory).
- *   TS_SCRATCH_AUTO (default): for the table-driven kernels global from
- *     d = 7, shared below; shared for the specialised kernels.
+ *   TS_SCRATCH_AUTO (default): global from d = 7, shared below.
  * Changing it drops the specialised kernels already built for tri (they are
  * rebuilt on next use).  Results are identical. */
 #define TS_SCRATCH_AUTO 0
@@ -135,8 +134,9 @@ ts_status ts_set_kernel(ts_tri *tri, int kind);
 ts_status ts_set_scratch(ts_tri *tri, int where);
 
 /* Resident blocks per SM the specialised kernels are compiled for (their
- * register budget): 1..16, or 0 for the default (2 with shared scratch, 4
- * with global scratch).  Drops kernels already built for tri. */
+ * register budget): 1..16, or 0 for the default (with global scratch 6, 5
+ * and 4 blocks of 128 threads for d = 7, 8, 9 and 4 otherwise; 2 with shared
+ * scratch).  Drops kernels already built for tri. */
 ts_status ts_set_occupancy(ts_tri *tri, int blocks_per_sm);
 
 /* Build the specialised kernels now (NVRTC compile and module load on the

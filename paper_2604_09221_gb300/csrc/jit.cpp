@@ -315,12 +315,17 @@ std::string jit_compile_uncached(const std::string &src, std::string *log) {
   return out;
 }
 
-// Configuration of the specialised kernels of a triangulation: scratch in
-// global memory when asked for (TS_SCRATCH_GLOBAL), blocks per SM from
-// ts_set_occupancy (default 2 with shared scratch, 4 with global scratch).
+// Configuration of the specialised kernels of a triangulation.  Scratch:
+// global from d = 7 unless asked otherwise (TS_SCRATCH_*); blocks per SM from
+// ts_set_occupancy, else the register budget measured fastest on GB300 for
+// the degree (d = 7: 6 blocks of 128 threads, 80 registers; d = 8: 5, 96;
+// d = 9: 4, 128), 4 for other degrees with global scratch, 2 with shared.
 void jit_config(const ts_tri *t, bool *global, int *min_blocks) {
-  *global = t->scratch == TS_SCRATCH_GLOBAL;
-  *min_blocks = t->occupancy > 0 ? t->occupancy : (*global ? 4 : 2);
+  *global = t->scratch == TS_SCRATCH_GLOBAL ||
+            (t->scratch == TS_SCRATCH_AUTO && t->d >= kGlobalScratchFrom);
+  int def = 2;
+  if (*global) def = t->d == 7 ? 6 : t->d == 8 ? 5 : 4;
+  *min_blocks = t->occupancy > 0 ? t->occupancy : def;
 }
 
 cudaError_t jit_prepare(ts_tri *t) {
