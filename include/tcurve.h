@@ -152,7 +152,8 @@ ts_status ts_specialized_log(const ts_tri *tri, char *buf, size_t len);
  * generated specialised CUDA source into buf (compile = 0), or compile it
  * with NVRTC for sm_103a and write the compiler log (compile = 1; returns
  * TS_ECUDA if it does not compile).  *needed receives the full length + 1.
- * TS_EUNSUPPORTED for d > 9. */
+ * The source is that of the default configuration (TS_SCRATCH_AUTO, default
+ * occupancy).  TS_EUNSUPPORTED for d > 9. */
 ts_status ts_specialized_source(int d, const int32_t *edges_ij, int n_edges, int compile, char *buf,
                                 size_t len, size_t *needed);
 

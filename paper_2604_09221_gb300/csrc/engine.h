@@ -106,6 +106,8 @@ cudaError_t scratch_alloc(void **p, size_t bytes, cudaStream_t stream);
 // Specialised kernels (jit.cpp).  global: per-thread scratch in global memory
 // (128-thread blocks); min_blocks: blocks per SM the register budget is set for.
 std::string jit_source(const Diamond &D, bool global = false, int min_blocks = 2);
+// Configuration for a degree and the TS_SCRATCH_* / occupancy settings.
+void jit_config(int d, int scratch, int occupancy, bool *global, int *min_blocks);
 // Compile the generated source with NVRTC for sm_103a; returns the cubin (or
 // an empty string and the log in *log).
 std::string jit_compile_cubin(const std::string &src, std::string *log);

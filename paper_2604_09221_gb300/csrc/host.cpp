@@ -388,7 +388,10 @@ ts_status ts_specialized_source(int d, const int32_t *edges_ij, int n_edges, int
   if (!triangles_of(d, edges_ij, n_edges, tris)) return TS_ENOTTRI;
   Diamond D;
   if (!build_diamond(d, tris, D)) return TS_ENOTTRI;
-  std::string out = jit_source(D);
+  bool global = false;
+  int minb = 2;
+  jit_config(d, TS_SCRATCH_AUTO, 0, &global, &minb);  // what runs by default
+  std::string out = jit_source(D, global, minb);
   ts_status st = TS_OK;
   if (compile) {
     std::string log;

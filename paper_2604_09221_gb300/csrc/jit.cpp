@@ -320,12 +320,11 @@ std::string jit_compile_uncached(const std::string &src, std::string *log) {
 // ts_set_occupancy, else the register budget measured fastest on GB300 for
 // the degree (d = 7: 6 blocks of 128 threads, 80 registers; d = 8: 5, 96;
 // d = 9: 4, 128), 4 for other degrees with global scratch, 2 with shared.
-void jit_config(const ts_tri *t, bool *global, int *min_blocks) {
-  *global = t->scratch == TS_SCRATCH_GLOBAL ||
-            (t->scratch == TS_SCRATCH_AUTO && t->d >= kGlobalScratchFrom);
+void jit_config(int d, int scratch, int occupancy, bool *global, int *min_blocks) {
+  *global = scratch == TS_SCRATCH_GLOBAL || (scratch == TS_SCRATCH_AUTO && d >= kGlobalScratchFrom);
   int def = 2;
-  if (*global) def = t->d == 7 ? 6 : t->d == 8 ? 5 : 4;
-  *min_blocks = t->occupancy > 0 ? t->occupancy : def;
+  if (*global) def = d == 7 ? 6 : d == 8 ? 5 : 4;
+  *min_blocks = occupancy > 0 ? occupancy : def;
 }
 
 cudaError_t jit_prepare(ts_tri *t) {
@@ -338,7 +337,7 @@ cudaError_t jit_prepare(ts_tri *t) {
   if (e != cudaSuccess) return e;
   bool global = false;
   int minb = 2;
-  jit_config(t, &global, &minb);
+  jit_config(t->d, t->scratch, t->occupancy, &global, &minb);
   const std::string src = jit_source(t->dia, global, minb);
   const std::string cubin = jit_compile_cubin(src, &t->jit_log);
   if (cubin.empty()) return cudaErrorInvalidSource;

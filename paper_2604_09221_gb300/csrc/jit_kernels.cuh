@@ -16,7 +16,12 @@ __device__ __forceinline__ TcScratch<TcK> tc_scratch(u32 *smem, u32 *gscr) {
 #define TC_SMEM_SCRATCH (TcK::GSCR ? 0u : TcK::WORDS * TcK::THREADS)
 
 // Codes of n sign vectors (one word each), grid-stride.
-extern "C" __global__ void __launch_bounds__(TcK::THREADS, TcK::MINB)
+// Register budgets: the block sweep is compiled for MINB resident blocks per
+// SM; the per-mask kernels, which keep more live state per thread, for at
+// most 4 (global scratch) or MINB (shared scratch).
+#define TC_MINB_MASK (TcK::GSCR && TcK::MINB > 4u ? 4u : TcK::MINB)
+
+extern "C" __global__ void __launch_bounds__(TcK::THREADS, TC_MINB_MASK)
     tc_real_schemes(const u64 *__restrict__ signs, u64 n, u64 *__restrict__ codes, u32 *err_word,
                     u32 *gscr) {
   extern __shared__ __align__(16) u32 tc_smem[];
@@ -32,7 +37,7 @@ extern "C" __global__ void __launch_bounds__(TcK::THREADS, TcK::MINB)
 #define TC_CHUNK (TcK::THREADS * 16)
 
 // Sweep of masks m(lo + i), i < total, in chunks pulled from a work counter.
-extern "C" __global__ void __launch_bounds__(TcK::THREADS, TcK::MINB)
+extern "C" __global__ void __launch_bounds__(TcK::THREADS, TC_MINB_MASK)
     tc_enumerate(u64 lo, u64 total, u32 flags, u64 *gkeys, unsigned long long *gcnt, u64 gslots,
                  u32 *gerr, unsigned long long *gfailed, unsigned long long *work, u32 *gscr) {
   extern __shared__ __align__(16) u32 tc_smem[];
