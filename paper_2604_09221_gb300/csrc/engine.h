@@ -53,6 +53,9 @@ struct Diamond {
 
 struct JitModule;  // compiled specialised kernels (jit.cpp)
 
+// Tables of the table-driven sweep (host.cpp; format in tc_runtime.cuh).
+bool pack_diamond_tables(const Diamond &D, std::vector<uint32_t> &tables, TableLayout &lay);
+
 }  // namespace tcurve
 
 struct ts_tri {

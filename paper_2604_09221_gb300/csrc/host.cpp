@@ -174,11 +174,15 @@ bool build_diamond(int d, const std::vector<std::array<Pt, 3>> &tris, Diamond &D
   return (int)D.anti.size() == 2 * d && (int)D.bedge.size() == 2 * d;
 }
 
+}  // namespace
+
+namespace tcurve {
 // Pack the diamond into the tables the table-driven kernels stage into
-// shared memory (format in tc_table_sweep.cuh).  Returns false if a field
-// does not fit: a vertex id (10 bits), a fan longer than the join list of
-// the kernels takes (tc_pcap), or a fan start beyond 16 bits.
-bool pack_tables(const Diamond &D, ts_tri *t) {
+// shared memory and the specialised kernels keep in constant memory (format
+// in tc_runtime.cuh).  Returns false if a field does not fit: a vertex id
+// (10 bits), a fan longer than the join list of the kernels takes (tc_pcap),
+// or a fan start beyond 16 bits.
+bool pack_diamond_tables(const Diamond &D, std::vector<uint32_t> &tables, TableLayout &lay) {
   const int V = D.V;
   constexpr uint32_t kNone = 1023u;
   if (V > (int)kNone) return false;
@@ -211,13 +215,20 @@ bool pack_tables(const Diamond &D, ts_tri *t) {
   L.off_fan = L.off_vdesc + V;
   L.off_vext = L.off_fan + L.NF;
   L.words = (L.off_vext + V + 3) & ~3u;
-  std::vector<uint32_t> buf(L.words, 0);
-  std::copy(vdesc.begin(), vdesc.end(), buf.begin() + L.off_vdesc);
-  std::copy(fan.begin(), fan.end(), buf.begin() + L.off_fan);
-  std::copy(vext.begin(), vext.end(), buf.begin() + L.off_vext);
-  t->lay = L;
-  t->host_tables = std::move(buf);
-  t->V = V;
+  tables.assign(L.words, 0);
+  std::copy(vdesc.begin(), vdesc.end(), tables.begin() + L.off_vdesc);
+  std::copy(fan.begin(), fan.end(), tables.begin() + L.off_fan);
+  std::copy(vext.begin(), vext.end(), tables.begin() + L.off_vext);
+  lay = L;
+  return true;
+}
+}  // namespace tcurve
+
+namespace {
+
+bool pack_tables(const Diamond &D, ts_tri *t) {
+  if (!pack_diamond_tables(D, t->host_tables, t->lay)) return false;
+  t->V = D.V;
   return true;
 }
 

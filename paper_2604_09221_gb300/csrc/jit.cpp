@@ -41,7 +41,8 @@ typedef TcLayout Layout;
 // Scratch layout of the specialised kernels: 256-thread blocks (fewer if two
 // do not fit shared memory) with shared scratch, 128 with global scratch.
 Layout layout_for(const Diamond &D, bool global) {
-  Layout L = tc_layout(D.d, false, global ? 128 : kJitThreads);
+  // one label per vertex: the block sweep's half-diamonds run table-driven
+  Layout L = tc_layout(D.d, true, global ? 128 : kJitThreads);
   if (global) L.threads = 128;
   return L;
 }
@@ -152,6 +153,14 @@ std::string jit_source(const Diamond &D, bool global, int min_blocks) {
   o << kRuntimeSrc;
   o << "#define TC_BIT(k) ((k) < 32 ? ((slo >> ((k) & 31)) & 1u) : ((shi >> ((k) & 31)) & 1u))\n"
     << "typedef TcScratch<TcK> TcS;\n\n";
+  // the triangulation tables, for the table-driven half-diamonds of the block
+  // sweep (warp-uniform reads: constant memory)
+  std::vector<uint32_t> tab;
+  TableLayout tl{};
+  if (!pack_diamond_tables(D, tab, tl)) return std::string();
+  o << "__constant__ u32 tc_ctab[" << tab.size() << "] = {";
+  for (size_t i = 0; i < tab.size(); ++i) o << (i % 12 ? " " : "\n  ") << tab[i] << "u,";
+  o << "\n};\n\n";
   // which antipodal pairs / boundary edges complete at each vertex
   std::vector<std::vector<int>> anti_at(V), bedge_at(V);
   for (size_t i = 0; i < D.anti.size(); ++i) anti_at[D.anti[i].second].push_back((int)i);
@@ -233,7 +242,11 @@ std::string jit_source(const Diamond &D, bool global, int min_blocks) {
     << "  const u32 lane = threadIdx.x & 31u;\n"
     << "  const u32 slo = (u32)sig_hi, shi = (u32)(sig_hi >> 32);\n  u32 nl = 0, nb = 0, np = 0;\n"
     << "  tc_clear_odd(S);\n";
-  for (int v = 0; v < Vo; ++v) emit_vertex(v, "  ", nullptr, true);
+  // the half-diamonds: one table-driven loop (they run once per warp for
+  // 32 x ireps instances; straight-line code for them would crowd the
+  // instruction caches)
+  o << "  tc_sweep_table(TcSig<1>{{sig_hi}}, tc_ctab + " << tl.off_vdesc << "u, tc_ctab + "
+    << tl.off_fan << "u, tc_ctab + " << tl.off_vext << "u, 0u, " << Vo << "u, S, nl, nb, np);\n";
   o << "  tc_unions(S, np);\n  np = 0;\n  const u32 nl_o = nl, nb_o = nb;\n"
     << "  tc_flatten(S, nl_o);  // every instance of the warp then finds a half's root in one hop\n"
     << "  if (nl_o > 32u) {  // snapshot too small (never seen in practice): no reuse\n"
@@ -241,6 +254,17 @@ std::string jit_source(const Diamond &D, bool global, int min_blocks) {
     << "      const u64 key = tc_classify_slow(sig_hi | ((u64)(lane + 32u * j) << ishift), S, err);\n"
     << "      failed += key == 0;\n"
     << "      tc_hist_add<TcK::HASH>(key, hkeys, hcnt, gkeys, gcnt, gslots, gerr);\n    }\n    return;\n  }\n";
+  // signs and labels of the half-diamond vertices the middle row reads
+  std::vector<char> used(V, 0);
+  for (int v = Vo; v < V; ++v) {
+    for (int u : D.fan[v]) used[u] = 1;
+    for (int i : anti_at[v]) used[D.anti[i].first] = 1;
+    for (int i : bedge_at[v]) used[D.bedge[i].first] = used[D.bedge[i].second] = 1;
+  }
+  for (int u = 0; u < Vo; ++u)
+    if (used[u])
+      o << "  const u32 s" << u << " = TC_BIT(" << D.k[u] << ") ^ " << D.c[u] << "u, L" << u
+        << " = *S.lab(TcK::OFF_LAB, " << u << ");\n";
   for (int w = 0; w < L.snapw; ++w)
     o << "  const u32 snap" << w << " = S.word(TcK::OFF_LPAR, " << w << ");\n";
   o << "  const u32 osnap = S.word(TcK::OFF_ODD, 0);\n";
