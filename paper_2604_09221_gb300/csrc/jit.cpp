@@ -249,6 +249,9 @@ std::string jit_source(const Diamond &D, bool global, int min_blocks) {
     << tl.off_fan << "u, tc_ctab + " << tl.off_vext << "u, 0u, " << Vo << "u, S, nl, nb, np);\n";
   o << "  tc_unions(S, np);\n  np = 0;\n  const u32 nl_o = nl, nb_o = nb;\n"
     << "  tc_flatten(S, nl_o);  // every instance of the warp then finds a half's root in one hop\n"
+    << "  u32 skip = 0;  // half labels that are no roots (they never become roots again)\n"
+    << "  for (u32 l = 0; l < nl_o && l < 32u; ++l)\n"
+    << "    skip |= ((S.lpar(l) & TcS::LOW) != l ? 1u : 0u) << l;\n"
     << "  if (nl_o > 32u) {  // snapshot too small (never seen in practice): no reuse\n"
     << "    for (u32 j = 0; j < ireps; ++j) {\n"
     << "      const u64 key = tc_classify_slow(sig_hi | ((u64)(lane + 32u * j) << ishift), S, err);\n"
@@ -280,7 +283,7 @@ std::string jit_source(const Diamond &D, bool global, int min_blocks) {
   for (int v = Vo; v < V; ++v) mid_pushes += pushes_at(v);
   for (int v = Vo; v < V; ++v) emit_vertex(v, "    ", "sm", mid_pushes > L.pcap);
   o << "    tc_unions(S, np);\n"
-    << "    const u64 key = tc_backend(S, nl, nb, err);\n"
+    << "    const u64 key = tc_backend(S, nl, nb, err, skip);\n"
     << "    failed += key == 0;\n"
     << "    tc_hist_add<TcK::HASH>(key, hkeys, hcnt, gkeys, gcnt, gslots, gerr);\n  }\n}\n";
 

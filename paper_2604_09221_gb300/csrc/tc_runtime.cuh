@@ -230,27 +230,49 @@ __device__ __forceinline__ void tc_store_node(const TcScratch<K> &S, u32 x,
 // already oriented towards region 0.  Re-rooting at the non-orientable region
 // (even d) or the pseudoline's region (odd d) reverses the path between the
 // two.  AHU codes follow, internal regions only: a leaf's code is '10'.
+// Region of a label after step 1 of tc_backend: labels in `skip` (below 32)
+// were passed over; their parent link points straight at their root.
 template <class K>
-__device__ __noinline__ u64 tc_backend(const TcScratch<K> &S, u32 nl, u32 nb, u32 &err) {
+__device__ __forceinline__ u32 tc_region_of(const TcScratch<K> &S, u32 x, u32 skip) {
+  const bool via_root = x < 32u && ((skip >> x) & 1u);
+  return S.lpar(via_root ? (S.lpar(x) & TcScratch<K>::LOW) : x);
+}
+
+// skip: labels below 32 known not to be roots whose parent link is their
+// root (the half-diamond labels of a block sweep, flattened once per warp);
+// the region pass leaves them out and lookups go through their root.
+template <class K>
+__device__ __noinline__ u64 tc_backend(const TcScratch<K> &S, u32 nl, u32 nb, u32 &err,
+                                       u32 skip = 0u) {
   typedef typename TcCode<K::CODE64>::T code_t;
   constexpr u32 BITS = TcCode<K::CODE64>::BITS;
   // 1. region ids over lpar (label order), odd-cycle flags, smallest labels
   u32 R = 0;
   u64 odd = 0;
-  for (u32 l = 0; l < nl; ++l) {
+  auto visit = [&](u32 l) -> bool {
     const u32 p = S.lpar(l) & TcScratch<K>::LOW;
     const u32 is_root = p == l;
     const u32 rp = S.lpar(p);  // p < l holds its region id already
     if (is_root) {
-      if (R >= K::RMAX) {
-        err |= TC_ERR_OVERFLOW;
-        return 0;
-      }
+      if (R >= K::RMAX) return false;
       odd |= (u64)tc_odd(S, l) << R;
       *S.byte(K::OFF_RLAB, R) = (u8)l;
     }
     S.set_lpar(l, is_root ? R : rp);
     R += is_root;
+    return true;
+  };
+  bool fits = true;
+  if (!skip) {
+    for (u32 l = 0; l < nl && fits; ++l) fits = visit(l);
+  } else {  // the labels below 32 not in skip, in order, then the rest
+    for (u32 todo = ~skip & (nl >= 32u ? ~0u : ((1u << nl) - 1u)); todo && fits; todo &= todo - 1u)
+      fits = visit(__ffs(todo) - 1u);
+    for (u32 l = 32; l < nl && fits; ++l) fits = visit(l);
+  }
+  if (!fits) {
+    err |= TC_ERR_OVERFLOW;
+    return 0;
   }
   // 2. root: odd antipodal cycle (even d) / both sides of the pseudoline (odd d)
   int root = -1;
@@ -263,7 +285,7 @@ __device__ __noinline__ u64 tc_backend(const TcScratch<K> &S, u32 nl, u32 nb, u3
   } else {
     for (u32 i = 0; i < nb; ++i) {
       const u32 e = S.word(K::OFF_BPAIR, i);
-      const u32 ra = S.lpar(e & 0xFFFFu), rb = S.lpar(e >> 16);
+      const u32 ra = tc_region_of(S, e & 0xFFFFu, skip), rb = tc_region_of(S, e >> 16, skip);
       if (ra != rb) continue;
       if (root >= 0 && root != (int)ra) {
         err |= TC_ERR_INTERNAL;
@@ -285,7 +307,7 @@ __device__ __noinline__ u64 tc_backend(const TcScratch<K> &S, u32 nl, u32 nb, u3
       err |= TC_ERR_INTERNAL;
       return 0;
     }
-    const u32 p = S.lpar(c);
+    const u32 p = tc_region_of(S, c, skip);
     if (p >= r) {
       err |= TC_ERR_INTERNAL;
       return 0;
