@@ -173,9 +173,21 @@ std::string jit_source(const Diamond &D, bool global, int min_blocks) {
   // check_flush: emit the test that applies the pending joins when the list
   // might overflow (left out where the joins pushed since the last flush
   // provably fit).
+  // Joins a vertex can push: one per run of same-sign fan entries after the
+  // first, plus its antipodal join.  A run starts at entry i when e_i = 1 and
+  // not (e_{i-1} = 1 with entries i-1, i linked); the most starts over all
+  // sign patterns follow from a two-state recursion over the fan.
   auto pushes_at = [&](int v) {
+    const auto &lk = D.link[v];
     const int m = (int)D.fan[v].size();
-    return (m >= 2 ? m - 1 : 0) + (int)anti_at[v].size();
+    int f0 = 0, f1 = m ? 1 : 0;  // most starts so far, last entry 0 / 1
+    for (int i = 1; i < m; ++i) {
+      const int n0 = std::max(f0, f1), n1 = std::max(f0 + 1, f1 + (lk[i] ? 0 : 1));
+      f0 = n0;
+      f1 = n1;
+    }
+    const int starts = std::max(f0, f1);
+    return (starts > 1 ? starts - 1 : 0) + (int)anti_at[v].size();
   };
   auto emit_vertex = [&](int v, const char *ind, const char *mid_sig, bool check_flush) {
     const auto &fan = D.fan[v];
