@@ -279,7 +279,7 @@ std::string jit_source(const Diamond &D, bool global, int min_blocks) {
   for (int u = 0; u < Vo; ++u)
     if (used[u])
       o << "  const u32 s" << u << " = TC_BIT(" << D.k[u] << ") ^ " << D.c[u] << "u, L" << u
-        << " = *S.lab(TcK::OFF_LAB, " << u << ");\n";
+        << " = *S.lab(TcK::OFF_LAB, " << u << ") & TcS::LOW;\n";
   for (int w = 0; w < L.snapw; ++w)
     o << "  const u32 snap" << w << " = S.word(TcK::OFF_LPAR, " << w << ");\n";
   o << "  const u32 osnap = S.word(TcK::OFF_ODD, 0);\n";

@@ -638,7 +638,9 @@ __device__ __noinline__ void tc_backend_wide(const TcScratch<K> &S, u32 nl, u32 
 // same-sign runs in a vertex's fan, antipodal pairs) are appended to the
 // join list (applied when it might overflow); crossed boundary edges are
 // kept for the root of odd degree.  SIG provides bit(k); labels of the
-// vertices are stored in the scratch's [lab] region.
+// vertices are stored in the scratch's [lab] region with the vertex's sign in
+// the top bit (labels need at most 15 of 16 / 7 of 8 bits), so a fan entry
+// reads its neighbour's label and sign in one load.
 template <class K, class SIG>
 __device__ __forceinline__ void tc_sweep_table(const SIG &sig, const u32 *__restrict__ vdesc,
                                                const u32 *__restrict__ fan,
@@ -653,11 +655,13 @@ __device__ __forceinline__ void tc_sweep_table(const SIG &sig, const u32 *__rest
       tc_unions(S, np);
       np = 0;
     }
+    constexpr u32 SB = 8u * K::LBYTES - 1u;  // the sign bit of a [lab] entry
     u32 lv = 0, l0 = TS::NONE, any = 0, prev = 0;
     for (u32 i = 0; i < m; ++i) {
       const u32 f = fan[fs + i];
-      const u32 lu = *S.lab(K::OFF_LAB, f & 1023u);
-      const u32 e = sig.bit((f >> 10) & 255u) ^ ((f >> 18) & 1u) ^ sv ^ 1u;
+      const u32 raw = *S.lab(K::OFF_LAB, f & 1023u);
+      const u32 lu = raw & TS::LOW;
+      const u32 e = (raw >> SB) ^ sv ^ 1u;
       const u32 st = e & ~(((f >> 19) & 1u) & prev) & 1u;  // e starts a run of the fan
       l0 = i == 0 ? lu : l0;
       // a run after the first: join its label with the vertex's label
@@ -673,10 +677,11 @@ __device__ __forceinline__ void tc_sweep_table(const SIG &sig, const u32 *__rest
       tc_newlab(S, nl, l0);
       ++nl;
     }
-    *S.lab(K::OFF_LAB, v) = (typename TS::lab_t)lv;
+    *S.lab(K::OFF_LAB, v) = (typename TS::lab_t)(lv | (sv << SB));
     const u32 x = vext[v];
     if ((x & 1023u) != TC_TAB_NONE) {  // the antipodal partner, reached earlier
-      S.word(K::OFF_PEND, np) = (u32)*S.lab(K::OFF_LAB, x & 1023u) | (lv << 16) | 0x80000000u;
+      S.word(K::OFF_PEND, np) =
+          ((u32)*S.lab(K::OFF_LAB, x & 1023u) & TS::LOW) | (lv << 16) | 0x80000000u;
       ++np;
     }
     if (K::D % 2) {  // crossed boundary edges, for the pseudoline's region
@@ -684,9 +689,9 @@ __device__ __forceinline__ void tc_sweep_table(const SIG &sig, const u32 *__rest
       for (u32 sh = 10; sh <= 20; sh += 10) {
         const u32 b = (x >> sh) & 1023u;
         if (b == TC_TAB_NONE) continue;
-        const u32 db = vdesc[b];
-        if ((sig.bit(db & 255u) ^ ((db >> 8) & 1u)) != sv) {
-          tc_bpair(S, nb, *S.lab(K::OFF_LAB, b), lv);
+        const u32 rb = *S.lab(K::OFF_LAB, b);
+        if ((rb >> SB) != sv) {
+          tc_bpair(S, nb, rb & TS::LOW, lv);
           ++nb;
         }
       }
