@@ -56,6 +56,15 @@ struct JitModule;  // compiled specialised kernels (jit.cpp)
 // Tables of the table-driven sweep (host.cpp; format in tc_runtime.cuh).
 bool pack_diamond_tables(const Diamond &D, std::vector<uint32_t> &tables, TableLayout &lay);
 
+// Most joins vertex v can push in a sweep: one per run of same-sign fan
+// entries after the first (a run starts at entry i when it has the vertex's
+// sign and entry i-1 has not, or the two are not linked), plus its antipodal
+// join.
+int vertex_pushes(const Diamond &D, int v);
+// Static flush schedule of the join list for vertices [v0, v1): flush[v] = 1
+// where the joins pushed since the last flush might not leave room for v's.
+std::vector<char> flush_schedule(const Diamond &D, int v0, int v1, int pcap);
+
 }  // namespace tcurve
 
 struct ts_tri {

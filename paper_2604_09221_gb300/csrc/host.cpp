@@ -177,11 +177,41 @@ bool build_diamond(int d, const std::vector<std::array<Pt, 3>> &tris, Diamond &D
 }  // namespace
 
 namespace tcurve {
+int vertex_pushes(const Diamond &D, int v) {
+  const auto &lk = D.link[v];
+  const int m = (int)D.fan[v].size();
+  int f0 = 0, f1 = m ? 1 : 0;  // most run starts so far, last entry 0 / 1
+  for (int i = 1; i < m; ++i) {
+    const int n0 = std::max(f0, f1), n1 = std::max(f0 + 1, f1 + (lk[i] ? 0 : 1));
+    f0 = n0;
+    f1 = n1;
+  }
+  const int starts = std::max(f0, f1);
+  int anti = 0;
+  for (auto &p : D.anti) anti += p.second == v;
+  return (starts > 1 ? starts - 1 : 0) + anti;
+}
+
+std::vector<char> flush_schedule(const Diamond &D, int v0, int v1, int pcap) {
+  std::vector<char> flush(D.V, 0);
+  int acc = 0;
+  for (int v = v0; v < v1; ++v) {
+    const int p = vertex_pushes(D, v);
+    if (acc + p > pcap) {
+      flush[v] = 1;
+      acc = 0;
+    }
+    acc += p;
+  }
+  return flush;
+}
+
 // Pack the diamond into the tables the table-driven kernels stage into
 // shared memory and the specialised kernels keep in constant memory (format
-// in tc_runtime.cuh).  Returns false if a field does not fit: a vertex id
-// (10 bits), a fan longer than the join list of the kernels takes (tc_pcap),
-// or a fan start beyond 16 bits.
+// in tc_runtime.cuh; bit 30 of vext[v]: apply the pending joins before v).
+// Returns false if a field does not fit: a vertex id (10 bits), a fan longer
+// than the join list of the kernels takes (tc_pcap), or a fan start beyond
+// 16 bits.
 bool pack_diamond_tables(const Diamond &D, std::vector<uint32_t> &tables, TableLayout &lay) {
   const int V = D.V;
   constexpr uint32_t kNone = 1023u;
@@ -199,6 +229,9 @@ bool pack_diamond_tables(const Diamond &D, std::vector<uint32_t> &tables, TableL
     }
   }
   for (auto &p : D.anti) vext[p.second] = (vext[p.second] & ~kNone) | (uint32_t)p.first;
+  const std::vector<char> flush = flush_schedule(D, 0, V, tc_pcap(D.d));
+  for (int v = 0; v < V; ++v)
+    if (flush[v]) vext[v] |= 1u << 30;
   if (D.d % 2) {
     for (auto &e : D.bedge) {
       const int late = std::max(e.first, e.second), early = std::min(e.first, e.second);

@@ -173,30 +173,17 @@ std::string jit_source(const Diamond &D, bool global, int min_blocks) {
   // check_flush: emit the test that applies the pending joins when the list
   // might overflow (left out where the joins pushed since the last flush
   // provably fit).
-  // Joins a vertex can push: one per run of same-sign fan entries after the
-  // first, plus its antipodal join.  A run starts at entry i when e_i = 1 and
-  // not (e_{i-1} = 1 with entries i-1, i linked); the most starts over all
-  // sign patterns follow from a two-state recursion over the fan.
-  auto pushes_at = [&](int v) {
-    const auto &lk = D.link[v];
-    const int m = (int)D.fan[v].size();
-    int f0 = 0, f1 = m ? 1 : 0;  // most starts so far, last entry 0 / 1
-    for (int i = 1; i < m; ++i) {
-      const int n0 = std::max(f0, f1), n1 = std::max(f0 + 1, f1 + (lk[i] ? 0 : 1));
-      f0 = n0;
-      f1 = n1;
-    }
-    const int starts = std::max(f0, f1);
-    return (starts > 1 ? starts - 1 : 0) + (int)anti_at[v].size();
-  };
-  auto emit_vertex = [&](int v, const char *ind, const char *mid_sig, bool check_flush) {
+  // Static flush schedules of the join list: the whole sweep (per-mask
+  // kernels) and the middle row alone (block sweep, empty list at its start).
+  const int Vo0 = V - (2 * d + 1);
+  const std::vector<char> flush_full = flush_schedule(D, 0, V, L.pcap);
+  const std::vector<char> flush_mid = flush_schedule(D, Vo0, V, L.pcap);
+  auto emit_vertex = [&](int v, const char *ind, const char *mid_sig, bool flush) {
     const auto &fan = D.fan[v];
     const auto &lk = D.link[v];
     const int m = (int)fan.size();
     o << ind << "// vertex " << v << " (" << D.x[v] << "," << D.y[v] << ")\n";
-    const int pushes = pushes_at(v);
-    if (pushes && check_flush)
-      o << ind << "if (np > TcK::PCAP - " << pushes << "u) { tc_unions(S, np); np = 0; }\n";
+    if (flush) o << ind << "tc_unions(S, np); np = 0;  // scheduled flush of the join list\n";
     if (mid_sig && D.y[v] == 0)
       o << ind << "const u32 s" << v << " = ((" << mid_sig << " >> " << D.k[v] << ") & 1u) ^ " << D.c[v]
         << "u;\n";
@@ -241,7 +228,7 @@ std::string jit_source(const Diamond &D, bool global, int min_blocks) {
   o << "__device__ __forceinline__ u64 tc_classify(u64 sig, const TcS &S, u32 &err) {\n"
     << "  const u32 slo = (u32)sig, shi = (u32)(sig >> 32);\n  u32 nl = 0, nb = 0, np = 0;\n"
     << "  tc_clear_odd(S);\n";
-  for (int v = 0; v < V; ++v) emit_vertex(v, "  ", nullptr, true);
+  for (int v = 0; v < V; ++v) emit_vertex(v, "  ", nullptr, flush_full[v] != 0);
   o << "  tc_unions(S, np);\n  return tc_backend(S, nl, nb, err);\n}\n\n";
   o << "__device__ __noinline__ u64 tc_classify_slow(u64 sig, const TcS &S, u32 &err) {\n"
     << "  return tc_classify(sig, S, err);\n}\n\n";
@@ -289,11 +276,8 @@ std::string jit_source(const Diamond &D, bool global, int min_blocks) {
     << "    for (u32 w = 1; w < TcK::WODD; ++w) S.word(TcK::OFF_ODD, w) = 0;\n"
     << "    nl = nl_o; nb = nb_o; np = 0;\n"
     << "    const u32 sm = slo | ((lane + 32u * j) << ishift);\n";
-  // the middle row starts from an empty join list: its flush tests are
-  // needed only if all of its joins might not fit
-  int mid_pushes = 0;
-  for (int v = Vo; v < V; ++v) mid_pushes += pushes_at(v);
-  for (int v = Vo; v < V; ++v) emit_vertex(v, "    ", "sm", mid_pushes > L.pcap);
+  // the middle row starts from an empty join list
+  for (int v = Vo; v < V; ++v) emit_vertex(v, "    ", "sm", flush_mid[v] != 0);
   o << "    tc_unions(S, np);\n"
     << "    const u64 key = tc_backend(S, nl, nb, err, skip);\n"
     << "    failed += key == 0;\n"

@@ -630,13 +630,15 @@ __device__ __noinline__ void tc_backend_wide(const TcScratch<K> &S, u32 nl, u32 
 //             bit 19 "u and the previous entry span a triangle with v"
 //   vext[V]   bits 0-9 the antipodal partner x < v of v, bits 10-19 and
 //             20-29 the other end b < v of up to two boundary edges kept for
-//             root detection (1023: none)
+//             root detection (1023: none), bit 30 "apply the pending joins
+//             before v" (a static schedule from the most joins each vertex
+//             can push, the same in every instance)
 #define TC_TAB_NONE 1023u
 
 // Sweep vertices [v0, v1) (Alg. 1, lines 3-4): every vertex takes the label
 // of its first same-sign earlier neighbour, or a fresh label; joins (several
 // same-sign runs in a vertex's fan, antipodal pairs) are appended to the
-// join list (applied when it might overflow); crossed boundary edges are
+// join list (applied where the tables' schedule says); crossed boundary edges are
 // kept for the root of odd degree.  SIG provides bit(k); labels of the
 // vertices are stored in the scratch's [lab] region with the vertex's sign in
 // the top bit (labels need at most 15 of 16 / 7 of 8 bits), so a fan entry
@@ -651,7 +653,8 @@ __device__ __forceinline__ void tc_sweep_table(const SIG &sig, const u32 *__rest
     const u32 desc = vdesc[v];
     const u32 sv = sig.bit(desc & 255u) ^ ((desc >> 8) & 1u);
     const u32 m = (desc >> 9) & 127u, fs = desc >> 16;
-    if (np + m + 1 > K::PCAP) {  // at most m - 1 run joins and one antipodal join at v
+    const u32 x = vext[v];
+    if ((x >> 30) & 1u) {  // the schedule's flush: the same vertex in every lane
       tc_unions(S, np);
       np = 0;
     }
@@ -678,7 +681,6 @@ __device__ __forceinline__ void tc_sweep_table(const SIG &sig, const u32 *__rest
       ++nl;
     }
     *S.lab(K::OFF_LAB, v) = (typename TS::lab_t)(lv | (sv << SB));
-    const u32 x = vext[v];
     if ((x & 1023u) != TC_TAB_NONE) {  // the antipodal partner, reached earlier
       S.word(K::OFF_PEND, np) =
           ((u32)*S.lab(K::OFF_LAB, x & 1023u) & TS::LOW) | (lv << 16) | 0x80000000u;
