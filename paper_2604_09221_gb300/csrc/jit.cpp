@@ -150,6 +150,7 @@ std::string jit_source(const Diamond &D, bool global, int min_blocks) {
   c("OFF_RLAB", L.off_rlab); c("OFF_TPAR", L.off_tpar); c("OFF_ORDER", L.off_order);
   c("OFF_CLEN", L.off_clen); c("OFF_ODD", L.off_odd); c("OFF_CODE", L.off_code);
   o << "};\n";
+  o << "#define TC_HEAVY_FN __forceinline__\n";
   o << kRuntimeSrc;
   o << "#define TC_BIT(k) ((k) < 32 ? ((slo >> ((k) & 31)) & 1u) : ((shi >> ((k) & 31)) & 1u))\n"
     << "typedef TcScratch<TcK> TcS;\n\n";

@@ -39,6 +39,14 @@ struct TcLab<2> {
   static constexpr u32 EPW = 2, TOP = 0x8000u;
 };
 
+// Attribute of the join pass and the narrow back end: out of line by
+// default (the table-driven kernels); the generated specialised sources
+// define it as __forceinline__ (measured faster there: the calls' register
+// saves cost more than the larger code).
+#ifndef TC_HEAVY_FN
+#define TC_HEAVY_FN __noinline__
+#endif
+
 constexpr u32 TC_ERR_INTERNAL = 1u;
 constexpr u32 TC_ERR_OVERFLOW = 2u;
 constexpr u32 TC_ERR_TIMEOUT = 4u;
@@ -134,7 +142,7 @@ __device__ __forceinline__ void tc_bpair(const TcScratch<K> &S, u32 i, u32 la, u
 
 // Apply the pending joins (a | b << 16 | parity << 31).
 template <class K>
-__device__ __noinline__ void tc_unions(const TcScratch<K> &S, u32 np) {
+__device__ TC_HEAVY_FN void tc_unions(const TcScratch<K> &S, u32 np) {
   for (u32 i = 0; i < np; ++i) {
     const u32 e = S.word(K::OFF_PEND, i);
     tc_unite(S, e & 0xFFFFu, (e >> 16) & 0x7FFFu, e >> 31);
@@ -242,8 +250,8 @@ __device__ __forceinline__ u32 tc_region_of(const TcScratch<K> &S, u32 x, u32 sk
 // root (the half-diamond labels of a block sweep, flattened once per warp);
 // the region pass leaves them out and lookups go through their root.
 template <class K>
-__device__ __noinline__ u64 tc_backend(const TcScratch<K> &S, u32 nl, u32 nb, u32 &err,
-                                       u32 skip = 0u) {
+__device__ TC_HEAVY_FN u64 tc_backend(const TcScratch<K> &S, u32 nl, u32 nb, u32 &err,
+                                      u32 skip = 0u) {
   typedef typename TcCode<K::CODE64>::T code_t;
   constexpr u32 BITS = TcCode<K::CODE64>::BITS;
   // 1. region ids over lpar (label order), odd-cycle flags, smallest labels
