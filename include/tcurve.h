@@ -269,6 +269,13 @@ ts_status ts_enumerate_noalloc(const ts_tri *tri, uint64_t lo, uint64_t hi, uint
                                uint64_t *codes, uint64_t *counts, uint64_t cap, uint64_t *n_out,
                                void *stream);
 
+/* Self-test of the engine's bounded device waits: runs a kernel whose only
+ * wait is on an mbarrier that nothing completes, polled at most iters times
+ * (1 <= iters <= 2^20), and returns the status the kernel reported:
+ * TS_ETIMEOUT when the wait gave up as designed (the GPU context stays
+ * usable), TS_ECUDA without a device.  Synchronises stream. */
+ts_status ts_selftest_wait(uint64_t iters, void *stream);
+
 /* Rohlin-Viro notation of a code (Sec. 2): "<0>", "<J>", "<4>", "<1<1>>",
  * "<J + 1<1> + 2>" ('+' stands for the disjoint union); writes at most len
  * bytes including the terminating NUL. */

@@ -73,6 +73,7 @@ def _load():
                 "ts_hist_read": ([P, P, P, U64, ctypes.POINTER(U64), ctypes.POINTER(U64), P], I),
                 "ts_scheme_string": ([I, P, I, ctypes.c_char_p, ctypes.c_size_t], I),
                 "ts_set_kernel": ([P, I], I),
+                "ts_selftest_wait": ([U64, P], I),
                 "ts_set_scratch": ([P, I], I),
                 "ts_set_occupancy": ([P, I], I),
                 "ts_prepare": ([P], I),
@@ -352,6 +353,14 @@ def splitmix_masks(d: int, base: int, n: int, out=None, stream=None):
     _check(_load().ts_splitmix_masks(int(d), int(base) & ((1 << 64) - 1), int(n), out.data_ptr(),
                                      _stream_handle(stream)), "ts_splitmix_masks")
     return out
+
+
+def selftest_wait(iters: int = 4096, stream=None) -> int:
+    """Run the bounded-wait self-test kernel (an mbarrier nothing completes,
+    polled ``iters`` times) on ``stream`` (default: the legacy default stream);
+    returns the status code (TS_ETIMEOUT = 6 when the wait gave up as
+    designed)."""
+    return int(_load().ts_selftest_wait(int(iters), None if stream is None else _stream_handle(stream)))
 
 
 def scheme_string(d: int, code) -> str:

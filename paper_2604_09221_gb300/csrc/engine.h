@@ -105,6 +105,7 @@ cudaError_t launch_real_schemes(const ts_tri *tri, const uint64_t *signs, uint64
 cudaError_t launch_enumerate(const ts_tri *tri, uint64_t lo, uint64_t hi, uint32_t flags,
                              ts_hist *hist, cudaStream_t stream, bool allow_global = true);
 cudaError_t launch_hist_clear(ts_hist *hist, cudaStream_t stream);
+cudaError_t launch_selftest_wait(unsigned long long iters, uint32_t *err, cudaStream_t stream);
 // Pack the occupied slots of the table into d_ckeys / d_ccnt (count flags
 // removed) and their number into d_cn.
 cudaError_t launch_hist_compact(ts_hist *hist, cudaStream_t stream);

@@ -596,6 +596,20 @@ ts_status ts_hist_read(ts_hist *h, uint64_t *codes, uint64_t *counts, uint64_t c
   return err_word_status(err);
 }
 
+ts_status ts_selftest_wait(uint64_t iters, void *stream) {
+  if (iters == 0 || iters > (1ull << 20)) return TS_EINVAL;
+  uint32_t *d_err = nullptr, err = 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMalloc(&d_err, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, sizeof(uint32_t), st);
+  if (e == cudaSuccess) e = launch_selftest_wait(iters, d_err, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&err, d_err, sizeof(err), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (d_err) cudaFree(d_err);
+  if (e != cudaSuccess) return cuda_status(e);
+  return err_word_status(err);
+}
+
 ts_status ts_scheme_string(int d, const uint64_t *code, int code_words, char *buf, size_t len) {
   if (!code || !buf || len == 0 || code_words < 1 || d < 1) return TS_EINVAL;
   int top = -1;

@@ -222,6 +222,18 @@ __global__ void splitmix_masks_kernel(uint64_t base, uint64_t n, uint32_t npoint
     }
 }
 
+// Self-test of the bounded waits: the only wait is on an mbarrier that
+// nothing completes (no arrival, no copy), polled at most `iters` times; the
+// kernel reports kErrTimeout and returns.
+__global__ void selftest_wait_kernel(unsigned long long iters, uint32_t *err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  bool ok = false;
+  for (unsigned long long it = 0; it < iters && !ok; ++it) ok = mbar_try_wait(&bar, 0);
+  if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicOr(err, kErrTimeout);
+}
+
 __global__ void hist_clear_kernel(ts_hist h) {
   const uint64_t n = h.slots;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -426,6 +438,11 @@ cudaError_t launch_hist_compact(ts_hist *h, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   const uint64_t blocks = (h->slots + 255) / 256;
   hist_compact_kernel<<<(unsigned)(blocks < 2048 ? blocks : 2048), 256, 0, st>>>(*h);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_selftest_wait(unsigned long long iters, uint32_t *err, cudaStream_t st) {
+  selftest_wait_kernel<<<1, 32, 0, st>>>(iters, err);
   return cudaGetLastError();
 }
 

@@ -113,3 +113,26 @@ def test_specialized_kernels_compile_for_sm103a(eng, d):
         r"Function properties for (tc_\w+)\n[^\n]*?\d+ bytes stack frame, (\d+) bytes spill stores", log)}
     assert set(spills) == {"tc_real_schemes", "tc_enumerate", "tc_enumerate_blocks"}, log[-2000:]
     assert max(spills.values()) <= 256, spills
+
+
+@pytest.mark.parametrize("d", [2, 4, 6, 7, 8, 9])
+def test_diamond_tables_match_the_table_1_sizes(eng, d):
+    """The tables of T^diamond built on the host (read from the generated
+    source, no device needed): |A^diamond| = 2d^2 + 2d + 1 vertices and
+    |E(T^diamond)| = 6d^2 + 2d edges (Table 1), one fan entry per edge."""
+    import re
+    e = ti.regular_triangulation(d, seed=d) if d > 2 else ti.standard_triangulation(d)
+    src = eng.specialized_source(d, e)
+    V = int(re.search(r"static constexpr unsigned V = (\d+)u;", src).group(1))
+    words = int(re.search(r"__constant__ u32 tc_ctab\[(\d+)\]", src).group(1))
+    assert V == 2 * d * d + 2 * d + 1
+    edges = 6 * d * d + 2 * d
+    assert words == (2 * V + edges + 3) // 4 * 4   # vdesc[V], fan[|E|], vext[V], 16-byte padded
+
+
+def test_selftest_wait_needs_a_device(eng):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("covered by the GPU test")
+    assert eng.selftest_wait(16) == 4   # TS_ECUDA
+    assert eng.library().ts_selftest_wait(0, None) == 1   # TS_EINVAL

@@ -210,3 +210,25 @@ def test_server_with_wide_jobs(eng, orc):
         assert g.hist == dict(wh), (d, j["n"])
         if j["want_codes"]:
             assert (np.asarray(g.codes).reshape(want.shape) == want).all()
+
+
+def test_bounded_wait_reports_a_timeout(eng):
+    """A device wait that nothing completes gives up after its limit and
+    reports TS_ETIMEOUT; the context stays usable afterwards."""
+    import torch
+    assert eng.selftest_wait(2048) == 6   # TS_ETIMEOUT
+    tri = eng.Triangulation(6, ti.regular_triangulation(6, seed=1))
+    x = torch.zeros(64, dtype=torch.int64, device="cuda")
+    assert tri.real_schemes(x).shape == (64, 1)
+
+
+def test_histogram_overflow_is_reported(eng):
+    """A histogram with room for far fewer codes than the sweep produces
+    reports TS_EOVERFLOW (bounded probing, error word) instead of losing
+    counts silently."""
+    tri = eng.Triangulation(12, ti.regular_triangulation(12, seed=12))
+    h = eng.Histogram(2, tri.code_words)       # 16 slots
+    eng.enumerate_schemes(tri, 0, 20000, h, eng.TS_ENUM_SPLITMIX)
+    with pytest.raises(eng.TSError) as ex:
+        h.read()
+    assert ex.value.status == 5
