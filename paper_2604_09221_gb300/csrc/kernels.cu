@@ -1,25 +1,25 @@
 // kernels.cu -- table-driven sm_103a kernels of the T-curve real-scheme
-// engine (TS_KERNEL_TABLE): one kernel per degree, any triangulation of that
-// degree, no compilation at load time.
+// engine (TS_KERNEL_TABLE): one kernel per degree (1..16), any triangulation
+// of that degree, no compilation at load time.
 //
 // One thread classifies one sign vector with Algorithm 1 (Sec. 2):
-//   (a) the triangulation tables (host.cpp, layout in engine.h) are copied
-//       global -> shared once per block with cp.async.bulk completing on an
-//       mbarrier (plain bulk copy, no multicast; bounded wait);
+//   (a) the triangulation tables (host.cpp; format in tc_runtime.cuh) are
+//       copied global -> shared once per block with cp.async.bulk completing
+//       on an mbarrier (plain bulk copy, no multicast; bounded wait);
 //   (b) the sign of a diamond vertex is bit k(v) of sigma xor the Eq. 2
 //       parity constant c(v);
 //   (c) an edge is crossed iff its end points' signs differ;
-//   (d) Alg. 1 lines 3-4: a sweep of T^diamond in the fixed order of the
-//       tables gives every vertex the label of its first same-sign earlier
-//       neighbour (or a fresh label); joins between labels (several same-sign
-//       runs in a vertex's fan, antipodal pairs) are appended without
-//       branching and applied after the sweep (tc_runtime.cuh);
-//   (e)-(f) Alg. 1 lines 5-11: tc_backend (regions, region tree from the
-//       regions' smallest labels, root, AHU code).  Sweeps add codes to a
-//       block-private shared-memory hash table (warp-aggregated) that is merged
-//       into the device hash table at the end.
-// Per-thread scratch lives in shared memory, interleaved by 32-bit word
-// (tc_layout.h).
+//   (d) Alg. 1 lines 3-4: tc_sweep_table gives every vertex the label of its
+//       first same-sign earlier neighbour (or a fresh label); joins between
+//       labels (several same-sign runs in a vertex's fan, antipodal pairs)
+//       are appended without branching and applied on a static schedule;
+//   (e)-(f) Alg. 1 lines 5-11: tc_backend / tc_backend_wide (regions, region
+//       tree from the regions' smallest labels, root, AHU code).  Sweeps add
+//       codes to a block-private shared-memory hash table (warp-aggregated)
+//       that is merged into the device hash table at the end (multi-word
+//       codes: straight into the device table).
+// Per-thread scratch (tc_layout.h) is interleaved by 32-bit word across the
+// block, in shared memory or, from d = 7 by default, in global memory.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
