@@ -40,12 +40,26 @@ typedef TcLayout Layout;
 
 // Scratch layout of the specialised kernels: 256-thread blocks (fewer if two
 // do not fit shared memory) with shared scratch, 128 with global scratch.
+// The block sweep also keeps, after [odd], a snapshot of the half-diamonds'
+// label parents and odd flags beyond the first SNAPW words (which stay in
+// registers): [snap] = wlab + wodd words, emitted as OFF_SNAP.
 Layout layout_for(const Diamond &D, bool global) {
   // one label per vertex: the block sweep's half-diamonds run table-driven
   Layout L = tc_layout(D.d, true, global ? 128 : kJitThreads);
-  if (global) L.threads = 128;
+  const int snap_words = L.wlab + L.wodd;
+  L.words += snap_words;
+  if (global) {
+    L.threads = 128;
+  } else {  // two blocks per SM, as tc_layout sizes them
+    L.threads = kJitThreads;
+    while (L.threads > 32 && 2 * (L.words * 4 * L.threads + L.hash * 16 + 16) > 216 * 1024)
+      L.threads -= 32;
+  }
   return L;
 }
+
+// First word of the [snap] region (the end of tc_layout's words).
+int snap_offset(const Layout &L) { return L.words - (L.wlab + L.wodd); }
 
 // ---- NVRTC, opened on first use ----
 struct Nvrtc {
@@ -144,6 +158,7 @@ std::string jit_source(const Diamond &D, bool global, int min_blocks) {
   c("D", d); c("V", V); c("NPOINTS", (d + 1) * (d + 2) / 2); c("RMAX", L.rmax); c("NB", L.nb);
   c("THREADS", L.threads); c("HASH", L.hash); c("LBYTES", L.lbytes); c("CODE64", L.code64);
   c("PCAP", L.pcap); c("WODD", L.wodd); c("WORDS", L.words); c("B", d + 1); c("SNAPW", L.snapw);
+  c("WLAB", L.wlab); c("EPW", L.epw); c("OFF_SNAP", snap_offset(L));
   c("GSCR", global ? 1 : 0); c("MINB", min_blocks);
   c("OFF_LPAR", L.off_lpar); c("OFF_CAND", L.off_cand); c("OFF_LAB", L.off_lab);
   c("OFF_BPAIR", L.off_bpair); c("OFF_PEND", L.off_pend); c("OFF_ADJ", L.off_adj);
@@ -231,8 +246,6 @@ std::string jit_source(const Diamond &D, bool global, int min_blocks) {
     << "  tc_clear_odd(S);\n";
   for (int v = 0; v < V; ++v) emit_vertex(v, "  ", nullptr, flush_full[v] != 0);
   o << "  tc_unions(S, np);\n  return tc_backend(S, nl, nb, err);\n}\n\n";
-  o << "__device__ __noinline__ u64 tc_classify_slow(u64 sig, const TcS &S, u32 &err) {\n"
-    << "  return tc_classify(sig, S, err);\n}\n\n";
 
   // ---- block sweep: halves once, middle row per instance ----
   o << "__device__ __forceinline__ void tc_sweep_amortised(u64 sig_hi, u32 ishift, u32 ireps,\n"
@@ -251,12 +264,7 @@ std::string jit_source(const Diamond &D, bool global, int min_blocks) {
     << "  tc_flatten(S, nl_o);  // every instance of the warp then finds a half's root in one hop\n"
     << "  u32 skip = 0;  // half labels that are no roots (they never become roots again)\n"
     << "  for (u32 l = 0; l < nl_o && l < 32u; ++l)\n"
-    << "    skip |= ((S.lpar(l) & TcS::LOW) != l ? 1u : 0u) << l;\n"
-    << "  if (nl_o > 32u) {  // snapshot too small (never seen in practice): no reuse\n"
-    << "    for (u32 j = 0; j < ireps; ++j) {\n"
-    << "      const u64 key = tc_classify_slow(sig_hi | ((u64)(lane + 32u * j) << ishift), S, err);\n"
-    << "      failed += key == 0;\n"
-    << "      tc_hist_add<TcK::HASH>(key, hkeys, hcnt, gkeys, gcnt, gslots, gerr);\n    }\n    return;\n  }\n";
+    << "    skip |= ((S.lpar(l) & TcS::LOW) != l ? 1u : 0u) << l;\n";
   // signs and labels of the half-diamond vertices the middle row reads
   std::vector<char> used(V, 0);
   for (int v = Vo; v < V; ++v) {
@@ -268,13 +276,21 @@ std::string jit_source(const Diamond &D, bool global, int min_blocks) {
     if (used[u])
       o << "  const u32 s" << u << " = TC_BIT(" << D.k[u] << ") ^ " << D.c[u] << "u, L" << u
         << " = *S.lab(TcK::OFF_LAB, " << u << ") & TcS::LOW;\n";
+  // snapshot of the half-diamonds' union-find: the first SNAPW words of the
+  // parents and the first word of odd flags in registers, the rest (many
+  // half labels at d >= 8) in the [snap] region
   for (int w = 0; w < L.snapw; ++w)
     o << "  const u32 snap" << w << " = S.word(TcK::OFF_LPAR, " << w << ");\n";
-  o << "  const u32 osnap = S.word(TcK::OFF_ODD, 0);\n";
+  o << "  const u32 osnap = S.word(TcK::OFF_ODD, 0);\n"
+    << "  const u32 nw = (nl_o + TcK::EPW - 1u) / TcK::EPW, nwo = (nl_o + 31u) / 32u;\n"
+    << "  for (u32 w = TcK::SNAPW; w < nw; ++w) S.word(TcK::OFF_SNAP, w) = S.word(TcK::OFF_LPAR, w);\n"
+    << "  for (u32 w = 1; w < nwo; ++w) S.word(TcK::OFF_SNAP + TcK::WLAB, w) = S.word(TcK::OFF_ODD, w);\n";
   o << "  for (u32 j = 0; j < ireps; ++j) {\n";
   for (int w = 0; w < L.snapw; ++w) o << "    S.word(TcK::OFF_LPAR, " << w << ") = snap" << w << ";\n";
-  o << "    S.word(TcK::OFF_ODD, 0) = osnap;\n"
-    << "    for (u32 w = 1; w < TcK::WODD; ++w) S.word(TcK::OFF_ODD, w) = 0;\n"
+  o << "    for (u32 w = TcK::SNAPW; w < nw; ++w) S.word(TcK::OFF_LPAR, w) = S.word(TcK::OFF_SNAP, w);\n"
+    << "    S.word(TcK::OFF_ODD, 0) = osnap;\n"
+    << "    for (u32 w = 1; w < TcK::WODD; ++w)\n"
+    << "      S.word(TcK::OFF_ODD, w) = w < nwo ? S.word(TcK::OFF_SNAP + TcK::WLAB, w) : 0u;\n"
     << "    nl = nl_o; nb = nb_o; np = 0;\n"
     << "    const u32 sm = slo | ((lane + 32u * j) << ishift);\n";
   // the middle row starts from an empty join list
