@@ -285,20 +285,38 @@ std::string jit_source(const Diamond &D, bool global, int min_blocks) {
     << "  const u32 nw = (nl_o + TcK::EPW - 1u) / TcK::EPW, nwo = (nl_o + 31u) / 32u;\n"
     << "  for (u32 w = TcK::SNAPW; w < nw; ++w) S.word(TcK::OFF_SNAP, w) = S.word(TcK::OFF_LPAR, w);\n"
     << "  for (u32 w = 1; w < nwo; ++w) S.word(TcK::OFF_SNAP + TcK::WLAB, w) = S.word(TcK::OFF_ODD, w);\n";
-  o << "  for (u32 j = 0; j < ireps; ++j) {\n";
-  for (int w = 0; w < L.snapw; ++w) o << "    S.word(TcK::OFF_LPAR, " << w << ") = snap" << w << ";\n";
-  o << "    for (u32 w = TcK::SNAPW; w < nw; ++w) S.word(TcK::OFF_LPAR, w) = S.word(TcK::OFF_SNAP, w);\n"
-    << "    S.word(TcK::OFF_ODD, 0) = osnap;\n"
-    << "    for (u32 w = 1; w < TcK::WODD; ++w)\n"
-    << "      S.word(TcK::OFF_ODD, w) = w < nwo ? S.word(TcK::OFF_SNAP + TcK::WLAB, w) : 0u;\n"
-    << "    nl = nl_o; nb = nb_o; np = 0;\n"
-    << "    const u32 sm = slo | ((lane + 32u * j) << ishift);\n";
-  // the middle row starts from an empty join list
-  for (int v = Vo; v < V; ++v) emit_vertex(v, "    ", "sm", flush_mid[v] != 0);
-  o << "    tc_unions(S, np);\n"
-    << "    const u64 key = tc_backend(S, nl, nb, err, skip);\n"
-    << "    failed += key == 0;\n"
-    << "    tc_hist_add<TcK::HASH>(key, hkeys, hcnt, gkeys, gcnt, gslots, gerr);\n  }\n}\n";
+  // The per-lane loop: every instance restores the snapshot, sweeps the
+  // middle row and classifies.  Emitted twice: warps whose half-diamonds left
+  // at most 32 labels restore from registers only (the common case below
+  // d = 8, and measured faster), the others also from the [snap] region.
+  auto emit_lane_loop = [&](bool with_snap, const char *ind) {
+    const std::string in(ind), in2 = in + "  ";
+    o << in << "for (u32 j = 0; j < ireps; ++j) {\n";
+    for (int w = 0; w < L.snapw; ++w)
+      o << in2 << "S.word(TcK::OFF_LPAR, " << w << ") = snap" << w << ";\n";
+    if (with_snap)
+      o << in2 << "for (u32 w = TcK::SNAPW; w < nw; ++w) S.word(TcK::OFF_LPAR, w) = S.word(TcK::OFF_SNAP, w);\n";
+    o << in2 << "S.word(TcK::OFF_ODD, 0) = osnap;\n";
+    if (with_snap)
+      o << in2 << "for (u32 w = 1; w < TcK::WODD; ++w)\n"
+        << in2 << "  S.word(TcK::OFF_ODD, w) = w < nwo ? S.word(TcK::OFF_SNAP + TcK::WLAB, w) : 0u;\n";
+    else
+      o << in2 << "for (u32 w = 1; w < TcK::WODD; ++w) S.word(TcK::OFF_ODD, w) = 0u;\n";
+    o << in2 << "nl = nl_o; nb = nb_o; np = 0;\n"
+      << in2 << "const u32 sm = slo | ((lane + 32u * j) << ishift);\n";
+    // the middle row starts from an empty join list
+    for (int v = Vo; v < V; ++v) emit_vertex(v, in2.c_str(), "sm", flush_mid[v] != 0);
+    o << in2 << "tc_unions(S, np);\n"
+      << in2 << "const u64 key = tc_backend(S, nl, nb, err, skip);\n"
+      << in2 << "failed += key == 0;\n"
+      << in2 << "tc_hist_add<TcK::HASH>(key, hkeys, hcnt, gkeys, gcnt, gslots, gerr);\n"
+      << in << "}\n";
+  };
+  o << "  if (nl_o <= 32u) {\n";
+  emit_lane_loop(false, "    ");
+  o << "  } else {\n";
+  emit_lane_loop(true, "    ");
+  o << "  }\n}\n";
 
   o << kKernelsSrc;
   return o.str();
