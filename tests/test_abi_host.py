@@ -102,9 +102,10 @@ def test_specialized_kernels_compile_for_sm103a(eng, d):
     e = ti.regular_triangulation(d, seed=d) if d > 2 else ti.standard_triangulation(d)
     src = eng.specialized_source(d, e)
     # every vertex appears once in the per-mask sweep; the block sweep has the
-    # middle row in straight-line code (its half-diamonds run from tables)
+    # middle row in straight-line code twice (restore from registers only, or
+    # also from the snapshot region); its half-diamonds run from tables
     V = 2 * d * d + 2 * d + 1
-    assert "tc_classify" in src and src.count("// vertex ") == V + 2 * d + 1
+    assert "tc_classify" in src and src.count("// vertex ") == V + 2 * (2 * d + 1)
     assert "tc_sweep_table(" in src and "__constant__ u32 tc_ctab" in src
     log = eng.specialized_source(d, e, compile=True)
     # the three entry kernels (the cold per-mask fallback of the block sweep,
