@@ -40,9 +40,10 @@ struct TcLab<2> {
 };
 
 // Attribute of the join pass and the narrow back end: out of line by
-// default (the table-driven kernels); the generated specialised sources
-// define it as __forceinline__ (measured faster there: the calls' register
-// saves cost more than the larger code).
+// default (the table-driven kernels, where inlining measured 9 % slower at
+// d = 7 and 23 % at d = 9); the generated specialised sources define it as
+// __forceinline__ (measured faster there: the calls' register saves cost
+// more than the larger code).
 #ifndef TC_HEAVY_FN
 #define TC_HEAVY_FN __noinline__
 #endif
