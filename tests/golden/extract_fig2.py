@@ -9,8 +9,8 @@ This script reads the paper's LaTeX source and writes:
   fig2_<name>.edges          one edge "i1 j1 i2 j2" per line
   fig2_oval_percentages.txt  "<name> <k> <percent>" per line
 
-Run it by hand with the paper's source path:
-    python tests/golden/extract_fig2.py /root/reference/PAPER.md
+Run it by hand with the path of the paper's LaTeX source:
+    python tests/golden/extract_fig2.py <paper source>
 """
 import os
 import re
