@@ -1,0 +1,63 @@
+// Test infrastructure: run the block sweep of a generated specialised source
+// (included as GEN) on the host, one lane at a time, for whole warps, and
+// compare each warp's histogram with the oracle's over the same masks.
+// Usage: run_block_sweep <edges file> <warps>; exit status 0 when all match.
+#include "device_shims.h"
+#include GEN
+extern "C" {
+#include "tcurve_oracle.h"
+}
+#include <fstream>
+#include <map>
+#include <vector>
+
+int main(int argc, char **argv) {
+  const int d = TcK::D;
+  std::vector<int32_t> e;
+  {
+    std::ifstream f(argv[1]);
+    int a;
+    while (f >> a) e.push_back(a);
+  }
+  const int nh = argc > 2 ? atoi(argv[2]) : 8;
+  std::vector<int32_t> otri(6 * d * d);
+  if (orc_triangles_from_edges(d, (int)e.size() / 4, e.data(), otri.data(), d * d) != d * d) return 2;
+  const unsigned ib = d + 1, oshift = d + 1, ishift = 0, ireps = (1u << ib) / 32u;
+  std::vector<unsigned> scr((size_t)TcK::WORDS * TcK::THREADS + 64, 0xA5A5A5A5u);
+  const unsigned npts = (d + 1) * (d + 2) / 2;
+  const unsigned long long hmax = 1ull << (npts - ib);
+  unsigned long long state = 12345;
+  int bad = 0;
+  for (int t = 0; t < nh; ++t) {
+    state = state * 6364136223846793005ull + 1442695040888963407ull;
+    const unsigned long long h = t == 0 ? 0 : (t == 1 ? hmax - 1 : (state >> 11) % hmax);
+    std::vector<u64> hkeys(TcK::HASH, 0), gkeys(1 << 12, 0);
+    std::vector<unsigned long long> hcnt(TcK::HASH, 0), gcnt(1 << 12, 0);
+    u32 gerr = 0, err = 0;
+    unsigned long long failed = 0;
+    for (unsigned lane = 0; lane < 32; ++lane) {
+      threadIdx.x = lane;
+      const TcS S{scr.data() + lane};
+      tc_sweep_amortised(h << oshift, ishift, ireps, S, err, hkeys.data(), hcnt.data(), gkeys.data(),
+                         gcnt.data(), gkeys.size(), &gerr, failed);
+    }
+    std::map<u64, unsigned long long> got, want;
+    for (size_t s = 0; s < hkeys.size(); ++s)
+      if (hkeys[s]) got[hkeys[s]] += hcnt[s];
+    for (size_t s = 0; s < gkeys.size(); ++s)
+      if (gkeys[s]) got[gkeys[s]] += gcnt[s];
+    for (unsigned long long tt = 0; tt < (1ull << ib); ++tt) {
+      const uint64_t m = (h << oshift) | tt;
+      uint64_t code = 0;
+      if (orc_real_scheme(d, otri.data(), &m, &code, 1, nullptr) != 0) return 3;
+      want[code] += 1;
+    }
+    if (got != want || err || gerr || failed) {
+      ++bad;
+      printf("warp h=%llu differs (%zu codes, oracle %zu; err %u %u, failed %llu)\n", h, got.size(),
+             want.size(), err, gerr, failed);
+    }
+  }
+  printf("d=%d warps=%d differing=%d\n", d, nh, bad);
+  return bad != 0;
+}

@@ -1,0 +1,43 @@
+"""The generated specialised sources, run on the CPU: the block sweep of a
+triangulation's generated CUDA source is compiled as plain C++ with host
+definitions of the CUDA intrinsics (tests/host/), run one lane at a time over
+whole warps (each warp classifies all middle-row patterns of one value of
+the high bits), and its histograms must equal the oracle's over the same
+masks.  Catches mistakes of the code generator without a GPU; the GPU tests
+check the same code compiled for sm_103a."""
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import tcurve_inputs as ti
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+
+
+@pytest.fixture(scope="module")
+def eng():
+    from paper_2604_09221_gb300 import build
+    build.build()
+    import paper_2604_09221_gb300 as e
+    e.library()
+    return e
+
+
+@pytest.mark.skipif(shutil.which("g++") is None, reason="needs g++")
+@pytest.mark.parametrize("d,seed", [(4, 4), (5, 5), (7, 7), (8, 8), (9, 9)])
+def test_block_sweep_source_on_the_host(eng, tmp_path, d, seed):
+    edges = ti.regular_triangulation(d, seed=seed)
+    (tmp_path / "gen.cu").write_text(eng.specialized_source(d, edges))
+    np.savetxt(tmp_path / "tri.txt", edges, fmt="%d")
+    exe = tmp_path / "run"
+    cmd = ["g++", "-std=c++17", "-O1", "-w", f'-DGEN="{tmp_path / "gen.cu"}"',
+           f"-I{os.path.join(HERE, 'host')}", f"-I{os.path.join(ROOT, 'oracle')}",
+           "-o", str(exe), os.path.join(HERE, "host", "run_block_sweep.cpp"),
+           "-x", "c", os.path.join(ROOT, "oracle", "tcurve_oracle.c"), "-x", "none", "-lpthread"]
+    subprocess.run(cmd, check=True, capture_output=True)
+    out = subprocess.run([str(exe), str(tmp_path / "tri.txt"), "6"], capture_output=True, text=True)
+    assert out.returncode == 0, out.stdout + out.stderr
