@@ -115,6 +115,20 @@ def _stream_handle(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
+def _check_words(t, n_words: int, what: str, writable: bool = False):
+    """Raise ValueError unless ``t`` can be handed to the library as a device
+    buffer of at least ``n_words`` 64-bit words.  The C ABI takes bare
+    pointers, so a short buffer would be read or written past its end."""
+    if t.is_floating_point() or t.is_complex() or t.element_size() != 8:
+        raise ValueError(f"{what}: 64-bit integer words expected, got {t.dtype}")
+    if writable and not t.is_contiguous():
+        raise ValueError(f"{what}: the output tensor must be contiguous")
+    if t.numel() < n_words:
+        raise ValueError(f"{what}: {t.numel()} words, {n_words} needed")
+    if not t.is_cuda:
+        raise ValueError(f"{what}: a CUDA tensor is required")
+
+
 def max_degree() -> int:
     return _load().ts_max_degree()
 
@@ -180,12 +194,20 @@ class Triangulation:
         of code words on the same device.  With ``sync`` the call waits and
         raises on instance errors (ts_sync)."""
         import torch
+        if signs.numel() % self.sign_words:
+            raise ValueError(f"signs: {signs.numel()} words is not a multiple of "
+                             f"sign_words = {self.sign_words}")
+        n = signs.numel() // self.sign_words
+        if out is not None:
+            _check_words(out, n * self.code_words, "out", writable=True)
         if not signs.is_cuda:
             raise ValueError("signs must be a CUDA tensor (use real_schemes_host for host arrays)")
+        _check_words(signs, n * self.sign_words, "signs")
         s = signs.contiguous()
-        n = s.numel() // self.sign_words
         if out is None:
             out = torch.empty((n, self.code_words), dtype=torch.int64, device=s.device)
+        elif out.device != s.device:
+            raise ValueError(f"out is on {out.device}, signs on {s.device}")
         st = _stream_handle(stream)
         _check(_lib.ts_real_schemes(self._h, s.data_ptr(), n, out.data_ptr(), st), "ts_real_schemes")
         if sync:
@@ -260,10 +282,16 @@ class Batch:
 
     def __init__(self, tris, counts, bases, code_outputs=None, hist_capacity: int = 1 << 16):
         n = len(tris)
+        cnt = np.ascontiguousarray(np.asarray(counts, dtype=np.uint64).ravel())
+        bs = np.ascontiguousarray(np.asarray(bases, dtype=np.uint64).ravel())
+        if len(cnt) != n or len(bs) != n or (code_outputs is not None and len(code_outputs) != n):
+            raise ValueError("tris, counts, bases and code_outputs need one entry per job")
+        if code_outputs is not None:
+            for t, c, o in zip(tris, cnt, code_outputs):
+                if o is not None:
+                    _check_words(o, int(c) * t.code_words, "code_outputs", writable=True)
         self.tris = list(tris)  # keep the triangulations alive
         th = (ctypes.c_void_p * n)(*[t.handle.value for t in tris])
-        cnt = np.ascontiguousarray(np.asarray(counts, dtype=np.uint64))
-        bs = np.ascontiguousarray(np.asarray(bases, dtype=np.uint64))
         outs = None
         if code_outputs is not None:
             self._outs = list(code_outputs)
@@ -347,9 +375,11 @@ def splitmix_masks(d: int, base: int, n: int, out=None, stream=None):
     of counter k is splitmix64(k * W + w), cut to |A| bits): an int64 tensor
     of shape (n,) for one sign word, (n, W) otherwise."""
     import torch
+    W = ((d + 1) * (d + 2) // 2 + 63) // 64
     if out is None:
-        W = ((d + 1) * (d + 2) // 2 + 63) // 64
         out = torch.empty(n if W == 1 else (n, W), dtype=torch.int64, device="cuda")
+    else:
+        _check_words(out, n * W, "out", writable=True)
     _check(_load().ts_splitmix_masks(int(d), int(base) & ((1 << 64) - 1), int(n), out.data_ptr(),
                                      _stream_handle(stream)), "ts_splitmix_masks")
     return out
