@@ -11,7 +11,8 @@
  *  - A sign vector is ts_sign_words(tri) little-endian uint64 words; bit k
  *    (word k/64, bit k%64) is sigma at lattice index k.  Bit 1 means a
  *    negative coefficient: the coefficient of x^i y^j is (-1)^sigma(i,j)
- *    (Thm. 1).  Bits at positions >= |A| must be zero.
+ *    (Thm. 1).  Bits at positions >= |A| are ignored: every kernel clears
+ *    them when it loads a sign vector.
  *  - A scheme code is ts_code_words(tri) little-endian uint64 words holding
  *    the integer (1 << nbits) | bits, where bits is the canonical encoding of
  *    the nesting tree of the ovals: enc(oval) = '1' . (encodings of the ovals
@@ -44,7 +45,7 @@ typedef struct ts_hist ts_hist; /* a device hash histogram: scheme code -> count
 
 typedef enum ts_status {
   TS_OK = 0,
-  TS_EINVAL = 1,       /* bad argument (range, null pointer, stray sign bits) */
+  TS_EINVAL = 1,       /* bad argument (range, null pointer, unknown flag) */
   TS_ENOTTRI = 2,      /* edges are not a unimodular triangulation of d*Delta_2 */
   TS_ENOMEM = 3,       /* host or device allocation failed */
   TS_ECUDA = 4,        /* CUDA error or no usable device */
