@@ -305,6 +305,9 @@ def main():
                 "kernel_ms": kms,
                 "achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s",
                 "frac": achieved_tops / peak_tops, "traffic": None,
+                "traffic_note": "no input is read; DRAM carries only scratch write-backs from L2 "
+                                "(55.6 MB per 2^26-mask launch by ncu), which do not scale with the "
+                                "masks swept, so no per-launch figure is given for 2^32",
                 "peak_source": f"{n_sm} SMs x {INT_LANES_PER_SM} INT32 lanes x {sm_max:.0f} MHz (derived)",
                 "alg_ops_per_instance": ALG_OPS_PER_INSTANCE}
     line = {"metric": METRIC, "value": value, "unit": "schemes/s", "n_gpus": ws,
