@@ -159,11 +159,13 @@ def reference_arm(args):
         times.append(time.perf_counter() - t0)
     v = sample * len(times) / sum(times)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "schemes/s",
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": "d7_sweep_oracle_sample", "degree": D, "masks_per_step": sample,
-                       "triangulation": f"regular, lifting seed {TRI_SEED}"},
+            "config": {"workload": "d7_batched_sweep", "degree": D,
+                       "triangulation": f"regular unimodular, lifting seed {TRI_SEED}",
+                       "sample": f"{sample} consecutive masks of the sweep per step",
+                       "parallelism": f"the oracle on rank 0's {cores} host cores"},
             "cpu_baseline": {"value": v, "unit": "schemes/s", "cores": cores, "kind": "oracle",
                              "sample": f"{sample} consecutive masks per step"},
             "e2e": {"value": v, "unit": "schemes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
