@@ -1,7 +1,10 @@
 // Test infrastructure: run the block sweep of a generated specialised source
 // (included as GEN) on the host, one lane at a time, for whole warps, and
 // compare each warp's histogram with the oracle's over the same masks.
-// Usage: run_block_sweep <edges file> <warps>; exit status 0 when all match.
+// Usage: run_block_sweep <edges file> <warps> [plain|flip|reduced]; the mask
+// map of a warp is (h << oshift) | (t << ishift), t < 2^ib, as in the sweeps
+// without flags, with TS_ENUM_FLIP (bit 0 fixed) and with TS_ENUM_REDUCED
+// (bits 0, 1 and d + 1 fixed).  Exit status 0 when all match.
 #include "device_shims.h"
 #include GEN
 extern "C" {
@@ -9,6 +12,7 @@ extern "C" {
 }
 #include <fstream>
 #include <map>
+#include <string>
 #include <vector>
 
 int main(int argc, char **argv) {
@@ -20,12 +24,18 @@ int main(int argc, char **argv) {
     while (f >> a) e.push_back(a);
   }
   const int nh = argc > 2 ? atoi(argv[2]) : 8;
+  const std::string mode = argc > 3 ? argv[3] : "plain";
   std::vector<int32_t> otri(6 * d * d);
   if (orc_triangles_from_edges(d, (int)e.size() / 4, e.data(), otri.data(), d * d) != d * d) return 2;
-  const unsigned ib = d + 1, oshift = d + 1, ishift = 0, ireps = (1u << ib) / 32u;
+  unsigned ib = d + 1, oshift = d + 1, ishift = 0;
+  if (mode == "flip") { ib = d; ishift = 1; }
+  else if (mode == "reduced") { ib = d - 1; ishift = 2; oshift = d + 2; }
+  else if (mode != "plain") return 2;
+  if (ib < 5) return 2;  // fewer middle-row patterns than lanes: no block sweep
+  const unsigned ireps = (1u << ib) / 32u;
   std::vector<unsigned> scr((size_t)TcK::WORDS * TcK::THREADS + 64, 0xA5A5A5A5u);
   const unsigned npts = (d + 1) * (d + 2) / 2;
-  const unsigned long long hmax = 1ull << (npts - ib);
+  const unsigned long long hmax = 1ull << (npts - oshift);
   unsigned long long state = 12345;
   int bad = 0;
   for (int t = 0; t < nh; ++t) {
@@ -47,7 +57,7 @@ int main(int argc, char **argv) {
     for (size_t s = 0; s < gkeys.size(); ++s)
       if (gkeys[s]) got[gkeys[s]] += gcnt[s];
     for (unsigned long long tt = 0; tt < (1ull << ib); ++tt) {
-      const uint64_t m = (h << oshift) | tt;
+      const uint64_t m = (h << oshift) | (tt << ishift);
       uint64_t code = 0;
       if (orc_real_scheme(d, otri.data(), &m, &code, 1, nullptr) != 0) return 3;
       want[code] += 1;
@@ -58,6 +68,10 @@ int main(int argc, char **argv) {
              want.size(), err, gerr, failed);
     }
   }
-  printf("d=%d warps=%d differing=%d\n", d, nh, bad);
+#ifdef TC_TEST_COUNT_SNAP
+  // lanes whose half-diamonds left more than 32 labels (the snapshot path)
+  printf("snapshot_lanes=%ld ", tc_test_snap_lanes);
+#endif
+  printf("d=%d map=%s warps=%d differing=%d\n", d, mode.c_str(), nh, bad);
   return bad != 0;
 }
