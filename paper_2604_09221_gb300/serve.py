@@ -13,7 +13,9 @@ code buffers when it wants codes; nothing else, the histograms are resident)
 fits in what the running jobs leave of ``mem_budget``; jobs that finish free
 their slot and memory at once, so admission is continuous rather than batch by
 batch.  Triangulations (with their kernels prepared) and histograms stay
-resident for the server's life.
+resident for the server's life.  A job whose launch or result raises (a CUDA
+error, failed instances, an overflow that cannot be recovered) fails its own
+future only; its slot and memory return to the pool and the server goes on.
 
 The scheduling logic talks to the device through an executor; the GPU
 executor drives the C ABI, and tests can pass a fake one to check admission on
@@ -149,6 +151,7 @@ class Server:
         self.peak_mem = 0
         self.peak_running = 0
         self.completed: List[Job] = []
+        self.failed: List[Job] = []     # jobs whose start or result raised
         self.cv = threading.Condition()
         self.stop_flag = False
         self.error: Optional[BaseException] = None
@@ -186,33 +189,51 @@ class Server:
                         job = self.queue.popleft()
                         slot = self.free.pop()
                         job.admitted = time.perf_counter()
+                        try:
+                            self.ex.start(slot, job)
+                        except Exception as e:  # this job fails; the slot stays free
+                            self.free.append(slot)
+                            self._fail(job, e)
+                            continue
                         self.running[slot] = job
                         self.mem_used += job.mem_bytes()
                         self.peak_mem = max(self.peak_mem, self.mem_used)
                         self.peak_running = max(self.peak_running, len(self.running))
-                        self.ex.start(slot, job)
                     running = list(self.running.items())
                 finished = [(s, j) for s, j in running if self.ex.done(s)]
                 for slot, job in finished:
-                    hist, codes = self.ex.result(slot, job)
+                    try:
+                        hist, codes = self.ex.result(slot, job)
+                        err = None
+                    except Exception as e:  # this job fails; the others keep running
+                        err = e
                     job.finished = time.perf_counter()
                     with self.cv:
                         del self.running[slot]
                         self.free.append(slot)
                         self.mem_used -= job.mem_bytes()
-                        self.completed.append(job)
+                        if err is None:
+                            self.completed.append(job)
+                    if err is not None:
+                        self._fail(job, err)
+                        continue
                     job.future.set_result(Result(hist, codes, job.finished - job.submitted,
                                                  job.admitted - job.submitted))
                 if not finished:
                     with self.cv:
                         if not self.queue or not self.free:
                             self.cv.wait(timeout=0.0002)
-        except BaseException as e:  # surface scheduler failures to the caller
+        except BaseException as e:  # a failure of the scheduler itself ends it
             self.error = e
             with self.cv:
                 for j in list(self.queue) + list(self.running.values()):
                     if not j.future.done():
                         j.future.set_exception(e)
+
+    def _fail(self, job: Job, err: BaseException):
+        job.finished = time.perf_counter()
+        self.failed.append(job)
+        job.future.set_exception(err)
 
     def latencies(self) -> List[float]:
         return [j.finished - j.submitted for j in self.completed]

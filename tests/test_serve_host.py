@@ -76,3 +76,35 @@ def test_continuous_admission_fills_a_freed_slot_before_the_batch_drains():
 def test_percentile():
     xs = list(range(101))
     assert percentile(xs, 50) == 50 and percentile(xs, 99) == 99
+
+
+class FlakyExecutor(FakeExecutor):
+    """Fails to launch the job with base 7 and to read the job with base 13."""
+
+    def start(self, slot, job):
+        if job.base == 7:
+            raise RuntimeError("launch failed")
+        super().start(slot, job)
+
+    def result(self, slot, job):
+        if job.base == 13:
+            raise RuntimeError("3 instances failed")
+        return super().result(slot, job)
+
+
+def test_a_failing_job_fails_alone():
+    ex = FlakyExecutor()
+    srv = Server(ex, slots=3, mem_budget=16 * 4000)
+    jobs = [Job(tri=i % 3, n=300 + 11 * i, base=i, want_codes=i % 2 == 0) for i in range(24)]
+    futs = [srv.submit(j) for j in jobs]
+    for j, f in zip(jobs, futs):
+        if j.base in (7, 13):
+            with pytest.raises(RuntimeError):
+                f.result(timeout=30)
+        else:
+            assert f.result(timeout=30).hist == {j.tri * 1000 + j.base % 97: j.n}
+    # the server keeps serving, and every slot and byte came back
+    assert srv.submit(Job(tri=1, n=50, base=99)).result(timeout=30).hist == {1000 + 99 % 97: 50}
+    srv.close()
+    assert sorted(j.base for j in srv.failed) == [7, 13]
+    assert len(srv.completed) == 23 and srv.mem_used == 0 and sorted(srv.free) == [0, 1, 2]
