@@ -81,3 +81,38 @@ def test_checkpointed_sweep_resumes(tmp_path, orc):
     assert second.done and resumed == fn(0, 50000)
     with pytest.raises(ValueError):
         sweep.CheckpointedSweep(0, 60000, 7000, path, fn, tag="d5")
+
+
+def _synthetic_hist(rank, cw):
+    """Histogram of rank ``rank``: codes of ``cw`` words with the top bit of
+    every word set in some of them (int64 wrap-around), shared and own keys,
+    and no keys at all on rank 2."""
+    import random
+    if rank == 2:
+        return {}
+    rng = random.Random(40 + rank)
+    shared = [(1 << (64 * cw - 1)) | (0xFFFF << 64) | 5, (1 << 63) | 3, 1 << (64 * (cw - 1))]
+    own = [rng.getrandbits(64 * cw) | 1 for _ in range(5 + 7 * rank)]
+    return {k: 1 + rng.randrange(1000) for k in shared + own}
+
+
+def _rank_main_multiword(rank, world, port, cw, out_path):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    merged = sweep.all_gather_histogram(dist, _synthetic_hist(rank, cw), code_words=cw)
+    with open(f"{out_path}.{rank}", "w") as f:
+        f.write(repr(sorted(merged.items())))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_gloo_merge_of_multiword_codes(tmp_path):
+    cw, world = 3, 3
+    out = str(tmp_path / "merged")
+    mp.start_processes(_rank_main_multiword, args=(world, _free_port(), cw, out), nprocs=world,
+                       join=True, start_method="spawn")
+    want = sweep.merge(*[_synthetic_hist(r, cw) for r in range(world)])
+    for r in range(world):   # every rank holds the whole merged histogram
+        assert dict(eval(open(f"{out}.{r}").read())) == want
