@@ -221,3 +221,29 @@ def test_kernels_agree_on_full_size_sweep(eng):
     a = gpu_hist(eng, load(eng, d, e, "table"), 0, 1 << 32)
     b = gpu_hist(eng, load(eng, d, e, "specialized"), 0, 1 << 32)
     assert a == b
+
+
+def test_d6_plain_full_size(eng, orc):
+    """The degree-6 query workload at its full size: 64 distinct seeded
+    regular triangulations, 2^20 uniform random sign vectors each (512 MiB of
+    signs in all), through ts_real_schemes (table-driven kernel; the
+    specialised kernel on four of them).  Per triangulation, 4096 sampled
+    rows and the first and last rows equal the oracle's codes; at full size,
+    no instance failed, every scheme satisfies the classical restrictions and
+    at most 55 distinct nonempty sextic schemes occur."""
+    d, n, k = 6, 1 << 20, 64
+    tris = ti.regular_triangulations(d, k, seed=6)
+    rng = np.random.default_rng(606)
+    seen = set()
+    for t, e in enumerate(tris):
+        masks = ti.random_masks(n, d, seed=6, stream=t)
+        tri = load(eng, d, e, "specialized" if t < 4 else "table")
+        got = gpu_codes(eng, tri, masks)[:, 0]
+        assert got.shape == (n,) and (got != 0).all()
+        idx = np.unique(np.concatenate([rng.integers(0, n, 4096), [0, n - 1]]))
+        want = orc.real_schemes(d, orc.triangles(d, e), masks[idx])[:, 0]
+        assert (got[idx] == want).all(), t
+        seen |= {int(c) for c in np.unique(got)}
+    assert len(seen) <= 55
+    for c in seen:
+        assert check_classical(d, c) == [], c
