@@ -104,3 +104,46 @@ def test_autotuner_picks_tiles_that_run(eng, jobs, tmp_path):
     batch.run()
     for j in range(len(sel)):
         assert sum(hist_of(batch, j).values()) == counts[j]
+
+
+def test_mixed_batch_full_size(eng, orc):
+    """The mixed-degree batch workload at its full size: 32 seeded regular
+    triangulations for each d in 5..10, 2^U(10,24) splitmix64 sign vectors
+    per triangulation (about 3.3e8 in all), one graph launch.  Every job's
+    histogram accounts for all its sign vectors, none failed, and every
+    scheme satisfies the classical restrictions; one job per degree also
+    stores its codes, and 1024 sampled rows of each equal the oracle's codes
+    of the same sign vectors."""
+    import torch
+    from schemes import check_classical
+    degrees, per_degree, seed = (5, 6, 7, 8, 9, 10), 32, 31
+    rng = np.random.default_rng(seed)
+    tris, edges, counts, bases = [], [], [], []
+    for d in degrees:
+        for k, e in enumerate(ti.regular_triangulations(d, per_degree, seed=seed + d)):
+            tris.append(eng.Triangulation(d, e))
+            edges.append(e)
+            counts.append(int(2 ** rng.uniform(10, 24)))
+            bases.append(job_base(seed * 100 + d, k))
+    sampled = [degrees.index(d) * per_degree for d in degrees]   # first job of each degree
+    outs = [torch.zeros((counts[j], tris[j].code_words), dtype=torch.int64, device="cuda")
+            if j in sampled else None for j in range(len(tris))]
+    batch = eng.Batch(tris, counts, bases, code_outputs=outs)
+    batch.run(graph=True)
+    torch.cuda.synchronize()
+    checked = set()
+    for j, t in enumerate(tris):
+        codes, cnt, failed = batch.read(j)
+        assert failed == 0 and int(cnt.sum()) == counts[j], j
+        for c in codes.reshape(len(cnt), -1):
+            key = (t.d, eng.code_to_int(c))
+            if key not in checked:
+                assert check_classical(*key) == [], key
+                checked.add(key)
+    for j in sampled:
+        d, n = tris[j].d, counts[j]
+        idx = np.unique(np.concatenate([rng.integers(0, n, 1024), [0, n - 1]]))
+        signs = np.concatenate([ti.splitmix_sign_vectors(d, bases[j] + int(i), 1) for i in idx])
+        want = orc.real_schemes(d, orc.triangles(d, edges[j]), signs)
+        got = outs[j].cpu().numpy().view(np.uint64)[idx]
+        assert (got == want).all(), (d, j)
