@@ -511,8 +511,8 @@ def mixed_workload(args, degrees=(5, 6, 7, 8, 9, 10), per_degree=32, seed=31):
             tris.append(eng.Triangulation(d, e))
             counts.append(int(2 ** rng.uniform(10, 24)))
             bases.append(job_base(seed * 100 + d, k))
-    tiles = autotune.autotune(tris, counts, bases, cache=os.path.join(ROOT, "gpurun_out", "tiles.json")
-                              if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None, reps=1)
+    # tiles cached in the file TCURVE_TILE_CACHE names, when set
+    tiles = autotune.autotune(tris, counts, bases, reps=1)
     batch = eng.Batch(tris, counts, bases)
     autotune.apply(batch, tiles)
     for _ in range(max(args.warmup, 1)):
