@@ -446,6 +446,10 @@ ts_status ts_batch_set_tile(ts_batch *b, int d, int threads, int chunk, int scra
     if (g.d != d) continue;
     const bool global = scratch == TS_SCRATCH_AUTO ? d >= kGlobalScratchFrom : scratch == TS_SCRATCH_GLOBAL;
     if (!jobs_fn_dt(d, threads, global)) return TS_EINVAL;  // block does not fit shared memory
+    // runs already launched (graph launches included) read the job table and
+    // the scratch that this call rewrites or frees: let them finish first
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_st(e);
     g.threads = threads;
     g.chunk = chunk;
     g.global = global;
@@ -453,7 +457,7 @@ ts_status ts_batch_set_tile(ts_batch *b, int d, int threads, int chunk, int scra
       cudaGraphExecDestroy(b->exec);
       b->exec = nullptr;
     }
-    cudaError_t e = upload_group(b, g);
+    e = upload_group(b, g);
     if (e == cudaSuccess) e = prepare_group(g);
     return cuda_st(e);
   }
