@@ -114,3 +114,17 @@ def test_table_sweep_on_the_host(tmp_path, d):
         out = subprocess.run([str(exe), str(d), str(tmp_path / "tri.txt"), "600"],
                              capture_output=True, text=True)
         assert out.returncode == 0, (name, out.stdout + out.stderr)
+
+
+@pytest.mark.skipif(shutil.which("g++") is None, reason="needs g++")
+def test_histogram_inserts_on_the_host(tmp_path):
+    """The device histogram inserts (one-word, block-private with spill,
+    multi-word with the BUSY / READY flags) compiled for the host and run one
+    call at a time against a std::map, including full tables."""
+    csrc = os.path.join(ROOT, "paper_2604_09221_gb300", "csrc")
+    exe = tmp_path / "run"
+    subprocess.run(["g++", "-std=c++17", "-O1", "-w", f"-I{os.path.join(HERE, 'host')}", f"-I{csrc}",
+                    "-o", str(exe), os.path.join(HERE, "host", "run_hash_insert.cpp")],
+                   check=True, capture_output=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0, out.stdout + out.stderr
