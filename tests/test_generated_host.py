@@ -128,3 +128,53 @@ def test_histogram_inserts_on_the_host(tmp_path):
                    check=True, capture_output=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True)
     assert out.returncode == 0, out.stdout + out.stderr
+
+
+def expected_mask_words(d, flags, k):
+    """The masks of include/tcurve.h written out with Python integers: k;
+    k << 1 (TS_ENUM_FLIP); k with zero bits inserted at positions 0, 1 and
+    d + 1 (TS_ENUM_REDUCED); word w = splitmix64(k * W + w), bits >= |A|
+    cleared (TS_ENUM_SPLITMIX).  Words beyond the W sign words are dropped."""
+    W, npts, m64 = ti.sign_words(d), ti.num_points(d), (1 << 64) - 1
+    if flags == 4:
+        words = [ti.splitmix64_int((k * W + w) & m64) for w in range(W)]
+        top = npts - 64 * (W - 1)
+        if top < 64:
+            words[-1] &= (1 << top) - 1
+        return words
+    if flags == 1:
+        m = k << 1
+    elif flags == 2:
+        low, high = k & ((1 << (d - 1)) - 1), k >> (d - 1)
+        m = (low << 2) | (high << (d + 2))
+    else:
+        m = k
+    return [(m >> (64 * w)) & m64 for w in range(W)]
+
+
+@pytest.mark.skipif(shutil.which("g++") is None, reason="needs g++")
+def test_sweep_mask_maps_on_the_host(tmp_path):
+    """tc_enum_sig against the mask maps' definitions, at the edges of the
+    64-bit counter (carries from word 0 into word 1) for one to three sign
+    words."""
+    csrc = os.path.join(ROOT, "paper_2604_09221_gb300", "csrc")
+    exe = tmp_path / "run"
+    subprocess.run(["g++", "-std=c++17", "-O1", "-w", f"-I{os.path.join(HERE, 'host')}", f"-I{csrc}",
+                    "-o", str(exe), os.path.join(HERE, "host", "run_enum_sig.cpp")],
+                   check=True, capture_output=True)
+    rng = np.random.default_rng(12)
+    cases = []
+    for d in (4, 5, 9, 10, 11, 12, 15, 16):
+        ks = {0, 1, 2, (1 << (d - 1)) - 1, 1 << (d - 1), (1 << 62) + 5, (1 << 63) - 1, 1 << 63,
+              (1 << 64) - 1, *[int(x) for x in rng.integers(0, 1 << 63, 6, dtype=np.int64)]}
+        for flags in (0, 1, 2, 4):
+            for k in sorted(ks):
+                if ti.sign_words(d) == 1 and flags != 4 and k >= 1 << (ti.num_points(d) - 3):
+                    continue   # one sign word: the ABI bounds the range so that masks fit
+                cases.append((d, flags, k))
+    inp = "".join(f"{d} {f} {k}\n" for d, f, k in cases)
+    out = subprocess.run([str(exe)], input=inp, capture_output=True, text=True, check=True)
+    lines = out.stdout.split("\n")
+    for (d, f, k), line in zip(cases, lines):
+        assert [int(x, 16) for x in line.split()] == expected_mask_words(d, f, k), (d, f, k)
+    assert len(lines) == len(cases) + 1
