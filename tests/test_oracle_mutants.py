@@ -56,6 +56,20 @@ MUTANTS = [
     ("no_sentinel", "    code[nbits >> 6] |= (uint64_t)1 << (nbits & 63);\n", "\n"),
     ("depth_off_by_one", "for (int b = 0; b < no; b++) depth[a] += in[a * no + b];",
      "for (int b = 0; b < no; b++) depth[a] += in[b * no + a];"),
+    # the containment relation stored with its operands transposed
+    ("containment_transposed", "in[a * no + b] = (char)r;", "in[b * no + a] = (char)r;"),
+    # a boundary passage not counted
+    ("jump_not_counted", "        C->jumps++;\n", "\n"),
+    # the orientation determinant with a wrong sign on one term
+    ("orientation_sign", "return (bx - ax) * (cy - ay) - (by - ay) * (cx - ax);",
+     "return (bx - ax) * (cy - ay) + (by - ay) * (cx - ax);"),
+    # the count of crossed edges (a statistic the hand trace pins)
+    ("crossed_edges_miscounted", "for (int e = 0; e < c.ne; e++) ncr += crossed(&c, e);",
+     "for (int e = 0; e < c.ne; e++) ncr += 1;"),
+    # the test point of an oval at a crossed edge's midpoint instead of a
+    # segment's midpoint: on the glued boundary for a boundary edge
+    ("test_point_on_an_edge", "C->px = (segs[C->first].x0 + segs[C->first].x1) / 2;",
+     "C->px = segs[C->first].x0;"),
 ]
 
 # Equivalent rewrites that must pass: testing the first leg of the ray in
