@@ -69,8 +69,9 @@ int main(int argc, char **argv) {
     }
   }
 #ifdef TC_TEST_COUNT_SNAP
-  // lanes whose half-diamonds left more than 32 labels (the snapshot path)
-  printf("snapshot_lanes=%ld ", tc_test_snap_lanes);
+  // lanes whose half-diamonds left more than 32 labels (the snapshot path),
+  // and lanes with an odd-cycle flag set when the snapshot was taken
+  printf("snapshot_lanes=%ld odd_lanes=%ld ", tc_test_snap_lanes, tc_test_odd_lanes);
 #endif
   printf("d=%d map=%s warps=%d differing=%d\n", d, mode.c_str(), nh, bad);
   return bad != 0;

@@ -28,18 +28,24 @@ def eng():
 
 
 SNAP_BRANCH = "  if (nl_o <= 32u) {\n"   # the generated choice of the lane loop
+ODD_SNAPSHOT = ("  for (u32 w = 1; w < nwo; ++w) S.word(TcK::OFF_SNAP + TcK::WLAB, w) = "
+                "S.word(TcK::OFF_ODD, w);\n")     # the snapshot of the odd-cycle flags
 
 
 def build_block_sweep(eng, tmp_path, d, edges, count_snap=False):
     """Compile the generated block sweep of (d, edges) with the host driver;
     with count_snap, a copy of the source counts the lanes that take the
-    snapshot path (more than 32 labels left by the half-diamonds)."""
+    snapshot path (more than 32 labels left by the half-diamonds) and the
+    lanes with an odd-cycle flag set when the snapshot is taken."""
     src = eng.specialized_source(d, edges)
     flags = []
     if count_snap:
-        assert src.count(SNAP_BRANCH) == 1
-        src = ("static long tc_test_snap_lanes = 0;\n" +
-               src.replace(SNAP_BRANCH, "  if (nl_o > 32u) ++tc_test_snap_lanes;\n" + SNAP_BRANCH))
+        assert src.count(SNAP_BRANCH) == 1 and src.count(ODD_SNAPSHOT) == 1
+        src = ("static long tc_test_snap_lanes = 0, tc_test_odd_lanes = 0;\n" +
+               src.replace(SNAP_BRANCH, "  if (nl_o > 32u) ++tc_test_snap_lanes;\n" + SNAP_BRANCH)
+                  .replace(ODD_SNAPSHOT, ODD_SNAPSHOT +
+                           "  for (u32 w = 0; w < TcK::WODD; ++w)\n"
+                           "    if (S.word(TcK::OFF_ODD, w)) { ++tc_test_odd_lanes; break; }\n"))
         flags = ["-DTC_TEST_COUNT_SNAP"]
     (tmp_path / "gen.cu").write_text(src)
     np.savetxt(tmp_path / "tri.txt", edges, fmt="%d")
@@ -76,7 +82,10 @@ def test_block_sweep_of_the_fig2_triangulations(eng, tmp_path, name):
     """The three printed d = 8 triangulations, swept as the exhaustive Fig. 2
     check sweeps them (TS_ENUM_REDUCED) and without flags.  On rank016 and
     rank015 most warps' half-diamonds leave more than 32 labels, so the lane
-    loop that restores from the snapshot region runs too."""
+    loop that restores from the snapshot region runs too.  No odd-cycle flag
+    is ever set when the snapshot is taken: before the middle row the two
+    halves are linked only by antipodal pairs, so every cycle closed by then
+    crosses between them an even number of times and has even parity."""
     edges = np.loadtxt(os.path.join(HERE, "golden", f"fig2_{name}.edges"), dtype=np.int32,
                        comments="#")
     exe = build_block_sweep(eng, tmp_path, 8, edges, count_snap=True)
@@ -85,6 +94,7 @@ def test_block_sweep_of_the_fig2_triangulations(eng, tmp_path, name):
         lanes = int(out.split("snapshot_lanes=")[1].split()[0])
         if name != "bow_tie":
             assert lanes >= 32 * 4, out   # at least 4 of the 12 warps
+        assert int(out.split("odd_lanes=")[1].split()[0]) == 0, out
 
 
 CUDA_INCLUDE = "/usr/local/cuda/include"   # host.cpp's headers and the runtime it links
