@@ -117,12 +117,21 @@ int run(const char *edge_file, int n) {
 int main(int argc, char **argv) {
   const int d = atoi(argv[1]), n = atoi(argv[3]);
   switch (d) {
+    case 1: return run<1>(argv[2], n);
+    case 2: return run<2>(argv[2], n);
+    case 3: return run<3>(argv[2], n);
+    case 4: return run<4>(argv[2], n);
     case 5: return run<5>(argv[2], n);
+    case 6: return run<6>(argv[2], n);
     case 7: return run<7>(argv[2], n);
     case 8: return run<8>(argv[2], n);
+    case 9: return run<9>(argv[2], n);
     case 10: return run<10>(argv[2], n);
     case 11: return run<11>(argv[2], n);
+    case 12: return run<12>(argv[2], n);
     case 13: return run<13>(argv[2], n);
+    case 14: return run<14>(argv[2], n);
+    case 15: return run<15>(argv[2], n);
     case 16: return run<16>(argv[2], n);
   }
   return 2;

@@ -101,27 +101,34 @@ CUDA_INCLUDE = "/usr/local/cuda/include"   # host.cpp's headers and the runtime 
 CUDA_LIB = "/usr/local/cuda/lib64"
 
 
-@pytest.mark.skipif(shutil.which("g++") is None or not os.path.isdir(CUDA_INCLUDE)
-                    or not os.path.isdir(CUDA_LIB),
-                    reason="needs g++ and the CUDA headers")
-@pytest.mark.parametrize("d", [5, 7, 8, 10, 11, 13, 16])
-def test_table_sweep_on_the_host(tmp_path, d):
-    """The table-driven sweep (both back ends, multi-word sign vectors and
-    codes) compiled for the host, on the tables host.cpp builds, against the
-    oracle: random and special sign vectors, standard and regular
-    triangulations."""
+@pytest.fixture(scope="module")
+def table_sweep_exe(tmp_path_factory):
+    """The host build of the table-driven sweep driver (every degree)."""
+    if shutil.which("g++") is None or not os.path.isdir(CUDA_INCLUDE) or not os.path.isdir(CUDA_LIB):
+        pytest.skip("needs g++ and the CUDA headers")
     csrc = os.path.join(ROOT, "paper_2604_09221_gb300", "csrc")
-    exe = tmp_path / "run"
+    exe = tmp_path_factory.mktemp("table_sweep") / "run"
     cmd = ["g++", "-std=c++17", "-O1", "-w", f"-I{csrc}", f"-I{os.path.join(HERE, 'host')}",
            f"-I{os.path.join(ROOT, 'oracle')}", f"-I{CUDA_INCLUDE}", "-o", str(exe),
            os.path.join(HERE, "host", "run_table_sweep.cpp"),
            "-x", "c", os.path.join(ROOT, "oracle", "tcurve_oracle.c"), "-x", "none",
            f"-L{CUDA_LIB}", f"-Wl,-rpath,{CUDA_LIB}", "-lcudart", "-lpthread"]
     subprocess.run(cmd, check=True, capture_output=True)
-    for name, edges in (("standard", ti.standard_triangulation(d)),
-                        ("regular", ti.regular_triangulation(d, seed=100 + d))):
+    return exe
+
+
+@pytest.mark.parametrize("d", list(range(1, 17)))
+def test_table_sweep_on_the_host(table_sweep_exe, tmp_path, d):
+    """The table-driven sweep (both back ends, multi-word sign vectors and
+    codes) compiled for the host, on the tables host.cpp builds, against the
+    oracle: random and special sign vectors, the standard triangulation and
+    (d >= 3) a regular one."""
+    cases = [("standard", ti.standard_triangulation(d))]
+    if d >= 3:
+        cases.append(("regular", ti.regular_triangulation(d, seed=100 + d)))
+    for name, edges in cases:
         np.savetxt(tmp_path / "tri.txt", edges, fmt="%d")
-        out = subprocess.run([str(exe), str(d), str(tmp_path / "tri.txt"), "600"],
+        out = subprocess.run([str(table_sweep_exe), str(d), str(tmp_path / "tri.txt"), "600"],
                              capture_output=True, text=True)
         assert out.returncode == 0, (name, out.stdout + out.stderr)
 
