@@ -6,7 +6,9 @@ process per GPU) sweeps a contiguous part of the index range with
 histograms (at most a few thousand distinct codes) at the end.  Long sweeps
 (2^42 masks of a degree-8 triangulation take hours) are run in chunks; after
 each chunk the running histogram and the next index are written to a JSON
-file, so a sweep that stops can resume where it stopped.
+file, so a sweep that stops can resume where it stopped.  Shards run on
+separate machines merge either by a collective (``all_gather_histogram``)
+or from their checkpoint files (``merge_checkpoint_files``).
 
 Everything here is host logic on top of the C ABI; the schemes themselves are
 computed by the engine's kernels (or, in tests, by whatever ``chunk_fn`` the
@@ -82,6 +84,38 @@ def engine_chunk_fn(tri, flags: int = 0, stream=None, capacity: int = 1 << 14):
         return {code_to_int(c): int(k) for c, k in zip(codes, counts)}
 
     return run
+
+
+def merge_checkpoint_files(paths, lo: Optional[int] = None, hi: Optional[int] = None,
+                           tag: Optional[str] = None) -> Dict[int, int]:
+    """Merge the checkpoint files of finished shards (one per process or
+    box; ``CheckpointedSweep`` wrote them) into the histogram of the whole
+    range.  The shards must carry one tag, be complete, be disjoint and cover
+    [lo, hi) exactly (by default the union of their ranges, which must then
+    be contiguous); otherwise ValueError."""
+    shards = []
+    for p in paths:
+        with open(p) as f:
+            st = json.load(f)
+        if int(st["next"]) < int(st["hi"]):
+            raise ValueError(f"{p}: shard [{st['lo']}, {st['hi']}) stopped at {st['next']}")
+        shards.append((int(st["lo"]), int(st["hi"]), st.get("tag", ""), st["hist"], p))
+    if not shards:
+        raise ValueError("no shards")
+    tags = {s[2] for s in shards}
+    if len(tags) != 1 or (tag is not None and tags != {tag}):
+        raise ValueError(f"shards of different sweeps: tags {sorted(tags)}")
+    shards.sort(key=lambda s: (s[0], s[1]))
+    lo = shards[0][0] if lo is None else lo
+    hi = max(s[1] for s in shards) if hi is None else hi
+    at = lo
+    for a, b, _, _, p in shards:
+        if a != at:
+            raise ValueError(f"{p}: shard starts at {a}, expected {at} (gap or overlap)")
+        at = b
+    if at != hi:
+        raise ValueError(f"shards end at {at}, the range at {hi}")
+    return merge(*[{int(k): int(v) for k, v in s[3].items()} for s in shards])
 
 
 class CheckpointedSweep:

@@ -116,3 +116,31 @@ def test_gloo_merge_of_multiword_codes(tmp_path):
     want = sweep.merge(*[_synthetic_hist(r, cw) for r in range(world)])
     for r in range(world):   # every rank holds the whole merged histogram
         assert dict(eval(open(f"{out}.{r}").read())) == want
+
+
+def test_shard_files_merge_to_the_whole_range(tmp_path, orc):
+    """Shards swept by separate processes (here one after another) each keep
+    a checkpoint file; merging the files gives the histogram of the whole
+    range, and gaps, overlaps, unfinished shards or foreign tags are refused."""
+    d, lo, hi, world = 5, 1000, 1000 + 30000, 3
+    fn = oracle_chunk_fn(d, ti.standard_triangulation(d))
+    paths = []
+    for r in range(world):
+        a, b = sweep.shard_range(lo, hi, r, world)
+        path = str(tmp_path / f"shard{r}.json")
+        sweep.CheckpointedSweep(a, b, 4000, path, fn, tag="d5").run()
+        paths.append(path)
+    assert sweep.merge_checkpoint_files(paths[::-1], lo, hi, tag="d5") == fn(lo, hi)
+    with pytest.raises(ValueError, match="gap or overlap"):
+        sweep.merge_checkpoint_files([paths[0], paths[2]])
+    with pytest.raises(ValueError, match="gap or overlap"):       # one shard given twice
+        sweep.merge_checkpoint_files(paths + [paths[1]])
+    with pytest.raises(ValueError, match="end at"):
+        sweep.merge_checkpoint_files(paths[:2], lo, hi)
+    with pytest.raises(ValueError, match="different sweeps"):
+        sweep.merge_checkpoint_files(paths, tag="d6")
+    unfinished = str(tmp_path / "unfinished.json")
+    a, b = sweep.shard_range(lo, hi, 1, world)
+    sweep.CheckpointedSweep(a, b, 4000, unfinished, fn, tag="d5").run(max_chunks=1)
+    with pytest.raises(ValueError, match="stopped at"):
+        sweep.merge_checkpoint_files([paths[0], unfinished, paths[2]])
