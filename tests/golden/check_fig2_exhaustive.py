@@ -10,6 +10,13 @@ checkpointing after every chunk, and compares both with the printed values
 stored in this directory.
 
     python tests/golden/check_fig2_exhaustive.py bow_tie [checkpoint.json]
+
+The range can also be split into N shards swept independently (one process
+or machine each, every shard with its own checkpoint) and merged afterwards:
+
+    python tests/golden/check_fig2_exhaustive.py rank015 s0.json --shard 0/4
+    ...
+    python tests/golden/check_fig2_exhaustive.py rank015 --merge s0.json s1.json s2.json s3.json
 """
 import collections
 import json
@@ -38,7 +45,7 @@ def printed(name):
     return out
 
 
-def main(name, ckpt):
+def main(name, ckpt, shard=(0, 1)):
     import torch
 
     import paper_2604_09221_gb300 as eng
@@ -57,9 +64,14 @@ def main(name, ckpt):
         print(f"[{time.time() - t0:8.1f} s] {hi / total:7.2%}", file=sys.stderr, flush=True)
         return out
 
-    run = sweep.CheckpointedSweep(0, total, 1 << 36, ckpt, chunk, tag=name)
+    lo, hi = sweep.shard_range(0, total, shard[0], shard[1])
+    run = sweep.CheckpointedSweep(lo, hi, 1 << 36, ckpt, chunk, tag=name)
     hist = run.run()
-    assert run.done and sum(hist.values()) == total
+    assert run.done and sum(hist.values()) == hi - lo
+    if shard[1] > 1:
+        print(json.dumps({"triangulation": name, "shard": list(shard), "range": [lo, hi],
+                          "checkpoint": ckpt, "distinct_schemes_in_shard": len(hist)}))
+        return 0
     return report(name, hist, total)
 
 
@@ -84,5 +96,16 @@ def report(name, hist, total=1 << 42):
 
 
 if __name__ == "__main__":
-    nm = sys.argv[1] if len(sys.argv) > 1 else "bow_tie"
-    sys.exit(main(nm, sys.argv[2] if len(sys.argv) > 2 else f"fig2_{nm}.ckpt.json"))
+    import argparse
+    ap = argparse.ArgumentParser()
+    ap.add_argument("name", nargs="?", default="bow_tie", choices=sorted(SCHEMES))
+    ap.add_argument("checkpoint", nargs="?")
+    ap.add_argument("--shard", default="0/1", help="r/N: sweep shard r of N")
+    ap.add_argument("--merge", nargs="+", metavar="CHECKPOINT",
+                    help="merge finished shard checkpoints and compare with Fig. 2")
+    a = ap.parse_args()
+    if a.merge:
+        from paper_2604_09221_gb300 import sweep
+        sys.exit(report(a.name, sweep.merge_checkpoint_files(a.merge, 0, 1 << 42, tag=a.name)))
+    r, n = (int(x) for x in a.shard.split("/"))
+    sys.exit(main(a.name, a.checkpoint or f"fig2_{a.name}.ckpt.json", (r, n)))
