@@ -63,11 +63,11 @@ def test_admission_respects_the_memory_budget():
 def test_continuous_admission_fills_a_freed_slot_before_the_batch_drains():
     ex = FakeExecutor()
     srv = Server(ex, slots=2, mem_budget=1 << 20)
-    long = srv.submit(Job(tri=0, n=200000, base=0))      # 0.2 s
+    long = srv.submit(Job(tri=0, n=1000000, base=0))     # 1 s
     short = [srv.submit(Job(tri=1, n=1000, base=i)) for i in range(1, 6)]
     for f in short:
         r = f.result(timeout=30)
-        assert r.latency < 0.15   # served while the long job still runs
+        assert r.latency < 0.8    # served while the long job still runs
     assert not long.done()
     long.result(timeout=30)
     srv.close()
