@@ -220,7 +220,7 @@ ts_status ts_hist_read(ts_hist *hist, uint64_t *codes, uint64_t *counts, uint64_
  * ts_code_words(tris[j]) uint64), it also stores every code there.  For each
  * degree present, one persistent kernel serves all jobs of that degree,
  * staging a job's tables into shared memory when it moves to that job; the
- * per-degree kernels run concurrently.  The triangulations must stay loaded
+ * per-degree kernels run concurrently.  counts[j] <= 2^62 (TS_EINVAL above).  The triangulations must stay loaded
  * while the batch exists.  Allocates device memory at creation only. */
 typedef struct ts_batch ts_batch;
 ts_status ts_batch_create(int njobs, ts_tri *const *tris, const uint64_t *counts,

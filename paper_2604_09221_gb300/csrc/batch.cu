@@ -353,7 +353,7 @@ ts_status ts_batch_create(int njobs, ts_tri *const *tris, const uint64_t *counts
   if (!b) return TS_ENOMEM;
   cudaError_t e = cudaGetDevice(&b->device);
   for (int j = 0; j < njobs; ++j) {
-    if (!tris[j]) {
+    if (!tris[j] || counts[j] > (1ull << 62)) {  // counts: room for the work-item arithmetic
       ts_batch_free(b);
       return TS_EINVAL;
     }

@@ -468,6 +468,7 @@ ts_status ts_real_schemes_host(const ts_tri *t, const uint64_t *signs_host, uint
                                uint64_t *codes_host) {
   if (!t || (n && (!signs_host || !codes_host))) return TS_EINVAL;
   if (n == 0) return TS_OK;
+  if (n > (SIZE_MAX / sizeof(uint64_t)) / (size_t)std::max(t->sw, t->cw)) return TS_EINVAL;
   uint64_t *ds = nullptr, *dc = nullptr;
   size_t bs = n * t->sw * sizeof(uint64_t), bc = n * t->cw * sizeof(uint64_t);
   cudaError_t e = cudaMalloc(&ds, bs);
