@@ -1,10 +1,12 @@
 // Test infrastructure: run the block sweep of a generated specialised source
 // (included as GEN) on the host, one lane at a time, for whole warps, and
 // compare each warp's histogram with the oracle's over the same masks.
-// Usage: run_block_sweep <edges file> <warps> [plain|flip|reduced]; the mask
-// map of a warp is (h << oshift) | (t << ishift), t < 2^ib, as in the sweeps
-// without flags, with TS_ENUM_FLIP (bit 0 fixed) and with TS_ENUM_REDUCED
-// (bits 0, 1 and d + 1 fixed).  Exit status 0 when all match.
+// Usage: run_block_sweep <edges file> <warps> [plain|flip|reduced|classify];
+// the mask map of a warp is (h << oshift) | (t << ishift), t < 2^ib, as in
+// the sweeps without flags, with TS_ENUM_FLIP (bit 0 fixed) and with
+// TS_ENUM_REDUCED (bits 0, 1 and d + 1 fixed).  "classify" runs the per-mask
+// classifier tc_classify (query kernel, per-mask sweeps) on 64 x <warps>
+// random masks and the constant ones instead.  Exit status 0 when all match.
 #include "device_shims.h"
 #include GEN
 extern "C" {
@@ -27,6 +29,31 @@ int main(int argc, char **argv) {
   const std::string mode = argc > 3 ? argv[3] : "plain";
   std::vector<int32_t> otri(6 * d * d);
   if (orc_triangles_from_edges(d, (int)e.size() / 4, e.data(), otri.data(), d * d) != d * d) return 2;
+  if (mode == "classify") {
+    const unsigned npts = (d + 1) * (d + 2) / 2;
+    const u64 valid = npts >= 64 ? ~0ull : (1ull << npts) - 1;
+    std::vector<unsigned> scr1((size_t)TcK::WORDS * TcK::THREADS + 64, 0xA5A5A5A5u);
+    unsigned long long st = 99991;
+    int bad = 0, n = 64 * nh + 2;
+    for (int i = 0; i < n; ++i) {
+      st = st * 6364136223846793005ull + 1442695040888963407ull;
+      const u64 m = i == 0 ? 0 : (i == 1 ? valid : (st ^ (st >> 29)) & valid);
+      threadIdx.x = (unsigned)(i & 31);
+      u32 err = 0;
+      const TcS S{scr1.data() + threadIdx.x};
+      const u64 got = tc_classify(m, S, err);
+      uint64_t want = 0;
+      const uint64_t mw = m;
+      if (orc_real_scheme(d, otri.data(), &mw, &want, 1, nullptr) != 0) return 3;
+      if (got != want || err) {
+        if (bad < 3) printf("mask %llx: %llx, oracle %llx (err %u)\n", (unsigned long long)m,
+                            (unsigned long long)got, (unsigned long long)want, err);
+        ++bad;
+      }
+    }
+    printf("d=%d map=classify masks=%d differing=%d\n", d, n, bad);
+    return bad != 0;
+  }
   unsigned ib = d + 1, oshift = d + 1, ishift = 0;
   if (mode == "flip") { ib = d; ishift = 1; }
   else if (mode == "reduced") { ib = d - 1; ishift = 2; oshift = d + 2; }

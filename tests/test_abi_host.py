@@ -108,8 +108,7 @@ def test_specialized_kernels_compile_for_sm103a(eng, d):
     assert "tc_classify" in src and src.count("// vertex ") == V + 2 * (2 * d + 1)
     assert "tc_sweep_table(" in src and "__constant__ u32 tc_ctab" in src
     log = eng.specialized_source(d, e, compile=True)
-    # the three entry kernels (the cold per-mask fallback of the block sweep,
-    # tc_classify_slow, is left out)
+    # the three entry kernels
     spills = {k: int(v) for k, v in re.findall(
         r"Function properties for (tc_\w+)\n[^\n]*?\d+ bytes stack frame, (\d+) bytes spill stores", log)}
     assert set(spills) == {"tc_real_schemes", "tc_enumerate", "tc_enumerate_blocks"}, log[-2000:]

@@ -69,11 +69,13 @@ def run_block_sweep(exe, tmp_path, warps, mode):
 @pytest.mark.parametrize("d,seed", [(4, 4), (5, 5), (7, 7), (8, 8), (9, 9)])
 def test_block_sweep_source_on_the_host(eng, tmp_path, d, seed):
     """Every mask map the block sweep serves: no flag (d + 1 middle-row bits),
-    TS_ENUM_FLIP (d) and TS_ENUM_REDUCED (d - 1), where 32 lanes fit."""
+    TS_ENUM_FLIP (d) and TS_ENUM_REDUCED (d - 1), where 32 lanes fit; and the
+    per-mask classifier of the same source on random masks."""
     exe = build_block_sweep(eng, tmp_path, d, ti.regular_triangulation(d, seed=seed))
     for mode, ib in (("plain", d + 1), ("flip", d), ("reduced", d - 1)):
         if ib >= 5:
             run_block_sweep(exe, tmp_path, 6, mode)
+    run_block_sweep(exe, tmp_path, 16, "classify")
 
 
 @pytest.mark.skipif(shutil.which("g++") is None, reason="needs g++")
@@ -95,6 +97,7 @@ def test_block_sweep_of_the_fig2_triangulations(eng, tmp_path, name):
         if name != "bow_tie":
             assert lanes >= 32 * 4, out   # at least 4 of the 12 warps
         assert int(out.split("odd_lanes=")[1].split()[0]) == 0, out
+    run_block_sweep(exe, tmp_path, 16, "classify")
 
 
 CUDA_INCLUDE = "/usr/local/cuda/include"   # host.cpp's headers and the runtime it links
