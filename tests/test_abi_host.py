@@ -136,3 +136,20 @@ def test_selftest_wait_needs_a_device(eng):
         pytest.skip("covered by the GPU test")
     assert eng.selftest_wait(16) == 4   # TS_ECUDA
     assert eng.library().ts_selftest_wait(0, None) == 1   # TS_EINVAL
+
+
+def test_header_and_library_from_c(eng, tmp_path):
+    """include/tcurve.h compiles as C11 and a plain C program links
+    libtcurve.so and gets the documented answers from the entry points that
+    need no device."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("needs gcc")
+    lib = eng.lib_path()
+    exe = tmp_path / "abi"
+    subprocess.run(["gcc", "-std=c11", "-Wall", "-Werror", f"-I{os.path.join(ROOT, 'include')}",
+                    "-o", str(exe), os.path.join(ROOT, "tests", "host", "abi_from_c.c"), lib,
+                    f"-Wl,-rpath,{os.path.dirname(lib)}"], check=True, capture_output=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0, out.stdout + out.stderr
