@@ -248,24 +248,31 @@ ts_status ts_batch_read(ts_batch *batch, int job, uint64_t *codes, uint64_t *cou
 
 /* Exhaustive sweep that allocates nothing (the paper has no counterpart; it
  * is an engine facility).  For callers that cannot allocate device memory at
- * the time they sweep -- code running while a stream is captured into a CUDA
- * graph, services that reserve all device memory up front and forbid later
- * allocations, threads that must not enter an allocator.  Same results as
- * ts_enumerate followed by ts_hist_read, computed by the table-driven sweep
- * kernel with its hash table, counters and error word in one static device
- * array of 65 600 bytes that every GPU loading this library keeps until the
+ * the time they sweep: services that reserve all device memory up front and
+ * forbid later allocations, and threads that must not enter an allocator (a
+ * real-time loop where an allocation could block, a thread that holds the
+ * allocator's lock).  Same results as ts_enumerate followed by ts_hist_read
+ * on the same range and flags, computed by the table-driven sweep kernel
+ * with its hash table, counters and error word in one static device array
+ * of 65 600 bytes that every GPU loading this library keeps until the
  * process exits.  The caller passes the outputs:
+ *   flags          0, TS_ENUM_FLIP or TS_ENUM_REDUCED (TS_ENUM_SPLITMIX is
+ *                  not accepted here: TS_EINVAL)
  *   codes, counts  device, cap uint64 each: the distinct codes (1 word each)
  *                  and their counts, unsorted
  *   cap            at most 2048 (the array's table holds 2048 codes);
  *                  larger values return TS_EINVAL
  *   n_out          device, 3 uint64: [0] distinct codes found (entries beyond
  *                  cap are dropped), [1] failed instances, [2] error bits
- *                  (nonzero: the table overflowed or an instance failed)
- * Requires d <= 9 and tri loaded on the current device.  Asynchronous on
- * stream.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) and caches it; make that first call before any
- * stream capture.  Every call reuses the same array and clears it first, so
+ *                  (nonzero: more than cap codes, a full table, or a failed
+ *                  instance)
+ * Requires d <= 9 (TS_EUNSUPPORTED above) and tri loaded on the current
+ * device.  Asynchronous on stream.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) and keeps it for the life of
+ * the process; make that first call before any stream capture.  The kept
+ * address belongs to the device's context of that time: after a
+ * cudaDeviceReset of the device, do not call this entry point again in the
+ * same process.  Every call reuses the same array and clears it first, so
  * calls that overlap on the GPU (different streams, or host threads without
  * ordering) race and corrupt each other's results: serialise them. */
 ts_status ts_enumerate_noalloc(const ts_tri *tri, uint64_t lo, uint64_t hi, uint32_t flags,

@@ -3,15 +3,18 @@
 //
 // The regular sweep (ts_enumerate) keeps its hash table, work counter and
 // error words in a ts_hist created with cudaMalloc.  Some callers cannot
-// allocate device memory when they run a sweep: code that runs while a CUDA
-// stream is being captured into a graph (allocation calls are not allowed
-// there), services that reserve all device memory at start-up and forbid
-// later allocations, and hosts whose allocator must not be entered from the
-// calling thread.  For them this entry point runs the same table-driven
-// sweep kernel with all of its scratch in one statically allocated device
-// array that every GPU loading this library holds until the process exits.
+// allocate device memory when they run a sweep: services that reserve all
+// device memory at start-up and forbid later allocations, and hosts whose
+// allocator must not be entered from the calling thread (a real-time loop
+// where an allocation could block, or a thread that holds the allocator's
+// lock).  For them this entry point runs the same table-driven sweep kernel
+// with all of its scratch in one statically allocated device array that
+// every GPU loading this library holds until the process exits.
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <atomic>
+#include <mutex>
 
 #include "engine.h"
 
@@ -26,7 +29,26 @@ constexpr size_t kScratchBytes = kSlots * 16 + 64;   // 65 600 bytes
 static __device__ __align__(256) unsigned char tc_noalloc_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
-unsigned char *g_scratch[kMaxDevices] = {};  // device address per device, set once
+// Device address of the array per device, looked up once (under g_setup_mu)
+// and then read without a lock.
+std::atomic<unsigned char *> g_scratch[kMaxDevices];  // static storage: zero-initialised
+std::mutex g_setup_mu;
+
+// The array's address on the current device `dev`: cudaGetSymbolAddress on
+// the first call for the device, the cached value after that.  Returns null
+// if the lookup fails (the next call tries again).
+unsigned char *scratch_address(int dev) {
+  unsigned char *p = g_scratch[dev].load(std::memory_order_acquire);
+  if (p) return p;
+  std::lock_guard<std::mutex> g(g_setup_mu);
+  p = g_scratch[dev].load(std::memory_order_relaxed);
+  if (p) return p;
+  void *q = nullptr;
+  if (cudaGetSymbolAddress(&q, tc_noalloc_scratch) != cudaSuccess || !q) return nullptr;
+  p = static_cast<unsigned char *>(q);
+  g_scratch[dev].store(p, std::memory_order_release);
+  return p;
+}
 
 // Copy the non-empty slots of the scratch table into the caller's arrays
 // (in slot order) and write n_out[0] = distinct codes, n_out[1] = failed
@@ -71,12 +93,8 @@ extern "C" ts_status ts_enumerate_noalloc(const ts_tri *t, uint64_t lo, uint64_t
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return TS_ECUDA;
   if (dev != t->device) return TS_EINVAL;
   // once per device: the device address of the static array
-  if (!g_scratch[dev]) {
-    void *p = nullptr;
-    if (cudaGetSymbolAddress(&p, tc_noalloc_scratch) != cudaSuccess || !p) return TS_ECUDA;
-    g_scratch[dev] = static_cast<unsigned char *>(p);
-  }
-  unsigned char *base = g_scratch[dev];
+  unsigned char *base = scratch_address(dev);
+  if (!base) return TS_ECUDA;
   ts_hist view;  // a histogram whose storage is the static array (owns nothing)
   view.cw = 1;
   view.slots = kSlots;
