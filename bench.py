@@ -24,11 +24,14 @@ continuous-batching server, p50/p99 job latency).  Other workloads:
                       sign vectors per job, p50/p99 latency and schemes/s
 
   --workload profile  a small sweep for profiler captures (--degree, --log2n,
-                      --kernel, --scratch, --splitmix); prints its rate, which
-                      is not a bench value
+                      --kernel, --scratch, --splitmix; --query: the plain query
+                      kernel on materialised masks instead); prints its rate,
+                      which is not a bench value
+  --workload intpeak  the integer-issue microbenchmark alone (all instruction
+                      kinds; --trips), for profiler captures
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--workload d7|mixed|serving|profile]
+                  [--workload d7|mixed|serving|profile|intpeak]
 """
 from __future__ import annotations
 
@@ -51,7 +54,6 @@ TRI_SEED = 7
 # crossing tests on the 308 edges of T^diamond, unions over non-crossed edges,
 # finds on crossed edges, antipodal unions, tree and encoding).
 ALG_OPS_PER_INSTANCE = 1.2e3
-INT_LANES_PER_SM = 128  # 4 SM sub-partitions x 32 INT32 lanes per clock
 METRIC = "real schemes/sec at d=7 on 1 GB300 (batched vs plain), bit-exact; p50/p99 job latency"
 
 
@@ -182,7 +184,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--workload", default="d7", choices=["d7", "mixed", "serving", "profile"])
+    ap.add_argument("--workload", default="d7",
+                    choices=["d7", "mixed", "serving", "profile", "intpeak"])
     ap.add_argument("--serve-seconds", type=float, default=6.0)
     # the small case of --workload profile (for ncu captures; not a bench value)
     ap.add_argument("--degree", type=int, default=D)
@@ -191,11 +194,16 @@ def main():
     ap.add_argument("--scratch", default="auto", choices=["auto", "shared", "global"])
     ap.add_argument("--splitmix", action="store_true")
     ap.add_argument("--occupancy", type=int, default=0)
+    ap.add_argument("--query", action="store_true")
+    ap.add_argument("--trips", type=int, default=1 << 15)
+    ap.add_argument("--no-stretch", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
     if args.workload == "profile":
         return profile_case(args)
+    if args.workload == "intpeak":
+        return intpeak_workload(args)
     if args.workload == "mixed":
         return mixed_workload(args)
     if args.workload == "serving":
@@ -229,6 +237,7 @@ def main():
         eng.enumerate_schemes(tri, lo, lo + SLICE, hist, stream=stream)
 
     tri.prepare()  # build the specialised kernels before anything is timed
+    int_peak = measure_int_peak(eng, args.trips)
 
     for _ in range(max(args.warmup, 0)):
         step()
@@ -297,10 +306,7 @@ def main():
         pg.destroy_process_group()
         return 0
 
-    peaks = measured_peaks()
-    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
-    sm_max = peaks.get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0
-    peak_tops = n_sm * INT_LANES_PER_SM * sm_max * 1e6 / 1e12
+    peak_tops = int_peak["peak"] / 1e12
     kms = sum(ktimes) / len(ktimes)
     achieved_tops = ALG_OPS_PER_INSTANCE * SLICE / (kms / 1e3) / 1e12
     roofline = {"bound": "alu", "kernel": "tc_enumerate_blocks (specialised to the triangulation)",
@@ -310,7 +316,9 @@ def main():
                 "traffic_note": "no input is read; DRAM carries only scratch write-backs from L2 "
                                 "(55.6 MB per 2^26-mask launch by ncu), which do not scale with the "
                                 "masks swept, so no per-launch figure is given for 2^32",
-                "peak_source": f"{n_sm} SMs x {INT_LANES_PER_SM} INT32 lanes x {sm_max:.0f} MHz (derived)",
+                "peak_source": "measured: ts_int_issue_peak, the best of its instruction kinds "
+                               f"({int_peak['best']}) on this GPU in this run",
+                "int_peak_tops": {k: v / 1e12 for k, v in int_peak["kinds"].items()},
                 "alg_ops_per_instance": ALG_OPS_PER_INSTANCE}
     line = {"metric": METRIC, "value": value, "unit": "schemes/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -330,6 +338,8 @@ def main():
             "roofline": roofline, "clocks": clk}
     if not args.no_plain:
         line["plain"] = plain_kernel(eng, tri, ti, stream)
+    if not args.no_stretch:
+        line["stretch"] = stretch_sweep(eng, tri, stream)
     if not args.no_serving:
         line["serving"] = serving_run(args.serve_seconds)
     if not args.no_cpu_baseline:
@@ -337,6 +347,56 @@ def main():
     print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
+    return 0
+
+
+def measure_int_peak(eng, trips):
+    """The integer-issue peak measured on this GPU now: lane operations per
+    second of each instruction kind of ts_int_issue_peak (best of two runs),
+    and the best kind, which is the roofline's denominator."""
+    kinds = {}
+    for k, name in eng.INT_PEAK_KINDS.items():
+        kinds[name] = max(eng.int_issue_peak(k, trips)[0] for _ in range(2))
+    best = max(kinds, key=kinds.get)
+    return {"kinds": kinds, "best": best, "peak": kinds[best]}
+
+
+def stretch_sweep(eng, tri, stream):
+    """All 2^35 masks of the d = 7 triangulation modulo the global sign flip
+    (TS_ENUM_FLIP: the 2^35 masks with sigma(0,0) = 0), one ts_enumerate,
+    timed once with CUDA events after one 2^30 warm-up sweep."""
+    import torch
+    n = 1 << (tri.num_points - 1)
+    h = eng.Histogram(4096, tri.code_words)
+    eng.enumerate_schemes(tri, 0, 1 << 30, h, eng.TS_ENUM_FLIP, stream=stream)
+    h.clear(stream)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    eng.enumerate_schemes(tri, 0, n, h, eng.TS_ENUM_FLIP, stream=stream)
+    b.record(stream)
+    b.synchronize()
+    ms = a.elapsed_time(b)
+    codes, counts, failed = h.read(stream)
+    assert failed == 0 and int(counts.sum()) == n, "stretch sweep lost instances"
+    assert len(codes) <= 121, "more than the 121 real schemes of degree 7"
+    return {"workload": "d7_flip_sweep_2p35", "masks": n, "ms": ms,
+            "value": n / (ms / 1e3), "unit": "schemes/s", "distinct_schemes": len(codes),
+            "flags": "TS_ENUM_FLIP"}
+
+
+def intpeak_workload(args):
+    """The integer-issue microbenchmark alone (for profiler captures)."""
+    import torch
+
+    import paper_2604_09221_gb300 as eng
+    from paper_2604_09221_gb300 import build as _b
+    torch.cuda.set_device(0)
+    _b.build()
+    r = measure_int_peak(eng, args.trips)
+    print(json.dumps({"intpeak": True, "trips": args.trips,
+                      "tops": {k: v / 1e12 for k, v in r["kinds"].items()}, "best": r["best"]}),
+          flush=True)
     return 0
 
 
@@ -360,8 +420,26 @@ def profile_case(args):
     tri.set_occupancy(args.occupancy)
     if args.kernel != "table" and d <= 9:
         tri.prepare()
-    flags = eng.TS_ENUM_SPLITMIX if (args.splitmix or d > 9) else 0
     n = 1 << args.log2n
+    if args.query:  # the plain query kernel on n materialised sign vectors
+        masks = eng.splitmix_masks(d, 0, n)
+        out = torch.empty((n, tri.code_words), dtype=torch.int64, device="cuda")
+        ms = []
+        for _ in range(2):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            tri.real_schemes(masks, out=out, sync=False)
+            b.record()
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        tri.sync()
+        print(json.dumps({"profile_case": True, "query": True, "degree": d, "n": n,
+                          "kernel": args.kernel, "ms": ms,
+                          "bytes_per_launch": n * 8 * (tri.sign_words + tri.code_words),
+                          "schemes_per_s": n / (min(ms) / 1e3)}), flush=True)
+        return 0
+    flags = eng.TS_ENUM_SPLITMIX if (args.splitmix or d > 9) else 0
     h = eng.Histogram(1 << 14, tri.code_words)
     ms = []
     for _ in range(2):
@@ -408,9 +486,14 @@ def plain_kernel(eng, tri, ti, stream):
         times.append(a.elapsed_time(b))
     tri.sync(stream)
     ms = statistics.median(times)
+    nbytes = n * 8 * (tri.sign_words + tri.code_words)  # sign words in, code words out
+    hbm_peak = measured_peaks().get("hbm_gbs")
+    gbs = nbytes / (ms / 1e3) / 1e9
     return {"value": n / (ms / 1e3), "unit": "schemes/s",
             "kernel": "tc_real_schemes (specialised, one launch over materialised masks)",
-            "n": n, "ms": ms, "hbm_bytes": n * 16}
+            "n": n, "ms": ms, "hbm_bytes": nbytes, "hbm_gbs": gbs,
+            "hbm_frac": gbs / hbm_peak if hbm_peak else None,
+            "hbm_peak_gbs": hbm_peak}
 
 
 def job_base(seed, stream):

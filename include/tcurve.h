@@ -286,6 +286,20 @@ ts_status ts_enumerate_noalloc(const ts_tri *tri, uint64_t lo, uint64_t hi, uint
  * usable), TS_ECUDA without a device.  Synchronises stream. */
 ts_status ts_selftest_wait(uint64_t iters, void *stream);
 
+/* Measured integer-issue peak (an engine facility for the roofline of the
+ * kernels above, which are integer work: no tensor-core or floating-point
+ * component; the paper has no counterpart).  Runs a kernel that fills every
+ * SM with 64 warps, each thread issuing independent chains of one integer
+ * instruction kind for `trips` loop trips (1 <= trips <= 2^24), and times it
+ * with CUDA events on stream:
+ *   kind 0  lop3 (three-input logic)     kind 2  mad.lo (integer multiply-add)
+ *   kind 1  add                          kind 3  lop3 and mad.lo alternating
+ * *lane_ops_per_s receives the lane operations per second (thread
+ * instructions of that kind per second); *ms (may be NULL) the kernel time.
+ * Synchronises stream.  TS_ECUDA without a device. */
+ts_status ts_int_issue_peak(int kind, uint64_t trips, double *lane_ops_per_s, double *ms,
+                            void *stream);
+
 /* Rohlin-Viro notation of a code (Sec. 2): "<0>", "<J>", "<4>", "<1<1>>",
  * "<J + 1<1> + 2>" ('+' stands for the disjoint union); writes at most len
  * bytes including the terminating NUL. */

@@ -87,6 +87,8 @@ def _load():
                 "ts_batch_set_tile": ([P, I, I, I, I], I),
                 "ts_batch_run": ([P, I, P], I),
                 "ts_batch_read": ([P, I, P, P, U64, ctypes.POINTER(U64), ctypes.POINTER(U64), P], I),
+                "ts_int_issue_peak": ([I, U64, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double), P], I),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -391,6 +393,19 @@ def selftest_wait(iters: int = 4096, stream=None) -> int:
     returns the status code (TS_ETIMEOUT = 6 when the wait gave up as
     designed)."""
     return int(_load().ts_selftest_wait(int(iters), None if stream is None else _stream_handle(stream)))
+
+
+INT_PEAK_KINDS = {0: "lop3", 1: "add", 2: "mad.lo", 3: "lop3+mad.lo"}
+
+
+def int_issue_peak(kind: int, trips: int = 1 << 15, stream=None):
+    """(lane operations per second, kernel ms) of the integer-issue
+    microbenchmark ts_int_issue_peak for one instruction kind (INT_PEAK_KINDS)."""
+    r = ctypes.c_double()
+    ms = ctypes.c_double()
+    _check(_load().ts_int_issue_peak(int(kind), int(trips), ctypes.byref(r), ctypes.byref(ms),
+                                     _stream_handle(stream)), "ts_int_issue_peak")
+    return r.value, ms.value
 
 
 def scheme_string(d: int, code) -> str:

@@ -147,12 +147,11 @@ struct JitModule {
   }
 };
 
-std::string jit_source(const Diamond &D, bool global, int min_blocks) {
-  const Layout L = layout_for(D, global);
-  const int d = D.d, V = D.V;
-  std::ostringstream o;
-  o << "// T-curve real-scheme kernels specialised to one triangulation of " << d
-    << "*Delta_2 (generated)\n";
+namespace {
+
+// The traits struct TcK of a generated source: degree, block size and the
+// scratch layout of tc_layout.h (both back ends' offsets).
+void emit_traits(std::ostringstream &o, const Layout &L, int d, int V, bool global, int min_blocks) {
   o << "struct TcK {\n";
   auto c = [&](const char *n, long v) { o << "  static constexpr unsigned " << n << " = " << v << "u;\n"; };
   c("D", d); c("V", V); c("NPOINTS", (d + 1) * (d + 2) / 2); c("RMAX", L.rmax); c("NB", L.nb);
@@ -160,41 +159,35 @@ std::string jit_source(const Diamond &D, bool global, int min_blocks) {
   c("PCAP", L.pcap); c("WODD", L.wodd); c("WORDS", L.words); c("B", d + 1); c("SNAPW", L.snapw);
   c("WLAB", L.wlab); c("EPW", L.epw); c("OFF_SNAP", snap_offset(L));
   c("GSCR", global ? 1 : 0); c("MINB", min_blocks);
+  c("W", L.sw); c("CW", L.cw); c("WIDE", L.wide);
   c("OFF_LPAR", L.off_lpar); c("OFF_CAND", L.off_cand); c("OFF_LAB", L.off_lab);
   c("OFF_BPAIR", L.off_bpair); c("OFF_PEND", L.off_pend); c("OFF_ADJ", L.off_adj);
   c("OFF_RLAB", L.off_rlab); c("OFF_TPAR", L.off_tpar); c("OFF_ORDER", L.off_order);
   c("OFF_CLEN", L.off_clen); c("OFF_ODD", L.off_odd); c("OFF_CODE", L.off_code);
+  c("OFF_WPAR", L.off_wpar); c("OFF_WFC", L.off_wfc); c("OFF_WNS", L.off_wns);
+  c("OFF_WENT", L.off_went); c("OFF_WARENA", L.off_warena); c("OFF_WTEMP", L.off_wtemp);
+  c("WARENA", L.warena_words);
   o << "};\n";
-  o << "#define TC_HEAVY_FN __forceinline__\n";
-  o << kRuntimeSrc;
-  o << "#define TC_BIT(k) ((k) < 32 ? ((slo >> ((k) & 31)) & 1u) : ((shi >> ((k) & 31)) & 1u))\n"
-    << "typedef TcScratch<TcK> TcS;\n\n";
-  // the triangulation tables, for the table-driven half-diamonds of the block
-  // sweep (warp-uniform reads: constant memory)
-  std::vector<uint32_t> tab;
-  TableLayout tl{};
-  if (!pack_diamond_tables(D, tab, tl)) return std::string();
-  o << "__constant__ u32 tc_ctab[" << tab.size() << "] = {";
-  for (size_t i = 0; i < tab.size(); ++i) o << (i % 12 ? " " : "\n  ") << tab[i] << "u,";
-  o << "\n};\n\n";
-  // which antipodal pairs / boundary edges complete at each vertex
-  std::vector<std::vector<int>> anti_at(V), bedge_at(V);
-  for (size_t i = 0; i < D.anti.size(); ++i) anti_at[D.anti[i].second].push_back((int)i);
-  if (d % 2)
-    for (size_t i = 0; i < D.bedge.size(); ++i)
-      bedge_at[std::max(D.bedge[i].first, D.bedge[i].second)].push_back((int)i);
+}
 
-  // One vertex of the sweep.  mid_sig: expression of the middle-row mask word
-  // (the block sweep varies it per instance), or empty to read slo/shi.
-  // check_flush: emit the test that applies the pending joins when the list
-  // might overflow (left out where the joins pushed since the last flush
-  // provably fit).
-  // Static flush schedules of the join list: the whole sweep (per-mask
-  // kernels) and the middle row alone (block sweep, empty list at its start).
-  const int Vo0 = V - (2 * d + 1);
-  const std::vector<char> flush_full = flush_schedule(D, 0, V, L.pcap);
-  const std::vector<char> flush_mid = flush_schedule(D, Vo0, V, L.pcap);
-  auto emit_vertex = [&](int v, const char *ind, const char *mid_sig, bool flush) {
+// Straight-line code of one vertex of the sweep (Alg. 1, lines 3-4): its
+// sign from TC_BIT (or, with mid_sig, from that expression: the block sweep's
+// middle-row pattern), its label from the first same-sign fan entry or a
+// fresh one, a join per further same-sign run of its fan, its antipodal
+// join and, for odd d, the crossed boundary edges it completes.  flush: apply
+// the pending joins first (the static schedule of flush_schedule).
+struct VertexEmitter {
+  const Diamond &D;
+  std::ostringstream &o;
+  std::vector<std::vector<int>> anti_at, bedge_at;  // pairs / boundary edges completed at v
+  VertexEmitter(const Diamond &DD, std::ostringstream &oo)
+      : D(DD), o(oo), anti_at(DD.V), bedge_at(DD.V) {
+    for (size_t i = 0; i < D.anti.size(); ++i) anti_at[D.anti[i].second].push_back((int)i);
+    if (D.d % 2)
+      for (size_t i = 0; i < D.bedge.size(); ++i)
+        bedge_at[std::max(D.bedge[i].first, D.bedge[i].second)].push_back((int)i);
+  }
+  void emit(int v, const char *ind, const char *mid_sig, bool flush) {
     const auto &fan = D.fan[v];
     const auto &lk = D.link[v];
     const int m = (int)fan.size();
@@ -237,6 +230,40 @@ std::string jit_source(const Diamond &D, bool global, int min_blocks) {
       o << ind << "if (s" << a << " ^ s" << b << ") { tc_bpair(S, nb, L" << a << ", L" << b
         << "); ++nb; }\n";
     }
+  }
+};
+
+}  // namespace
+
+std::string jit_source(const Diamond &D, bool global, int min_blocks) {
+  const Layout L = layout_for(D, global);
+  const int d = D.d, V = D.V;
+  std::ostringstream o;
+  o << "// T-curve real-scheme kernels specialised to one triangulation of " << d
+    << "*Delta_2 (generated)\n";
+  emit_traits(o, L, d, V, global, min_blocks);
+  o << "#define TC_HEAVY_FN __forceinline__\n";
+  o << kRuntimeSrc;
+  o << "#define TC_BIT(k) ((k) < 32 ? ((slo >> ((k) & 31)) & 1u) : ((shi >> ((k) & 31)) & 1u))\n"
+    << "typedef TcScratch<TcK> TcS;\n\n";
+  // the triangulation tables, for the table-driven half-diamonds of the block
+  // sweep (warp-uniform reads: constant memory)
+  std::vector<uint32_t> tab;
+  TableLayout tl{};
+  if (!pack_diamond_tables(D, tab, tl)) return std::string();
+  o << "__constant__ u32 tc_ctab[" << tab.size() << "] = {";
+  for (size_t i = 0; i < tab.size(); ++i) o << (i % 12 ? " " : "\n  ") << tab[i] << "u,";
+  o << "\n};\n\n";
+  VertexEmitter em(D, o);
+  const auto &anti_at = em.anti_at;
+  const auto &bedge_at = em.bedge_at;
+  // Static flush schedules of the join list: the whole sweep (per-mask
+  // kernels) and the middle row alone (block sweep, empty list at its start).
+  const int Vo0 = V - (2 * d + 1);
+  const std::vector<char> flush_full = flush_schedule(D, 0, V, L.pcap);
+  const std::vector<char> flush_mid = flush_schedule(D, Vo0, V, L.pcap);
+  auto emit_vertex = [&](int v, const char *ind, const char *mid_sig, bool flush) {
+    em.emit(v, ind, mid_sig, flush);
   };
   const int Vo = V - (2 * d + 1);  // the middle row comes last in the sweep
 
