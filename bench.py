@@ -197,6 +197,7 @@ def main():
     ap.add_argument("--query", action="store_true")
     ap.add_argument("--trips", type=int, default=1 << 15)
     ap.add_argument("--no-stretch", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -340,6 +341,10 @@ def main():
         line["plain"] = plain_kernel(eng, tri, ti, stream)
     if not args.no_stretch:
         line["stretch"] = stretch_sweep(eng, tri, stream)
+    if not args.no_mixed:
+        mx = mixed_run(args.steps, args.warmup)
+        mx["alg_frac"] = mx["alg_tops"] * 1e12 / int_peak["peak"]
+        line["mixed"] = mx
     if not args.no_serving:
         line["serving"] = serving_run(args.serve_seconds)
     if not args.no_cpu_baseline:
@@ -576,17 +581,28 @@ def serving_workload(args, seconds):
     return 0
 
 
-def mixed_workload(args, degrees=(5, 6, 7, 8, 9, 10), per_degree=32, seed=31):
-    """The mixed-degree batch as one CUDA-graph launch per step."""
+def alg_ops(d: int) -> float:
+    """Algorithmic integer operations per instance at degree d: sign
+    extension (3 per sign word), one crossing test, about 1.5 union steps and
+    one find per edge of T^diamond (6d^2 + 2d edges), 6 per antipodal pair
+    and about 4 per oval of Harnack's bound M for tree and code (1187 at d = 7)."""
+    W = ((d + 1) * (d + 2) // 2 + 63) // 64
+    E = 6 * d * d + 2 * d
+    M = (d - 1) * (d - 2) // 2 + 1
+    return 3 * W + 3.5 * E + 6 * d + 4 * M
+
+
+def mixed_run(steps, warmup, degrees=(5, 6, 7, 8, 9, 10), per_degree=32, seed=31):
+    """The mixed-degree batch: 32 seeded triangulations per d in 5..10,
+    2^U(10,24) splitmix64 sign vectors each, one CUDA-graph launch per step
+    (one persistent kernel per degree), tiles from the autotuner; every job's
+    histogram is checked to count all its sign vectors."""
     import numpy as np
     import torch
 
     import paper_2604_09221_gb300 as eng
     import tcurve_inputs as ti
     from paper_2604_09221_gb300 import autotune
-    from paper_2604_09221_gb300 import build as _b
-    torch.cuda.set_device(0)
-    _b.build()
     rng = np.random.default_rng(seed)
     tris, counts, bases = [], [], []
     for d in degrees:
@@ -594,20 +610,23 @@ def mixed_workload(args, degrees=(5, 6, 7, 8, 9, 10), per_degree=32, seed=31):
             tris.append(eng.Triangulation(d, e))
             counts.append(int(2 ** rng.uniform(10, 24)))
             bases.append(job_base(seed * 100 + d, k))
+    t0 = time.perf_counter()
+    batch = eng.Batch(tris, counts, bases)   # compiles the specialised groups
+    build_s = time.perf_counter() - t0
     # tiles cached in the file TCURVE_TILE_CACHE names, when set
     tiles = autotune.autotune(tris, counts, bases, reps=1)
-    batch = eng.Batch(tris, counts, bases)
     autotune.apply(batch, tiles)
-    for _ in range(max(args.warmup, 1)):
-        batch.run(graph=True)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(warmup, 1)):
+        batch.run(graph=True, stream=stream)
     torch.cuda.synchronize()
     times = []
-    for _ in range(args.steps):
+    for _ in range(steps):
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
-        a.record()
-        batch.run(graph=True)
-        b.record()
+        a.record(stream)
+        batch.run(graph=True, stream=stream)
+        b.record(stream)
         b.synchronize()
         times.append(a.elapsed_time(b))
     for j in range(len(tris)):
@@ -615,15 +634,36 @@ def mixed_workload(args, degrees=(5, 6, 7, 8, 9, 10), per_degree=32, seed=31):
         assert failed == 0 and int(cnt.sum()) == counts[j]
     ms = sum(times) / len(times)
     total = sum(counts)
+    ops = sum(n * alg_ops(t.d) for t, n in zip(tris, counts))
+    fam = {d: batch.info(d) for d in degrees}
+    return {"value": total / (ms / 1e3), "unit": "schemes/s", "ms": ms, "steps": steps,
+            "workload": "mixed_degree_batch", "degrees": list(degrees),
+            "triangulations_per_degree": per_degree, "jobs": len(tris), "sign_vectors": total,
+            "counts": "2^U(10,24) per triangulation",
+            "kernels": {str(d): fam[d]["kernel"] for d in degrees},
+            "tiles": {str(d): [fam[d]["threads"], fam[d]["chunk"], fam[d]["scratch"]] for d in degrees},
+            "build_s": build_s, "alg_tops": ops / (ms / 1e3) / 1e12,
+            "gpu_launches_per_step": len(degrees)}
+
+
+def mixed_workload(args):
+    """The mixed-degree batch as one CUDA-graph launch per step (its own line)."""
+    import torch
+
+    from paper_2604_09221_gb300 import build as _b
+    torch.cuda.set_device(0)
+    _b.build()
+    import paper_2604_09221_gb300 as eng
+    peak = measure_int_peak(eng, args.trips)
+    r = mixed_run(args.steps, args.warmup)
     line = {"metric": "mixed-degree batch: schemes/s (one CUDA graph launch per step)",
-            "value": total / (ms / 1e3), "unit": "schemes/s", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": "u64",
+            "value": r["value"], "unit": "schemes/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True, "dtype": "u64",
             "data": "synthetic",
-            "config": {"workload": "mixed_degree_batch", "degrees": list(degrees),
-                       "triangulations_per_degree": per_degree, "jobs": len(tris),
-                       "sign_vectors": total, "counts": "2^U(10,24) per triangulation",
-                       "tiles": {str(d): list(t) for d, t in tiles.items()}},
-            "gpu_launches": len(degrees) * args.steps}
+            "config": {k: r[k] for k in ("workload", "degrees", "triangulations_per_degree", "jobs",
+                                         "sign_vectors", "counts", "kernels", "tiles")},
+            "alg_frac": r["alg_tops"] * 1e12 / peak["peak"], "build_s": r["build_s"],
+            "gpu_launches": r["gpu_launches_per_step"] * args.steps}
     print(json.dumps(line), flush=True)
     return 0
 

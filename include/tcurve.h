@@ -240,6 +240,43 @@ ts_status ts_batch_set_tile(ts_batch *batch, int d, int threads, int chunk, int 
  * into a CUDA graph on the first call (and after a tile change) and the graph
  * is launched; otherwise the same work is enqueued directly. */
 ts_status ts_batch_run(ts_batch *batch, int use_graph, void *stream);
+/* Kernel family and tile of the degree-d group of a batch (an engine
+ * facility).  A group runs the table-driven kernel (TS_KERNEL_TABLE) or
+ * specialised code (TS_KERNEL_SPECIALIZED): every distinct triangulation of
+ * the group compiled into a straight-line sweep of its own (one relocatable
+ * object each, compiled with NVRTC in parallel host threads at
+ * ts_batch_create) and linked with the group's persistent kernel (nvJitLink),
+ * which calls each job's sweep.  A group is specialised when one of its
+ * triangulations was set to TS_KERNEL_SPECIALIZED, or, with TS_KERNEL_AUTO,
+ * when d <= 12 and the group holds at least 2^22 sign vectors; never when
+ * one of them was set to TS_KERNEL_TABLE, and not if the code cannot be
+ * built (log then says why).  Specialised groups have 128-thread blocks and
+ * global scratch (ts_batch_set_tile accepts only those; the chunk may vary).
+ *   kernel, threads, chunk, scratch (each may be NULL) receive the group's
+ *   TS_KERNEL_*, threads per block, sign vectors per work item, TS_SCRATCH_*
+ *   log (may be NULL; len bytes with the NUL) the reason a specialised
+ *   group fell back to the table-driven kernel, or ""
+ * TS_EINVAL if the batch has no job of degree d. */
+ts_status ts_batch_info(const ts_batch *batch, int d, int *kernel, int *threads, int *chunk,
+                        int *scratch, char *log, size_t len);
+/* Kernel family of the degree-d group: TS_KERNEL_TABLE, TS_KERNEL_SPECIALIZED
+ * (builds the group's specialised code now if it has none: about a second
+ * of compilation per triangulation, in parallel host threads) or
+ * TS_KERNEL_AUTO (the rule at creation).  Resets the group's tile to the
+ * family's default.  Waits for all work on the device first; the next
+ * ts_batch_run with use_graph captures a new graph.  TS_ECUDA if the
+ * specialised code cannot be built (the group then runs table-driven, and
+ * ts_batch_info's log says why), TS_EINVAL without a group of degree d. */
+ts_status ts_batch_set_kernel(ts_batch *batch, int d, int kind);
+/* Host-only helper (no device needed): validate ntri edge lists of degree d
+ * and build the specialised batch code for them as ts_batch_create would
+ * (one object per triangulation and the persistent kernel, compiled with
+ * NVRTC for sm_103a and linked with nvJitLink).  *linked_bytes receives the
+ * size of the linked image; log (len bytes) the compiler logs of all
+ * objects (their ptxas resource lines), or the failing step's log.
+ * TS_ENOTTRI for a bad edge list, TS_ECUDA if compiling or linking fails. */
+ts_status ts_batch_specialized_link(int d, int ntri, const int32_t *const *edges_ij,
+                                    const int *n_edges, size_t *linked_bytes, char *log, size_t len);
 /* Histogram of one job, sorted by code, after synchronising stream (same
  * output conventions as ts_hist_read with ts_code_words(tris[job]) words per
  * code; n_failed counts the whole batch). */

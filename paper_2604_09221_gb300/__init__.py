@@ -87,6 +87,11 @@ def _load():
                 "ts_batch_set_tile": ([P, I, I, I, I], I),
                 "ts_batch_run": ([P, I, P], I),
                 "ts_batch_read": ([P, I, P, P, U64, ctypes.POINTER(U64), ctypes.POINTER(U64), P], I),
+                "ts_batch_set_kernel": ([P, I, I], I),
+                "ts_batch_info": ([P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
+                                   ctypes.POINTER(I), ctypes.c_char_p, ctypes.c_size_t], I),
+                "ts_batch_specialized_link": ([I, I, P, P, ctypes.POINTER(ctypes.c_size_t),
+                                               ctypes.c_char_p, ctypes.c_size_t], I),
                 "ts_int_issue_peak": ([I, U64, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_double), P], I),
             }
@@ -330,6 +335,22 @@ class Batch:
         _check(_lib.ts_batch_set_tile(self._h, int(d), int(threads), int(chunk), int(scratch)),
                "ts_batch_set_tile")
 
+    def set_kernel(self, d: int, kind: int):
+        """Kernel family of the degree-d group (ts_batch_set_kernel): TS_KERNEL_TABLE,
+        TS_KERNEL_SPECIALIZED (compiled now if needed) or TS_KERNEL_AUTO."""
+        _check(_lib.ts_batch_set_kernel(self._h, int(d), int(kind)), "ts_batch_set_kernel")
+
+    def info(self, d: int) -> dict:
+        """Kernel family and tile of the degree-d group (ts_batch_info)."""
+        k, t, c, sc = (ctypes.c_int() for _ in range(4))
+        buf = ctypes.create_string_buffer(1 << 14)
+        _check(_lib.ts_batch_info(self._h, int(d), ctypes.byref(k), ctypes.byref(t), ctypes.byref(c),
+                                  ctypes.byref(sc), buf, len(buf)), "ts_batch_info")
+        return {"kernel": {TS_KERNEL_TABLE: "table", TS_KERNEL_SPECIALIZED: "specialized"}[k.value],
+                "threads": t.value, "chunk": c.value,
+                "scratch": {TS_SCRATCH_SHARED: "shared", TS_SCRATCH_GLOBAL: "global"}[sc.value],
+                "log": buf.value.decode(errors="replace")}
+
     def run(self, graph: bool = True, stream=None):
         _check(_lib.ts_batch_run(self._h, int(bool(graph)), _stream_handle(stream)), "ts_batch_run")
 
@@ -370,6 +391,22 @@ def specialized_source(d: int, edges, compile: bool = False) -> str:
     if st != 0:
         raise TSError(st, "ts_specialized_source: " + text[-3000:])
     return text
+
+
+def batch_specialized_link(d: int, edge_lists, with_log: bool = False):
+    """Build (compile and link, no device needed) the specialised batch code
+    of the given triangulations of degree d; returns the linked image's size
+    in bytes (and the compiler logs with ``with_log``), raises TSError with
+    the compiler or linker log on failure."""
+    arrs = [np.ascontiguousarray(np.asarray(e, dtype=np.int32).reshape(-1, 4)) for e in edge_lists]
+    ptrs = (ctypes.c_void_p * len(arrs))(*[a.ctypes.data for a in arrs])
+    ns = (ctypes.c_int * len(arrs))(*[len(a) for a in arrs])
+    size = ctypes.c_size_t()
+    buf = ctypes.create_string_buffer(1 << 20)
+    st = _load().ts_batch_specialized_link(int(d), len(arrs), ptrs, ns, ctypes.byref(size), buf, len(buf))
+    if st != 0:
+        raise TSError(st, "ts_batch_specialized_link: " + buf.value.decode(errors="replace")[-3000:])
+    return (size.value, buf.value.decode(errors="replace")) if with_log else size.value
 
 
 def splitmix_masks(d: int, base: int, n: int, out=None, stream=None):

@@ -3,11 +3,13 @@
 For every degree in a batch the persistent kernel has three knobs: threads
 per block, sign vectors per work item, and where the per-thread scratch
 lives (shared memory, or global memory for the large degrees whose scratch
-leaves few warps per SM).  The tuner times candidate tiles on the batch's own
-jobs of that degree (a sub-batch, so degrees are tuned independently), keeps
-the fastest, and can store the choice in a JSON cache keyed by GPU name and
-degree (path from the argument or the TCURVE_TILE_CACHE environment
-variable).
+leaves few warps per SM).  A degree group that runs specialised code
+(ts_batch_info: compiled per triangulation, 128-thread blocks and global
+scratch fixed at compile time) has one knob, the sign vectors per work item.
+The tuner times candidate tiles on the batch's own jobs of that degree (a
+sub-batch, so degrees are tuned independently), keeps the fastest, and can
+store the choice in a JSON cache keyed by GPU name, degree and kernel family
+(path from the argument or the TCURVE_TILE_CACHE environment variable).
 """
 from __future__ import annotations
 
@@ -46,26 +48,37 @@ def _time_batch(batch, reps: int) -> float:
     return best
 
 
+def candidates(d: int, family: dict, threads, chunk_per_thread, scratch):
+    """Tiles worth timing for a degree group of the given kernel family."""
+    if family["kernel"] == "specialized":
+        t = family["threads"]
+        return [(t, t * c, GLOBAL) for c in chunk_per_thread]
+    return [(t, t * c, s) for s in (scratch_choices(d) if scratch is None else scratch)
+            for t in threads for c in chunk_per_thread]
+
+
 def tune_degree(tris, counts, bases, threads: Iterable[int] = THREADS,
                 chunk_per_thread: Iterable[int] = CHUNK_PER_THREAD, reps: int = 3,
-                scratch: Optional[Iterable[int]] = None) -> Tuple[int, int, int, float]:
-    """Fastest (threads, chunk, scratch, ms) for the jobs (all of one degree)."""
+                scratch: Optional[Iterable[int]] = None, sub=None) -> Tuple[int, int, int, float]:
+    """Fastest (threads, chunk, scratch, ms) for the jobs (all of one degree);
+    ``sub``: a batch of exactly these jobs, if one exists already."""
     from . import Batch, TSError
     d = tris[0].d
     assert all(t.d == d for t in tris)
-    sub = Batch(tris, counts, bases)
+    own = sub is None
+    if own:
+        sub = Batch(tris, counts, bases)
     best = None
-    for s in (scratch_choices(d) if scratch is None else scratch):
-        for t in threads:
-            for c in chunk_per_thread:
-                try:
-                    sub.set_tile(d, t, t * c, s)
-                except TSError:
-                    continue  # the block does not fit shared memory
-                ms = _time_batch(sub, reps)
-                if best is None or ms < best[3]:
-                    best = (t, t * c, s, ms)
-    sub.close()
+    for t, c, s in candidates(d, sub.info(d), threads, chunk_per_thread, scratch):
+        try:
+            sub.set_tile(d, t, c, s)
+        except TSError:
+            continue  # the block does not fit shared memory
+        ms = _time_batch(sub, reps)
+        if best is None or ms < best[3]:
+            best = (t, c, s, ms)
+    if own:
+        sub.close()
     if best is None:
         raise RuntimeError(f"no tile fits degree {d}")
     return best
@@ -81,18 +94,21 @@ def autotune(tris, counts, bases, cache: Optional[str] = None, reps: int = 3,
     if cache and os.path.exists(cache):
         with open(cache) as f:
             store = json.load(f)
+    from . import Batch
     gpu = _gpu_name()
     tiles: Dict[int, Tuple[int, int, int]] = {}
     for d in sorted({t.d for t in tris}):
-        key = f"{gpu}|d={d}|tile3"
+        idx = [i for i, t in enumerate(tris) if t.d == d]
+        sel = ([tris[i] for i in idx], [counts[i] for i in idx], [bases[i] for i in idx])
+        sub = Batch(*sel)   # its kernel family decides the tile space
+        key = f"{gpu}|d={d}|{sub.info(d)['kernel']}|tile3"
         if key in store:
             tiles[d] = tuple(store[key][:3])
-            continue
-        idx = [i for i, t in enumerate(tris) if t.d == d]
-        t, c, s, ms = tune_degree([tris[i] for i in idx], [counts[i] for i in idx],
-                                  [bases[i] for i in idx], threads, chunk_per_thread, reps)
-        tiles[d] = (t, c, s)
-        store[key] = [t, c, s, ms]
+        else:
+            t, c, s, ms = tune_degree(*sel, threads, chunk_per_thread, reps, sub=sub)
+            tiles[d] = (t, c, s)
+            store[key] = [t, c, s, ms]
+        sub.close()
     if cache:
         tmp = cache + ".tmp"
         with open(tmp, "w") as f:

@@ -12,12 +12,21 @@
 // each degree has its own tile shape (threads per block, instances per work
 // item, scratch in shared or global memory), which ts_batch_set_tile
 // changes (the autotuner's knob).
+//
+// A degree group with many sign vectors (or whose triangulations ask for
+// TS_KERNEL_SPECIALIZED) runs specialised code instead: its persistent
+// kernel tcj_jobs (jit.cpp) calls, per job, the straight-line sweep generated
+// for that job's triangulation; all of the batch's objects are compiled in
+// parallel at creation and linked per degree.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <algorithm>
+#include <cstring>
 #include <map>
+#include <memory>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "engine.h"
@@ -53,7 +62,14 @@ struct DevJob {
   unsigned long long *hcnt;
   u64 hslots;
   u64 chunk0;         // first work item of the job
+  u32 fn, pad;        // specialised groups: index of the job's function in the module
 };
+static_assert(sizeof(DevJob) == 72, "the job table layout of the generated batch kernels");
+
+// Degree groups of at least this many sign vectors run specialised code
+// (TS_KERNEL_AUTO): the compile at creation (about a second per
+// triangulation, in parallel) pays for itself.
+constexpr uint64_t kJitGroupMin = 1ull << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -231,6 +247,8 @@ struct ts_batch {
   struct Group {  // all jobs of one degree
     int d = 0, threads = 64, chunk = 1024;
     bool global = false;        // per-thread scratch in global memory
+    std::shared_ptr<JitJobsModule> jit;  // specialised kernel (null: table-driven)
+    std::string jit_log;        // why the specialised kernel could not be built
     JobsFn fn = nullptr;        // the kernel of this tile, its launch shape
     size_t smem = 0;
     unsigned grid = 1;
@@ -258,6 +276,7 @@ struct ts_batch {
   cudaEvent_t fork = nullptr;
   cudaGraphExec_t exec = nullptr;
   int device = 0;
+  std::vector<ts_tri *> tris;  // triangulation of every job
 };
 
 namespace {
@@ -283,22 +302,30 @@ cudaError_t upload_group(ts_batch *b, ts_batch::Group &g) {
 // tile (host work only: done at creation and on a tile change, never while a
 // stream is being captured).
 cudaError_t prepare_group(ts_batch::Group &g) {
-  g.fn = jobs_fn_dt(g.d, g.threads, g.global);
-  if (!g.fn) return cudaErrorInvalidConfiguration;
-  g.smem = jobs_smem(g.d, g.threads, g.table_words, g.global);
-  cudaError_t e = cudaFuncSetAttribute((const void *)g.fn,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
-  if (e != cudaSuccess) return e;
   int per_sm = 0, sms = 0, dev = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)g.fn, g.threads, g.smem);
-  if (e != cudaSuccess) return e;
+  cudaError_t e = cudaSuccess;
+  if (g.jit) {  // specialised: 128-thread blocks, global scratch, grid from its occupancy
+    g.fn = nullptr;
+    g.smem = 0;
+    per_sm = jit_jobs_blocks_per_sm(*g.jit);
+  } else {
+    g.fn = jobs_fn_dt(g.d, g.threads, g.global);
+    if (!g.fn) return cudaErrorInvalidConfiguration;
+    g.smem = jobs_smem(g.d, g.threads, g.table_words, g.global);
+    e = cudaFuncSetAttribute((const void *)g.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)g.smem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)g.fn, g.threads, g.smem);
+    if (e != cudaSuccess) return e;
+  }
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const uint64_t cap = (uint64_t)per_sm * sms;
   g.grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(cap, g.items));
   if (g.global) {
-    const size_t need = (size_t)g.grid * scratch_words(g.d, g.threads) * 4;
+    const size_t need = g.jit ? (size_t)g.grid * jit_jobs_slab_bytes(*g.jit)
+                              : (size_t)g.grid * scratch_words(g.d, g.threads) * 4;
     if (need > g.scratch_bytes) {
       if (g.scratch) cudaFree(g.scratch);
       g.scratch = nullptr;
@@ -312,9 +339,12 @@ cudaError_t prepare_group(ts_batch::Group &g) {
 }
 
 cudaError_t launch_group(ts_batch *b, ts_batch::Group &g, cudaStream_t st) {
-  if (!g.fn) return cudaErrorInvalidConfiguration;
+  if (!g.fn && !g.jit) return cudaErrorInvalidConfiguration;
   cudaError_t e = cudaMemsetAsync(g.d_work, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
+  if (g.jit)
+    return jit_jobs_launch(*g.jit, g.grid, g.d_jobs, (uint32_t)g.jobs.size(), g.items,
+                           (uint32_t)g.chunk, g.d_work, b->d_err, b->d_failed, g.scratch, st);
   g.fn<<<g.grid, g.threads, g.smem, st>>>(g.d_jobs, (u32)g.jobs.size(), g.items, (u32)g.chunk,
                                           g.table_words, g.off_fan, g.off_vext, g.d_work, b->d_err,
                                           b->d_failed, g.scratch);
@@ -336,6 +366,72 @@ cudaError_t enqueue(ts_batch *b, cudaStream_t st) {
     if (e == cudaSuccess) e = cudaStreamWaitEvent(st, g.done, 0);
   }
   return e;
+}
+
+// Table-driven tile of a group at creation: global scratch from d = 7 with
+// 128-thread blocks, shared scratch below (64-thread blocks from d = 8).
+void table_defaults(ts_batch::Group &g) {
+  g.jit.reset();
+  g.global = g.d >= kGlobalScratchFrom;
+  g.threads = g.global ? 128 : (g.d >= 8 ? 64 : 128);
+  while (g.threads > 32 && !jobs_fn_dt(g.d, g.threads, g.global)) g.threads -= 32;
+  g.chunk = g.threads * 8;
+}
+
+// TS_KERNEL_AUTO at creation: specialised code for groups of at least
+// kJitGroupMin sign vectors up to degree kMaxBatchSpecialized, or when a
+// triangulation of the group asks for it; never when one asks for tables.
+bool wants_specialised(const ts_batch *b, const ts_batch::Group &g) {
+  bool table = false, forced = false;
+  uint64_t total = 0;
+  for (int j : g.jobs) {
+    table |= b->tris[j]->kernel == TS_KERNEL_TABLE;
+    forced |= b->tris[j]->kernel == TS_KERNEL_SPECIALIZED;
+    total += b->jobs[j].n;
+  }
+  return !table && (forced || (total >= kJitGroupMin && g.d <= kMaxBatchSpecialized));
+}
+
+// Build the specialised modules of the groups `gids` at once (one parallel
+// compile): every job gets the index of its triangulation's function (one
+// per distinct ts_tri of the group).  A group whose module cannot be built
+// gets the table-driven tile and the log.  Returns false if any failed.
+bool make_specialised(ts_batch *b, const std::vector<int> &gids) {
+  if (gids.empty()) return true;
+  std::vector<std::vector<const Diamond *>> want;
+  for (int gi : gids) {
+    auto &g = b->groups[gi];
+    std::map<const ts_tri *, uint32_t> fn;
+    std::vector<const Diamond *> dias;
+    for (int j : g.jobs) {
+      auto it = fn.find(b->tris[j]);
+      if (it == fn.end()) {
+        it = fn.emplace(b->tris[j], (uint32_t)dias.size()).first;
+        dias.push_back(&b->tris[j]->dia);
+      }
+      b->jobs[j].fn = it->second;
+    }
+    want.push_back(dias);
+  }
+  std::vector<std::shared_ptr<JitJobsModule>> mods;
+  std::vector<std::string> logs;
+  jit_jobs_build(want, &mods, &logs);
+  bool all = true;
+  for (size_t k = 0; k < gids.size(); ++k) {
+    auto &g = b->groups[gids[k]];
+    if (k < mods.size() && mods[k]) {
+      g.jit = mods[k];
+      g.jit_log.clear();
+      g.global = true;
+      g.threads = jit_jobs_threads();
+      g.chunk = g.threads * 16;
+    } else {
+      table_defaults(g);
+      g.jit_log = k < logs.size() && !logs[k].empty() ? logs[k] : "specialised batch kernel unavailable";
+      all = false;
+    }
+  }
+  return all;
 }
 
 }  // namespace
@@ -390,6 +486,7 @@ ts_status ts_batch_create(int njobs, ts_tri *const *tris, const uint64_t *counts
     x.hslots = b->jslots[j];
     b->jobs.push_back(x);
     b->degree.push_back(t->d);
+    b->tris.push_back(tris[j]);
     if (!gi.count(t->d)) {
       gi[t->d] = (int)b->groups.size();
       ts_batch::Group g;
@@ -397,13 +494,16 @@ ts_status ts_batch_create(int njobs, ts_tri *const *tris, const uint64_t *counts
       g.table_words = t->lay.words;
       g.off_fan = t->lay.off_fan;
       g.off_vext = t->lay.off_vext;
-      g.global = t->d >= kGlobalScratchFrom;
-      g.threads = g.global ? 128 : (t->d >= 8 ? 64 : 128);
-      while (g.threads > 32 && !jobs_fn_dt(t->d, g.threads, g.global)) g.threads -= 32;
-      g.chunk = g.threads * 8;
+      table_defaults(g);
       b->groups.push_back(g);
     }
     b->groups[gi[t->d]].jobs.push_back(j);
+  }
+  if (e == cudaSuccess) {
+    std::vector<int> spec;
+    for (size_t gi = 0; gi < b->groups.size(); ++gi)
+      if (wants_specialised(b, b->groups[gi])) spec.push_back((int)gi);
+    make_specialised(b, spec);
   }
   for (auto &g : b->groups) {
     if (e == cudaSuccess) e = cudaMalloc(&g.d_work, sizeof(unsigned long long));
@@ -444,8 +544,13 @@ ts_status ts_batch_set_tile(ts_batch *b, int d, int threads, int chunk, int scra
     return TS_EINVAL;
   for (auto &g : b->groups) {
     if (g.d != d) continue;
-    const bool global = scratch == TS_SCRATCH_AUTO ? d >= kGlobalScratchFrom : scratch == TS_SCRATCH_GLOBAL;
-    if (!jobs_fn_dt(d, threads, global)) return TS_EINVAL;  // block does not fit shared memory
+    bool global = scratch == TS_SCRATCH_AUTO ? d >= kGlobalScratchFrom : scratch == TS_SCRATCH_GLOBAL;
+    if (g.jit) {  // specialised: the block size and global scratch are fixed at compile time
+      if (threads != jit_jobs_threads() || scratch == TS_SCRATCH_SHARED) return TS_EINVAL;
+      global = true;
+    } else if (!jobs_fn_dt(d, threads, global)) {
+      return TS_EINVAL;  // block does not fit shared memory
+    }
     // runs already launched (graph launches included) read the job table and
     // the scratch that this call rewrites or frees: let them finish first
     cudaError_t e = cudaDeviceSynchronize();
@@ -460,6 +565,30 @@ ts_status ts_batch_set_tile(ts_batch *b, int d, int threads, int chunk, int scra
     e = upload_group(b, g);
     if (e == cudaSuccess) e = prepare_group(g);
     return cuda_st(e);
+  }
+  return TS_EINVAL;
+}
+
+ts_status ts_batch_set_kernel(ts_batch *b, int d, int kind) {
+  if (!b || kind < TS_KERNEL_AUTO || kind > TS_KERNEL_SPECIALIZED) return TS_EINVAL;
+  for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+    auto &g = b->groups[gi];
+    if (g.d != d) continue;
+    // runs already launched read the job table and scratch rewritten here
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_st(e);
+    if (b->exec) {
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
+    bool ok = true;
+    const bool spec = kind == TS_KERNEL_SPECIALIZED || (kind == TS_KERNEL_AUTO && wants_specialised(b, g));
+    if (!spec) table_defaults(g);
+    else if (!g.jit) ok = make_specialised(b, {(int)gi});
+    e = upload_group(b, g);
+    if (e == cudaSuccess) e = prepare_group(g);
+    if (e != cudaSuccess) return cuda_st(e);
+    return ok ? TS_OK : TS_ECUDA;
   }
   return TS_EINVAL;
 }
@@ -484,6 +613,25 @@ ts_status ts_batch_run(ts_batch *b, int use_graph, void *stream) {
     if (e != cudaSuccess) return cuda_st(e);
   }
   return cuda_st(cudaGraphLaunch(b->exec, st));
+}
+
+ts_status ts_batch_info(const ts_batch *b, int d, int *kernel, int *threads, int *chunk,
+                        int *scratch, char *log, size_t len) {
+  if (!b) return TS_EINVAL;
+  for (const auto &g : b->groups) {
+    if (g.d != d) continue;
+    if (kernel) *kernel = g.jit ? TS_KERNEL_SPECIALIZED : TS_KERNEL_TABLE;
+    if (threads) *threads = g.threads;
+    if (chunk) *chunk = g.chunk;
+    if (scratch) *scratch = g.global ? TS_SCRATCH_GLOBAL : TS_SCRATCH_SHARED;
+    if (log && len) {
+      const size_t n = std::min(len - 1, g.jit_log.size());
+      std::memcpy(log, g.jit_log.data(), n);
+      log[n] = 0;
+    }
+    return TS_OK;
+  }
+  return TS_EINVAL;
 }
 
 ts_status ts_batch_read(ts_batch *b, int job, uint64_t *codes, uint64_t *counts, uint64_t cap,

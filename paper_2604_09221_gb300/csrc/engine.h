@@ -17,6 +17,7 @@ namespace tcurve {
 constexpr int kMaxDegree = 16;     // |A| <= 153: three sign words, four code words
 constexpr int kMaxSpecialized = 9;  // triangulation-specialised kernels: one sign word
 constexpr int kGlobalScratchFrom = 7;  // TS_SCRATCH_AUTO: table kernels use global scratch from here
+constexpr int kMaxBatchSpecialized = 12;  // TS_KERNEL_AUTO: largest degree of specialised batch groups
 
 // Count words of multi-word histograms carry two flags in their top bits
 // (slot being written / key published); the count is the rest.
@@ -123,11 +124,34 @@ std::string jit_source(const Diamond &D, bool global = false, int min_blocks = 2
 void jit_config(int d, int scratch, int occupancy, bool *global, int *min_blocks);
 // Compile the generated source with NVRTC for sm_103a; returns the cubin (or
 // an empty string and the log in *log).
-std::string jit_compile_cubin(const std::string &src, std::string *log);
+std::string jit_compile_cubin(const std::string &src, std::string *log,
+                              const std::vector<std::string> &extra = {});
 cudaError_t jit_prepare(ts_tri *tri);  // compile + load once (thread-safe)
 cudaError_t launch_real_schemes_jit(ts_tri *tri, const uint64_t *signs, uint64_t n,
                                     uint64_t *codes, cudaStream_t stream);
 cudaError_t launch_enumerate_jit(ts_tri *tri, uint64_t lo, uint64_t hi, uint32_t flags,
                                  ts_hist *hist, cudaStream_t stream);
 void jit_release(ts_tri *tri);
+
+// Specialised kernels of batches (jit.cpp): per degree, one relocatable
+// object per distinct triangulation (its per-mask sweep as straight-line
+// code, exported as tcj_<i>) and one persistent kernel tcj_jobs that calls
+// them, compiled in parallel and linked with nvJitLink.
+struct JitJobsModule;
+std::string jit_job_source(const Diamond &D, int idx);
+std::string jit_jobs_kernel_source(int d, int nfn);
+// Compile and link without a device (the linked cubin, or empty and the log).
+std::string jit_jobs_link(const std::vector<const Diamond *> &tris, std::string *log);
+// Build the modules of several degree groups (each group: the diamonds of
+// its distinct triangulations, function i = group[i]) on the current device;
+// a group whose module cannot be built gets null and a log.
+cudaError_t jit_jobs_build(const std::vector<std::vector<const Diamond *>> &groups,
+                           std::vector<std::shared_ptr<JitJobsModule>> *mods,
+                           std::vector<std::string> *logs);
+int jit_jobs_threads();
+int jit_jobs_blocks_per_sm(const JitJobsModule &m);
+size_t jit_jobs_slab_bytes(const JitJobsModule &m);  // global scratch per block
+cudaError_t jit_jobs_launch(const JitJobsModule &m, unsigned grid, const void *jobs, uint32_t njobs,
+                            uint64_t items, uint32_t chunk, unsigned long long *work, uint32_t *err,
+                            unsigned long long *failed, uint32_t *scratch, cudaStream_t st);
 }  // namespace tcurve

@@ -453,6 +453,30 @@ ts_status ts_specialized_source(int d, const int32_t *edges_ij, int n_edges, int
   return st;
 }
 
+ts_status ts_batch_specialized_link(int d, int ntri, const int32_t *const *edges_ij,
+                                    const int *n_edges, size_t *linked_bytes, char *log, size_t len) {
+  if (d < 1 || ntri < 1 || !edges_ij || !n_edges || (len && !log)) return TS_EINVAL;
+  if (d > kMaxDegree) return TS_EUNSUPPORTED;
+  std::vector<Diamond> dias(ntri);
+  std::vector<const Diamond *> ptrs;
+  for (int i = 0; i < ntri; ++i) {
+    std::vector<std::array<Pt, 3>> tris;
+    if (n_edges[i] < 0 || (!edges_ij[i] && n_edges[i] > 0)) return TS_EINVAL;
+    if (!triangles_of(d, edges_ij[i], n_edges[i], tris) || !build_diamond(d, tris, dias[i]))
+      return TS_ENOTTRI;
+    ptrs.push_back(&dias[i]);
+  }
+  std::string lg;
+  const std::string cubin = jit_jobs_link(ptrs, &lg);
+  if (linked_bytes) *linked_bytes = cubin.size();
+  if (len) {
+    const size_t n = std::min(len - 1, lg.size());
+    std::memcpy(log, lg.data(), n);
+    log[n] = 0;
+  }
+  return cubin.empty() ? TS_ECUDA : TS_OK;
+}
+
 ts_status ts_sync(const ts_tri *t, void *stream) {
   if (!t) return TS_EINVAL;
   cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);

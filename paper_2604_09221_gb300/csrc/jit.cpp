@@ -13,12 +13,15 @@
 // is opened on first use).
 #include <cuda.h>
 #include <dlfcn.h>
+#include <nvJitLink.h>
 #include <nvrtc.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <map>
 #include <sstream>
+#include <thread>
 
 #include "engine.h"
 #include "tc_layout.h"
@@ -133,7 +136,8 @@ int sm_count_now() {
 
 }  // namespace
 
-std::string jit_compile_uncached(const std::string &src, std::string *log);
+std::string jit_compile_uncached(const std::string &src, std::string *log,
+                                 const std::vector<std::string> &extra);
 
 struct JitModule {
   CUmodule mod = nullptr;
@@ -349,29 +353,34 @@ std::string jit_source(const Diamond &D, bool global, int min_blocks) {
   return o.str();
 }
 
-std::string jit_compile_cubin(const std::string &src, std::string *log) {
+std::string jit_compile_cubin(const std::string &src, std::string *log,
+                              const std::vector<std::string> &extra) {
   // identical triangulations generate identical sources: compile once
   static std::mutex cache_mu;
-  static std::map<std::string, std::pair<std::string, std::string>> cache;  // src -> (cubin, log)
+  static std::map<std::string, std::pair<std::string, std::string>> cache;  // options + src -> (cubin, log)
+  std::string key;
+  for (const auto &x : extra) key += x + "\n";
+  key += src;
   {
     std::lock_guard<std::mutex> g(cache_mu);
-    auto it = cache.find(src);
+    auto it = cache.find(key);
     if (it != cache.end()) {
       if (log) *log = it->second.second;
       return it->second.first;
     }
   }
   std::string lg;
-  std::string out = jit_compile_uncached(src, &lg);
+  std::string out = jit_compile_uncached(src, &lg, extra);
   if (log) *log = lg;
   if (!out.empty()) {
     std::lock_guard<std::mutex> g(cache_mu);
-    cache.emplace(src, std::make_pair(out, lg));
+    cache.emplace(key, std::make_pair(out, lg));
   }
   return out;
 }
 
-std::string jit_compile_uncached(const std::string &src, std::string *log) {
+std::string jit_compile_uncached(const std::string &src, std::string *log,
+                                 const std::vector<std::string> &extra) {
   Nvrtc &nv = nvrtc();
   if (!nv.ok) {
     if (log) *log = "NVRTC library not found";
@@ -382,12 +391,14 @@ std::string jit_compile_uncached(const std::string &src, std::string *log) {
     if (log) *log = "nvrtcCreateProgram failed";
     return {};
   }
-  const char *opts[] = {"-arch=sm_103a", "--std=c++17", "-lineinfo", "--ptxas-options=-v"};
-  nvrtcResult r = nv.compile(prog, 4, opts);
+  std::vector<const char *> opts = {"-arch=sm_103a", "--std=c++17", "-lineinfo", "--ptxas-options=-v"};
+  for (const auto &x : extra) opts.push_back(x.c_str());
+  nvrtcResult r = nv.compile(prog, (int)opts.size(), opts.data());
   size_t ls = 0;
   nv.log_size(prog, &ls);
   std::string lg(ls, '\0');
   if (ls) nv.log(prog, &lg[0]);
+  while (!lg.empty() && lg.back() == '\0') lg.pop_back();  // the size counts the terminator
   if (log) *log = lg;
   std::string out;
   if (r == NVRTC_SUCCESS) {
@@ -565,6 +576,417 @@ cudaError_t launch_enumerate_jit(ts_tri *t, uint64_t lo, uint64_t hi, uint32_t f
       cudaSuccess)
     return e;
   if (b < hi && (e = enumerate_range(*m, h, b, hi, flags, st)) != cudaSuccess) return e;
+  return cudaSuccess;
+}
+
+
+// ---------------------------------------------------------------------------
+// Specialised code for batches of many triangulations (ts_batch).
+//
+// Every distinct triangulation of a batch gets its own relocatable object:
+// the per-mask sweep of Algorithm 1 as straight-line code (as tc_classify
+// above, for one to three sign words), the union pass and the narrow or wide
+// back end, all inside a namespace of its own and exported as one plain
+// device function tcj_<i>.  One more object per degree holds the persistent
+// kernel tcj_jobs, which pulls (job, chunk) work items, draws the splitmix64
+// sign vectors, calls the job's function through a switch on its index and
+// adds the codes to the job's histogram.  The objects are compiled by NVRTC
+// in parallel host threads and linked per degree with nvJitLink, so one
+// kernel per degree serves every job of that degree.
+
+namespace {
+
+constexpr int kJobThreads = 128;  // block size (the stride of the word-interleaved scratch)
+
+struct JitLink {
+  void *h = nullptr;
+  nvJitLinkResult (*create)(nvJitLinkHandle *, uint32_t, const char **) = nullptr;
+  nvJitLinkResult (*destroy)(nvJitLinkHandle *) = nullptr;
+  nvJitLinkResult (*add)(nvJitLinkHandle, nvJitLinkInputType, const void *, size_t,
+                         const char *) = nullptr;
+  nvJitLinkResult (*complete)(nvJitLinkHandle) = nullptr;
+  nvJitLinkResult (*cubin_size)(nvJitLinkHandle, size_t *) = nullptr;
+  nvJitLinkResult (*cubin)(nvJitLinkHandle, void *) = nullptr;
+  nvJitLinkResult (*log_size)(nvJitLinkHandle, size_t *) = nullptr;
+  nvJitLinkResult (*log)(nvJitLinkHandle, char *) = nullptr;
+  bool ok = false;
+};
+
+JitLink &jitlink() {
+  static JitLink j;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    const char *names[] = {"libnvJitLink.so.13", "libnvJitLink.so",
+                           "/usr/local/cuda/lib64/libnvJitLink.so.13",
+                           "/usr/local/cuda/lib64/libnvJitLink.so"};
+    for (const char *nm : names)
+      if ((j.h = dlopen(nm, RTLD_NOW | RTLD_GLOBAL))) break;
+    if (!j.h) return;
+    auto sym = [&](const char *versioned, const char *plain) {
+      void *f = dlsym(j.h, versioned);
+      return f ? f : dlsym(j.h, plain);
+    };
+    j.create = (decltype(j.create))sym("__nvJitLinkCreate_13_0", "nvJitLinkCreate");
+    j.destroy = (decltype(j.destroy))sym("__nvJitLinkDestroy_13_0", "nvJitLinkDestroy");
+    j.add = (decltype(j.add))sym("__nvJitLinkAddData_13_0", "nvJitLinkAddData");
+    j.complete = (decltype(j.complete))sym("__nvJitLinkComplete_13_0", "nvJitLinkComplete");
+    j.cubin_size =
+        (decltype(j.cubin_size))sym("__nvJitLinkGetLinkedCubinSize_13_0", "nvJitLinkGetLinkedCubinSize");
+    j.cubin = (decltype(j.cubin))sym("__nvJitLinkGetLinkedCubin_13_0", "nvJitLinkGetLinkedCubin");
+    j.log_size = (decltype(j.log_size))sym("__nvJitLinkGetErrorLogSize_13_0", "nvJitLinkGetErrorLogSize");
+    j.log = (decltype(j.log))sym("__nvJitLinkGetErrorLog_13_0", "nvJitLinkGetErrorLog");
+    j.ok = j.create && j.destroy && j.add && j.complete && j.cubin_size && j.cubin && j.log_size &&
+           j.log;
+  });
+  return j;
+}
+
+// Scratch layout of the batch kernels: one label per vertex (the wide back
+// end reuses that region), 128-thread blocks, global memory.
+Layout job_layout(int d) {
+  Layout L = tc_layout(d, true, kJobThreads);
+  L.threads = kJobThreads;
+  return L;
+}
+
+// Resident 128-thread blocks per SM the batch kernels of degree d are
+// compiled for (their register budget: 65536 / (128 x blocks) registers).
+int job_min_blocks(int d) { return d <= 7 ? 6 : d == 8 ? 5 : d <= 10 ? 4 : 3; }
+
+int job_max_registers(int d) {
+  const int r = 65536 / (kJobThreads * job_min_blocks(d));
+  return std::min(255, r / 8 * 8);
+}
+
+// Words of global scratch per block: the per-thread layout, then four u64
+// per thread (the slot where a batch function leaves its code words).
+size_t job_slab_words(const Layout &L) { return (size_t)L.words * L.threads + 8u * L.threads; }
+
+}  // namespace
+
+std::string jit_job_source(const Diamond &D, int idx) {
+  const Layout L = job_layout(D.d);
+  const int d = D.d, V = D.V;
+  if (L.sw > 3 || L.cw > 4) return std::string();
+  std::ostringstream o;
+  o << "// T-curve real-scheme function for one triangulation of " << d
+    << "*Delta_2 in a batch (generated, relocatable)\n";
+  o << "namespace tcj" << idx << " {\n";
+  emit_traits(o, L, d, V, true, job_min_blocks(d));
+  o << "#define TC_HEAVY_FN __forceinline__\n";
+  o << kRuntimeSrc;
+  o << "#define TC_BIT(k) ((((k) < 32 ? w0 : (k) < 64 ? w1 : (k) < 96 ? w2 : (k) < 128 ? w3 : "
+       "(k) < 160 ? w4 : w5) >> ((k) & 31)) & 1u)\n"
+    << "typedef TcScratch<TcK> TcS;\n\n";
+  o << "__device__ __forceinline__ void classify(u64 sg0, u64 sg1, u64 sg2, const TcS &S, u32 &err,\n"
+    << "                                         u64 *code) {\n"
+    << "  const u32 w0 = (u32)sg0, w1 = (u32)(sg0 >> 32), w2 = (u32)sg1, w3 = (u32)(sg1 >> 32),\n"
+    << "            w4 = (u32)sg2, w5 = (u32)(sg2 >> 32);\n"
+    << "  (void)w2; (void)w3; (void)w4; (void)w5;\n"
+    << "  u32 nl = 0, nb = 0, np = 0;\n  tc_clear_odd(S);\n";
+  VertexEmitter em(D, o);
+  const std::vector<char> flush = flush_schedule(D, 0, V, L.pcap);
+  for (int v = 0; v < V; ++v) em.emit(v, "  ", nullptr, flush[v] != 0);
+  o << "  tc_unions(S, np);\n";
+  if (L.wide)
+    o << "  tc_backend_wide(S, nl, nb, err, code);\n";
+  else
+    o << "  code[0] = tc_backend(S, nl, nb, err);\n";
+  o << "}\n}  // namespace tcj" << idx << "\n\n";
+  o << "extern \"C\" __device__ void tcj_" << idx
+    << "(unsigned long long sg0, unsigned long long sg1, unsigned long long sg2, unsigned int *scr,\n"
+    << "    unsigned int *gerr, unsigned long long *out) {\n"
+    << "  const tcj" << idx << "::TcS S{scr};\n"
+    << "  unsigned int err = 0;\n"
+    << "  unsigned long long code[tcj" << idx << "::TcK::CW];\n"
+    << "  tcj" << idx << "::classify(sg0, sg1, sg2, S, err, code);\n"
+    << "  if (err) atomicOr(gerr, err);\n"
+    << "#pragma unroll\n"
+    << "  for (unsigned w = 0; w < tcj" << idx << "::TcK::CW; ++w) out[w] = code[w];\n"
+    << "}\n";
+  return o.str();
+}
+
+std::string jit_jobs_kernel_source(int d, int nfn) {
+  const Layout L = job_layout(d);
+  std::ostringstream o;
+  o << "// T-curve batch kernel of degree " << d << " over " << nfn
+    << " specialised functions (generated, relocatable)\n";
+  o << "namespace tcjk {\n";
+  emit_traits(o, L, d, 2 * d * d + 2 * d + 1, true, job_min_blocks(d));
+  o << "#define TC_HEAVY_FN __forceinline__\n" << kRuntimeSrc << "}  // namespace tcjk\n\n";
+  for (int i = 0; i < nfn; ++i)
+    o << "extern \"C\" __device__ void tcj_" << i
+      << "(unsigned long long, unsigned long long, unsigned long long, unsigned int *, unsigned int *,"
+         " unsigned long long *);\n";
+  o << R"TCJOBS(
+// One job of the batch: the layout of the host's job table (72 bytes).
+struct TcjJob {
+  const unsigned *tab;
+  unsigned long long n, base;          // sign vectors; splitmix64 counter of the first
+  unsigned long long *codes;           // per-instance codes (or null)
+  unsigned long long *hkeys;           // the job's histogram
+  unsigned long long *hcnt;
+  unsigned long long hslots, chunk0;   // its slots; its first work item
+  unsigned fn, pad;                    // index of its specialised function
+};
+
+extern "C" __global__ void __launch_bounds__(tcjk::TcK::THREADS, tcjk::TcK::MINB)
+    tcj_jobs(const TcjJob *__restrict__ jobs, unsigned njobs, unsigned long long total_items,
+             unsigned chunk, unsigned long long *work, unsigned *err_word,
+             unsigned long long *failed_word, unsigned *gscr) {
+  typedef tcjk::TcK K;
+  typedef unsigned long long u64;
+  __shared__ u64 slot;
+  const unsigned lane = threadIdx.x & 31u;
+  unsigned *slab = gscr + (u64)blockIdx.x * (K::WORDS * K::THREADS + 8u * K::THREADS);
+  unsigned *scr = slab + threadIdx.x;
+  u64 *out = reinterpret_cast<u64 *>(slab + K::WORDS * K::THREADS) + 4u * threadIdx.x;
+  const u64 top = tcjk::tc_top_mask(K::NPOINTS, K::W);
+  u64 failed = 0;
+  for (;;) {
+    if (threadIdx.x == 0) slot = atomicAdd(work, 1ull);
+    __syncthreads();
+    const u64 c = slot;
+    __syncthreads();
+    if (c >= total_items) break;
+    unsigned lo = 0, hi = njobs;  // the job holding item c: last j with chunk0 <= c
+    while (hi - lo > 1) {
+      const unsigned mid = (lo + hi) / 2;
+      if (jobs[mid].chunk0 <= c) lo = mid; else hi = mid;
+    }
+    const TcjJob J = jobs[lo];
+    const u64 first = (c - J.chunk0) * (u64)chunk;
+    for (unsigned k = 0; k < chunk; k += K::THREADS) {
+      const u64 idx = first + k + threadIdx.x;
+      u64 key[K::CW];
+#pragma unroll
+      for (unsigned w = 0; w < K::CW; ++w) key[w] = 0;
+      if (idx < J.n) {
+        // the sign vector of counter base + idx, as ts_splitmix_masks writes it
+        u64 s[3] = {0, 0, 0};
+#pragma unroll
+        for (unsigned w = 0; w < K::W; ++w) s[w] = tcjk::tc_splitmix64((J.base + idx) * K::W + w);
+        s[K::W - 1] &= top;
+        switch (J.fn) {
+)TCJOBS";
+  for (int i = 0; i < nfn; ++i)
+    o << "          case " << i << "u: tcj_" << i << "(s[0], s[1], s[2], scr, err_word, out); break;\n";
+  o << R"TCJOBS(          default:
+#pragma unroll
+            for (unsigned w = 0; w < K::CW; ++w) out[w] = 0;
+            atomicOr(err_word, tcjk::TC_ERR_INTERNAL);
+        }
+        u64 any = 0;
+#pragma unroll
+        for (unsigned w = 0; w < K::CW; ++w) {
+          key[w] = out[w];
+          any |= key[w];
+          if (J.codes) J.codes[idx * K::CW + w] = key[w];
+        }
+        failed += any == 0;
+      }
+      if (K::CW == 1) {
+        const unsigned peers = __match_any_sync(0xffffffffu, key[0]);
+        if (key[0] != 0 && lane == (unsigned)(__ffs(peers) - 1))
+          tcjk::tc_global_add(J.hkeys, J.hcnt, J.hslots, err_word, key[0], (u64)__popc(peers));
+      } else {
+        tcjk::tc_hist_add_wide<K::CW>(key, J.hkeys, J.hcnt, J.hslots, err_word);
+      }
+    }
+  }
+  if (failed) atomicAdd(failed_word, failed);
+}
+)TCJOBS";
+  return o.str();
+}
+
+struct JitJobsModule {
+  CUmodule mod = nullptr;
+  CUfunction fn = nullptr;
+  int d = 0, bpsm = 0;
+  size_t slab_words = 0;
+  ~JitJobsModule() {
+    if (mod && driver().ok) driver().unload(mod);
+  }
+};
+
+namespace {
+
+// Compile the sources in parallel host threads (NVRTC is thread-safe);
+// returns false and the first failure's log if any source fails, else true
+// and the compiler logs (ptxas resource lines) of all objects.
+bool compile_parallel(const std::vector<std::string> &srcs,
+                      const std::vector<std::vector<std::string>> &opts,
+                      std::vector<std::string> &cubins, std::string *log) {
+  cubins.assign(srcs.size(), std::string());
+  std::vector<std::string> logs(srcs.size());
+  std::atomic<size_t> next{0};
+  auto work = [&] {
+    for (size_t i; (i = next.fetch_add(1)) < srcs.size();)
+      cubins[i] = jit_compile_cubin(srcs[i], &logs[i], opts[i]);
+  };
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const size_t nth = std::min<size_t>(hw, srcs.size());
+  std::vector<std::thread> pool;
+  for (size_t t = 1; t < nth; ++t) pool.emplace_back(work);
+  work();
+  for (auto &t : pool) t.join();
+  for (size_t i = 0; i < srcs.size(); ++i)
+    if (cubins[i].empty()) {
+      if (log) *log = "compile of batch object " + std::to_string(i) + " failed:\n" + logs[i];
+      return false;
+    }
+  if (log) {
+    log->clear();
+    for (size_t i = 0; i < srcs.size(); ++i) *log += "object " + std::to_string(i) + ":\n" + logs[i];
+  }
+  return true;
+}
+
+// Link relocatable cubins into one cubin for sm_103a.
+std::string link_cubins(const std::vector<const std::string *> &objs, std::string *log) {
+  JitLink &jl = jitlink();
+  if (!jl.ok) {
+    if (log) *log = "nvJitLink library not found";
+    return {};
+  }
+  nvJitLinkHandle h = nullptr;
+  const char *opts[] = {"-arch=sm_103a"};
+  if (jl.create(&h, 1, opts) != NVJITLINK_SUCCESS) {
+    if (log) *log = "nvJitLinkCreate failed";
+    return {};
+  }
+  bool ok = true;
+  for (size_t i = 0; i < objs.size() && ok; ++i) {
+    const std::string name = "tcj" + std::to_string(i);
+    ok = jl.add(h, NVJITLINK_INPUT_CUBIN, objs[i]->data(), objs[i]->size(), name.c_str()) ==
+         NVJITLINK_SUCCESS;
+  }
+  if (ok) ok = jl.complete(h) == NVJITLINK_SUCCESS;
+  std::string out;
+  if (ok) {
+    size_t n = 0;
+    ok = jl.cubin_size(h, &n) == NVJITLINK_SUCCESS;
+    if (ok) {
+      out.resize(n);
+      ok = jl.cubin(h, &out[0]) == NVJITLINK_SUCCESS;
+    }
+  }
+  if (!ok) {
+    size_t n = 0;
+    std::string lg;
+    if (jl.log_size(h, &n) == NVJITLINK_SUCCESS && n) {
+      lg.resize(n);
+      jl.log(h, &lg[0]);
+    }
+    if (log) *log = "nvJitLink failed:\n" + lg;
+    out.clear();
+  }
+  jl.destroy(&h);
+  return out;
+}
+
+}  // namespace
+
+std::string jit_jobs_link(const std::vector<const Diamond *> &tris, std::string *log) {
+  if (tris.empty()) return {};
+  const int d = tris[0]->d;
+  std::vector<std::string> srcs;
+  std::vector<std::vector<std::string>> opts;
+  const std::vector<std::string> o = {"-rdc=true", "-maxrregcount=" + std::to_string(job_max_registers(d))};
+  for (size_t i = 0; i < tris.size(); ++i) {
+    srcs.push_back(jit_job_source(*tris[i], (int)i));
+    if (srcs.back().empty()) {
+      if (log) *log = "no batch source for this degree";
+      return {};
+    }
+    opts.push_back(o);
+  }
+  srcs.push_back(jit_jobs_kernel_source(d, (int)tris.size()));
+  opts.push_back(o);
+  std::vector<std::string> cubins;
+  std::string clog;
+  if (!compile_parallel(srcs, opts, cubins, &clog)) {
+    if (log) *log = clog;
+    return {};
+  }
+  std::vector<const std::string *> objs;
+  for (auto &c : cubins) objs.push_back(&c);
+  std::string llog;
+  std::string out = link_cubins(objs, &llog);
+  if (log) *log = out.empty() ? llog : clog;
+  return out;
+}
+
+cudaError_t jit_jobs_build(const std::vector<std::vector<const Diamond *>> &groups,
+                           std::vector<std::shared_ptr<JitJobsModule>> *mods,
+                           std::vector<std::string> *logs) {
+  mods->assign(groups.size(), nullptr);
+  logs->assign(groups.size(), std::string());
+  Driver &dr = driver();
+  if (!dr.ok) return cudaErrorNotSupported;
+  cudaError_t e = cudaFree(0);  // make the primary context current
+  if (e != cudaSuccess) return e;
+  // every object of every group in one parallel compile, then one link per group
+  std::vector<std::string> srcs;
+  std::vector<std::vector<std::string>> opts;
+  std::vector<size_t> first(groups.size() + 1, 0);
+  for (size_t g = 0; g < groups.size(); ++g) {
+    first[g] = srcs.size();
+    if (groups[g].empty()) continue;
+    const int d = groups[g][0]->d;
+    const std::vector<std::string> o = {"-rdc=true",
+                                        "-maxrregcount=" + std::to_string(job_max_registers(d))};
+    for (size_t i = 0; i < groups[g].size(); ++i) {
+      srcs.push_back(jit_job_source(*groups[g][i], (int)i));
+      opts.push_back(o);
+    }
+    srcs.push_back(jit_jobs_kernel_source(d, (int)groups[g].size()));
+    opts.push_back(o);
+  }
+  first[groups.size()] = srcs.size();
+  for (const auto &src : srcs)
+    if (src.empty()) return cudaErrorNotSupported;
+  std::vector<std::string> cubins(srcs.size());
+  std::string lg;
+  if (!compile_parallel(srcs, opts, cubins, &lg)) {
+    for (auto &l : *logs) l = lg;
+    return cudaErrorInvalidSource;
+  }
+  lg.clear();
+  for (size_t g = 0; g < groups.size(); ++g) {
+    if (groups[g].empty()) continue;
+    std::vector<const std::string *> objs;
+    for (size_t i = first[g]; i < first[g + 1]; ++i) objs.push_back(&cubins[i]);
+    const std::string linked = link_cubins(objs, &(*logs)[g]);
+    if (linked.empty()) continue;
+    auto m = std::make_shared<JitJobsModule>();
+    m->d = groups[g][0]->d;
+    m->slab_words = job_slab_words(job_layout(m->d));
+    if (dr.load(&m->mod, linked.data()) != CUDA_SUCCESS ||
+        dr.get(&m->fn, m->mod, "tcj_jobs") != CUDA_SUCCESS ||
+        dr.occupancy(&m->bpsm, m->fn, kJobThreads, 0) != CUDA_SUCCESS || m->bpsm < 1) {
+      (*logs)[g] = "loading the linked batch module failed";
+      continue;
+    }
+    (*mods)[g] = m;
+  }
+  return cudaSuccess;
+}
+
+int jit_jobs_threads() { return kJobThreads; }
+int jit_jobs_blocks_per_sm(const JitJobsModule &m) { return m.bpsm; }
+size_t jit_jobs_slab_bytes(const JitJobsModule &m) { return m.slab_words * 4; }
+
+cudaError_t jit_jobs_launch(const JitJobsModule &m, unsigned grid, const void *jobs, uint32_t njobs,
+                            uint64_t items, uint32_t chunk, unsigned long long *work, uint32_t *err,
+                            unsigned long long *failed, uint32_t *scratch, cudaStream_t st) {
+  void *args[] = {(void *)&jobs, (void *)&njobs, (void *)&items, (void *)&chunk,
+                  (void *)&work, (void *)&err,   (void *)&failed, (void *)&scratch};
+  if (driver().launch(m.fn, grid, 1, 1, kJobThreads, 1, 1, 0, (CUstream)st, args, nullptr) !=
+      CUDA_SUCCESS)
+    return cudaErrorLaunchFailure;
   return cudaSuccess;
 }
 

@@ -115,6 +115,25 @@ def test_specialized_kernels_compile_for_sm103a(eng, d):
     assert max(spills.values()) <= 256, spills
 
 
+@pytest.mark.parametrize("d", [1, 4, 7, 10, 11, 16])
+def test_specialized_batch_code_compiles_and_links(eng, d):
+    """The specialised batch code (one relocatable object per triangulation,
+    the degree's persistent kernel, linked with nvJitLink) builds for
+    sm_103a on the host: one to three sign words, one to four code words,
+    narrow and wide back ends.  Every object of the log reports its
+    resources; a broken edge list is refused before compiling."""
+    e = [ti.regular_triangulation(d, seed=d)] if d > 2 else [ti.standard_triangulation(d)]
+    if d in (7, 10):
+        e.append(ti.regular_triangulation(d, seed=d + 100))
+    size, log = eng.batch_specialized_link(d, e, with_log=True)
+    assert size > 0
+    assert log.count("object ") == len(e) + 1
+    bad = np.asarray(e[0]).reshape(-1, 4)[1:]
+    with pytest.raises(eng.TSError) as err:
+        eng.batch_specialized_link(d, [bad])
+    assert err.value.status == 2
+
+
 @pytest.mark.parametrize("d", [2, 4, 6, 7, 8, 9])
 def test_diamond_tables_match_the_table_1_sizes(eng, d):
     """The tables of T^diamond built on the host (read from the generated

@@ -1,7 +1,8 @@
 """Host logic of the tile autotuner (paper_2604_09221_gb300.autotune) with a
 fake batch and fake timings (no GPU): the fastest tile wins, tiles the
-library refuses are skipped, each degree is tuned on its own jobs only, and
-cached choices are reused without timing."""
+library refuses are skipped, each degree is tuned on its own jobs only, a
+specialised group is tuned over its chunk alone, and cached choices are
+reused without timing."""
 import json
 
 import pytest
@@ -17,8 +18,11 @@ class FakeTri:
 
 class FakeBatch:
     """Records what the tuner asks of a batch; tiles with more than 192
-    threads at global scratch are refused like a tile that does not fit."""
+    threads at global scratch are refused like a tile that does not fit.
+    Degrees in ``specialized`` report specialised code (128 threads, global
+    scratch fixed)."""
     made = []
+    specialized = set()
 
     def __init__(self, tris, counts, bases):
         self.tris, self.counts, self.bases = list(tris), list(counts), list(bases)
@@ -27,8 +31,16 @@ class FakeBatch:
         self.tiles = {}
         FakeBatch.made.append(self)
 
+    def info(self, d):
+        if d in FakeBatch.specialized:
+            return {"kernel": "specialized", "threads": 128, "chunk": 2048, "scratch": "global",
+                    "log": ""}
+        return {"kernel": "table", "threads": 64, "chunk": 512, "scratch": "shared", "log": ""}
+
     def set_tile(self, d, threads, chunk, scratch=0):
         if scratch == autotune.GLOBAL and threads > 192:
+            raise eng.TSError(1, "ts_batch_set_tile")
+        if d in FakeBatch.specialized and (threads != 128 or scratch == autotune.SHARED):
             raise eng.TSError(1, "ts_batch_set_tile")
         self.tile = (threads, chunk, scratch)
         self.tiles[d] = self.tile
@@ -50,6 +62,7 @@ def fake_ms(batch, reps):
 @pytest.fixture
 def fakes(monkeypatch):
     FakeBatch.made = []
+    FakeBatch.specialized = set()
     timed = []
 
     def timer(batch, reps):
@@ -89,12 +102,24 @@ def test_autotune_tunes_degrees_apart_and_reuses_the_cache(fakes, tmp_path):
     assert subs[5].counts == [10, 30] and subs[5].bases == [1, 3]
     assert subs[10].counts == [20, 40, 50] and subs[10].bases == [2, 4, 5]
     store = json.load(open(cache))
-    assert set(store) == {"FakeGPU|d=5|tile3", "FakeGPU|d=10|tile3"}
-    # a second run takes every tile from the cache without timing
+    assert set(store) == {"FakeGPU|d=5|table|tile3", "FakeGPU|d=10|table|tile3"}
+    # a second run takes every tile from the cache without timing (it still
+    # makes the sub-batches, whose kernel family is part of the key)
     fakes.clear()
     FakeBatch.made = []
     assert autotune.autotune(tris, counts, bases, cache=cache) == tiles
-    assert fakes == [] and FakeBatch.made == []
+    assert fakes == [] and len(FakeBatch.made) == 2
+
+
+def test_specialised_groups_tune_the_chunk_only(fakes, tmp_path):
+    FakeBatch.specialized = {10}
+    t, c, s, _ = autotune.tune_degree([FakeTri(10)] * 2, [100, 200], [0, 1])
+    assert (t, c, s) == (128, 128 * 16, autotune.GLOBAL)
+    assert fakes == [(128, 128 * k, autotune.GLOBAL) for k in autotune.CHUNK_PER_THREAD]
+    cache = str(tmp_path / "tiles.json")
+    autotune.autotune([FakeTri(5), FakeTri(10)], [1, 2], [0, 0], cache=cache)
+    assert set(json.load(open(cache))) == {"FakeGPU|d=5|table|tile3",
+                                           "FakeGPU|d=10|specialized|tile3"}
 
 
 def test_apply_sets_only_the_degrees_of_the_batch():

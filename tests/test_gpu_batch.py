@@ -109,7 +109,8 @@ def test_autotuner_picks_tiles_that_run(eng, jobs, tmp_path):
 def test_mixed_batch_full_size(eng, orc):
     """The mixed-degree batch workload at its full size: 32 seeded regular
     triangulations for each d in 5..10, 2^U(10,24) splitmix64 sign vectors
-    per triangulation (about 3.3e8 in all), one graph launch.  Every job's
+    per triangulation (about 3.3e8 in all), one graph launch, every degree
+    group on specialised code.  Every job's
     histogram accounts for all its sign vectors, none failed, and every
     scheme satisfies the classical restrictions; one job per degree also
     stores its codes, and 1024 sampled rows of each equal the oracle's codes
@@ -129,6 +130,8 @@ def test_mixed_batch_full_size(eng, orc):
     outs = [torch.zeros((counts[j], tris[j].code_words), dtype=torch.int64, device="cuda")
             if j in sampled else None for j in range(len(tris))]
     batch = eng.Batch(tris, counts, bases, code_outputs=outs)
+    for d in degrees:   # every group is large enough for specialised code
+        assert batch.info(d)["kernel"] == "specialized", batch.info(d)["log"][-2000:]
     batch.run(graph=True)
     torch.cuda.synchronize()
     checked = set()
@@ -147,3 +150,95 @@ def test_mixed_batch_full_size(eng, orc):
         want = orc.real_schemes(d, orc.triangles(d, edges[j]), signs)
         got = outs[j].cpu().numpy().view(np.uint64)[idx]
         assert (got == want).all(), (d, j)
+
+
+def specialised_jobs(eng, degrees, seed, max_n):
+    """Two triangulations per degree and three jobs per degree: the first
+    triangulation twice (one ts_tri in two jobs), the second once."""
+    rng = np.random.default_rng(seed)
+    jobs = []
+    for d in degrees:
+        es = ti.regular_triangulations(d, 2, seed=seed + d)
+        ts = [eng.Triangulation(d, e) for e in es]
+        for k, i in enumerate((0, 1, 0)):
+            jobs.append({"d": d, "edges": es[i], "tri": ts[i], "n": int(rng.integers(1, max_n)),
+                         "base": job_base(seed * 10 + d, k)})
+    return jobs
+
+
+def test_specialised_batch_matches_oracle(eng, orc):
+    """Specialised batch groups (each triangulation compiled into a
+    straight-line sweep of its own, linked with the group's persistent
+    kernel) for degrees 3..12: one and two sign and code words, narrow and
+    wide back ends, ragged counts, codes stored for every other job.  Every
+    job's histogram and stored codes equal the oracle's on the same
+    splitmix64 sign vectors, in one graph launch, on replay, after a chunk
+    change, and after a switch to the table-driven kernel and back; a tile
+    of another block size is refused."""
+    import torch
+    degrees = (3, 5, 6, 7, 8, 9, 10, 11, 12)
+    jobs = specialised_jobs(eng, degrees, 700, 6000)
+    tris = [j["tri"] for j in jobs]
+    outs = [torch.zeros((j["n"], j["tri"].code_words), dtype=torch.int64, device="cuda")
+            if i % 2 == 0 else None for i, j in enumerate(jobs)]
+    batch = eng.Batch(tris, [j["n"] for j in jobs], [j["base"] for j in jobs], code_outputs=outs)
+    for d in degrees:
+        batch.set_kernel(d, eng.TS_KERNEL_SPECIALIZED)
+        info = batch.info(d)
+        assert info["kernel"] == "specialized" and info["threads"] == 128, info["log"][-2000:]
+    batch.run(graph=True)
+    got = []
+    for i, j in enumerate(jobs):
+        codes, cnt, failed = batch.read(i)
+        assert failed == 0
+        h = collections.Counter({eng.code_to_int(c): int(k)
+                                 for c, k in zip(codes.reshape(len(cnt), -1), cnt)})
+        want = orc.real_schemes(j["d"], orc.triangles(j["d"], j["edges"]),
+                                ti.splitmix_sign_vectors(j["d"], j["base"], j["n"]))
+        assert h == collections.Counter(orc.code_to_int(w) for w in want), (i, j["d"])
+        if outs[i] is not None:
+            assert (outs[i].cpu().numpy().view(np.uint64) == want).all(), (i, j["d"])
+        got.append(h)
+
+    def hists():
+        out = []
+        for i in range(len(jobs)):
+            codes, cnt, failed = batch.read(i)
+            assert failed == 0
+            out.append(collections.Counter({eng.code_to_int(c): int(k)
+                                            for c, k in zip(codes.reshape(len(cnt), -1), cnt)}))
+        return out
+    batch.run(graph=True)
+    assert hists() == got
+    batch.set_tile(10, 128, 128 * 2, eng.TS_SCRATCH_GLOBAL)
+    batch.run(graph=True)
+    assert hists() == got
+    with pytest.raises(eng.TSError):
+        batch.set_tile(10, 64, 64 * 16, eng.TS_SCRATCH_GLOBAL)
+    batch.set_kernel(7, eng.TS_KERNEL_TABLE)
+    assert batch.info(7)["kernel"] == "table"
+    batch.run(graph=False)
+    assert hists() == got
+    batch.set_kernel(7, eng.TS_KERNEL_SPECIALIZED)
+    batch.run(graph=True)
+    assert hists() == got
+
+
+def test_specialised_batch_by_size(eng):
+    """TS_KERNEL_AUTO at creation: a degree group of at least 2^22 sign
+    vectors runs specialised code, a smaller one the table-driven kernel, and
+    a group with a triangulation set to TS_KERNEL_TABLE stays table-driven;
+    the large groups count all their sign vectors."""
+    t9 = [eng.Triangulation(9, e) for e in ti.regular_triangulations(9, 2, seed=909)]
+    t6 = eng.Triangulation(6, ti.regular_triangulation(6, seed=606))
+    t8 = eng.Triangulation(8, ti.regular_triangulation(8, seed=808))
+    t8.set_kernel(eng.TS_KERNEL_TABLE)
+    counts = [1 << 21, 1 << 21, 5000, 1 << 23]
+    batch = eng.Batch(t9 + [t6, t8], counts, [1, 2, 3, 4])
+    assert batch.info(9)["kernel"] == "specialized", batch.info(9)["log"][-2000:]
+    assert batch.info(6)["kernel"] == "table"
+    assert batch.info(8)["kernel"] == "table"
+    batch.run()
+    for j, n in enumerate(counts):
+        codes, cnt, failed = batch.read(j)
+        assert failed == 0 and int(cnt.sum()) == n
