@@ -198,6 +198,7 @@ def main():
     ap.add_argument("--trips", type=int, default=1 << 15)
     ap.add_argument("--no-stretch", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--families", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -508,10 +509,14 @@ def job_base(seed, stream):
 
 
 def serving_run(seconds, degrees=tuple(range(6, 17)), per_degree=4, slots=8, seed=2027):
-    """Poisson stream of jobs on the continuous-batching server: d uniform in
-    `degrees`, 2^U(8,22) sign vectors per job (splitmix64 streams), resident
-    triangulations (table-driven kernels, nothing compiled) and histograms.
-    The arrival rate is 70 % of the capacity measured on a closed burst."""
+    """Poisson stream of jobs on the continuous-batching server, d uniform in
+    `degrees` over resident triangulations (table-driven kernels, nothing
+    compiled) and histograms.  Job kinds: half are sampled jobs (2^U(8,22)
+    splitmix64 sign vectors, one in eight also returning codes), a quarter
+    query jobs (2^U(8,18) caller sign vectors from host memory, codes back),
+    a quarter exhaustive enumeration ranges (2^U(8,22) masks, flags 0,
+    TS_ENUM_FLIP or TS_ENUM_REDUCED).  The arrival rate is 70 % of the
+    capacity measured on a closed burst.  Latency percentiles per kind."""
     import numpy as np
     import torch
 
@@ -522,14 +527,24 @@ def serving_run(seconds, degrees=tuple(range(6, 17)), per_degree=4, slots=8, see
             for e in ti.regular_triangulations(d, per_degree, seed=seed + d)]
     ex = GpuExecutor(tris, slots=slots, kernel=eng.TS_KERNEL_TABLE)
     rng = np.random.default_rng(seed)
+    flag_set = (0, eng.TS_ENUM_FLIP, eng.TS_ENUM_REDUCED)
 
     def draw():
-        return Job(tri=int(rng.integers(0, len(tris))), n=int(2 ** rng.uniform(8, 22)),
-                   base=int(rng.integers(0, 1 << 62)))
+        t = int(rng.integers(0, len(tris)))
+        u = rng.uniform()
+        if u < 0.5:
+            return Job(tri=t, n=int(2 ** rng.uniform(8, 22)), base=int(rng.integers(0, 1 << 62)),
+                       want_codes=bool(rng.uniform() < 0.125))
+        if u < 0.75:
+            n = int(2 ** rng.uniform(8, 18))
+            return Job(tri=t, kind="query",
+                       signs=ti.random_masks(n, tris[t].d, int(rng.integers(0, 1 << 30))))
+        lo = int(rng.integers(0, 1 << 24))
+        return Job(tri=t, kind="enum", lo=lo, hi=lo + int(2 ** rng.uniform(8, 22)),
+                   flags=flag_set[int(rng.integers(0, 3))])
 
     srv = Server(ex, slots=slots, mem_budget=1 << 32)
-    warm = [draw() for _ in range(2 * slots)]
-    for f in [srv.submit(j) for j in warm]:
+    for f in [srv.submit(draw()) for _ in range(2 * slots)]:
         f.result()
     burst = [draw() for _ in range(64)]
     t0 = time.perf_counter()
@@ -556,12 +571,18 @@ def serving_run(seconds, degrees=tuple(range(6, 17)), per_degree=4, slots=8, see
     torch.cuda.synchronize()
     lat = [r.latency * 1e3 for r in res]
     inst = sum(j.n for j in jobs)
+    kinds = {}
+    for k in ("sample", "query", "enum"):
+        lk = [r.latency * 1e3 for r in res if r.kind == k]
+        kinds[k] = {"jobs": len(lk), "p50_ms": percentile(lk, 50), "p99_ms": percentile(lk, 99),
+                    "schemes": sum(j.n for j in jobs if j.kind == k)}
     return {"jobs": len(jobs), "arrival_rate_jobs_per_s": rate, "capacity_jobs_per_s": cap_jobs,
-            "p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99),
+            "p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99), "kinds": kinds,
             "mean_queue_ms": 1e3 * sum(r.queued for r in res) / len(res),
             "schemes_per_s": inst / wall, "slots": slots, "degrees": list(degrees),
-            "sign_vectors_per_job": "2^U(8,22)",
+            "sign_vectors_per_job": "sample 2^U(8,22), query 2^U(8,18), enum 2^U(8,22)",
             "kernel": "table-driven (resident, uncompiled; global scratch from d = 7)",
+            "resident_mb": srv.resident / 2 ** 20, "requeued": len(srv.requeued),
             "peak_running": srv.peak_running, "seconds": wall}
 
 
@@ -646,6 +667,45 @@ def mixed_run(steps, warmup, degrees=(5, 6, 7, 8, 9, 10), per_degree=32, seed=31
             "gpu_launches_per_step": len(degrees)}
 
 
+def mixed_families(reps=3, degrees=(5, 6, 7, 8, 9, 10), per_degree=32, seed=31):
+    """Each degree group of the mixed batch alone, table-driven and
+    specialised (default tiles): schemes/s and the launch's resources."""
+    import numpy as np
+    import torch
+
+    import paper_2604_09221_gb300 as eng
+    import tcurve_inputs as ti
+    rng = np.random.default_rng(seed)
+    out = {}
+    for d in degrees:
+        tris, counts, bases = [], [], []
+        for k, e in enumerate(ti.regular_triangulations(d, per_degree, seed=seed + d)):
+            tris.append(eng.Triangulation(d, e))
+            counts.append(int(2 ** rng.uniform(10, 24)))
+            bases.append(job_base(seed * 100 + d, k))
+        batch = eng.Batch(tris, counts, bases)
+        row = {}
+        for fam in (eng.TS_KERNEL_TABLE, eng.TS_KERNEL_SPECIALIZED):
+            batch.set_kernel(d, fam)
+            batch.run(graph=False)
+            torch.cuda.synchronize()
+            best = float("inf")
+            for _ in range(reps):
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record()
+                batch.run(graph=False)
+                b.record()
+                b.synchronize()
+                best = min(best, a.elapsed_time(b))
+            info = batch.info(d)
+            info.pop("log")
+            row[info["kernel"]] = dict(info, schemes_per_s=sum(counts) / (best / 1e3), ms=best)
+        out[str(d)] = row
+        batch.close()
+    return out
+
+
 def mixed_workload(args):
     """The mixed-degree batch as one CUDA-graph launch per step (its own line)."""
     import torch
@@ -654,6 +714,9 @@ def mixed_workload(args):
     torch.cuda.set_device(0)
     _b.build()
     import paper_2604_09221_gb300 as eng
+    if args.families:
+        print(json.dumps({"mixed_families": mixed_families()}), flush=True)
+        return 0
     peak = measure_int_peak(eng, args.trips)
     r = mixed_run(args.steps, args.warmup)
     line = {"metric": "mixed-degree batch: schemes/s (one CUDA graph launch per step)",

@@ -240,25 +240,32 @@ ts_status ts_batch_set_tile(ts_batch *batch, int d, int threads, int chunk, int 
  * into a CUDA graph on the first call (and after a tile change) and the graph
  * is launched; otherwise the same work is enqueued directly. */
 ts_status ts_batch_run(ts_batch *batch, int use_graph, void *stream);
-/* Kernel family and tile of the degree-d group of a batch (an engine
- * facility).  A group runs the table-driven kernel (TS_KERNEL_TABLE) or
- * specialised code (TS_KERNEL_SPECIALIZED): every distinct triangulation of
- * the group compiled into a straight-line sweep of its own (one relocatable
- * object each, compiled with NVRTC in parallel host threads at
- * ts_batch_create) and linked with the group's persistent kernel (nvJitLink),
- * which calls each job's sweep.  A group is specialised when one of its
+/* Kernel family, tile and launch resources of the degree-d group of a batch
+ * (an engine facility).  A group runs the table-driven kernel
+ * (TS_KERNEL_TABLE) or specialised code (TS_KERNEL_SPECIALIZED): every
+ * distinct triangulation of the group compiled into a straight-line sweep of
+ * its own (one relocatable object each, compiled with NVRTC in parallel host
+ * threads) and linked with the group's persistent kernel (nvJitLink), which
+ * calls each job's sweep.  A group is specialised at creation when one of its
  * triangulations was set to TS_KERNEL_SPECIALIZED, or, with TS_KERNEL_AUTO,
- * when d <= 12 and the group holds at least 2^22 sign vectors; never when
+ * when d <= 6 and the group holds at least 2^22 sign vectors; never when
  * one of them was set to TS_KERNEL_TABLE, and not if the code cannot be
- * built (log then says why).  Specialised groups have 128-thread blocks and
- * global scratch (ts_batch_set_tile accepts only those; the chunk may vary).
- *   kernel, threads, chunk, scratch (each may be NULL) receive the group's
- *   TS_KERNEL_*, threads per block, sign vectors per work item, TS_SCRATCH_*
- *   log (may be NULL; len bytes with the NUL) the reason a specialised
- *   group fell back to the table-driven kernel, or ""
+ * built (log then says why); ts_batch_set_kernel changes it later.
+ * Specialised groups have 128-thread blocks and global scratch
+ * (ts_batch_set_tile accepts only those; the chunk may vary).
+ *   info  receives kernel (TS_KERNEL_*), threads per block, chunk (sign
+ *         vectors per work item), scratch (TS_SCRATCH_*), registers per
+ *         thread, local_bytes (per-thread local memory: spills, call
+ *         frames), blocks_per_sm (resident blocks of the launch) and grid
+ *   log   (may be NULL; len bytes with the NUL) the reason a specialised
+ *         group fell back to the table-driven kernel, or ""
  * TS_EINVAL if the batch has no job of degree d. */
-ts_status ts_batch_info(const ts_batch *batch, int d, int *kernel, int *threads, int *chunk,
-                        int *scratch, char *log, size_t len);
+typedef struct ts_batch_group_info {
+  int kernel, threads, chunk, scratch;
+  int registers, local_bytes, blocks_per_sm, grid;
+} ts_batch_group_info;
+ts_status ts_batch_info(const ts_batch *batch, int d, ts_batch_group_info *info, char *log,
+                        size_t len);
 /* Kernel family of the degree-d group: TS_KERNEL_TABLE, TS_KERNEL_SPECIALIZED
  * (builds the group's specialised code now if it has none: about a second
  * of compilation per triangulation, in parallel host threads) or

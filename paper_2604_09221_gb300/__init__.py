@@ -34,6 +34,12 @@ _lock = threading.Lock()
 _lib = None
 
 
+class BatchGroupInfo(ctypes.Structure):
+    """ts_batch_group_info of include/tcurve.h."""
+    _fields_ = [(f, ctypes.c_int) for f in ("kernel", "threads", "chunk", "scratch", "registers",
+                                            "local_bytes", "blocks_per_sm", "grid")]
+
+
 class TSError(RuntimeError):
     def __init__(self, status: int, what: str = ""):
         self.status = int(status)
@@ -88,8 +94,8 @@ def _load():
                 "ts_batch_run": ([P, I, P], I),
                 "ts_batch_read": ([P, I, P, P, U64, ctypes.POINTER(U64), ctypes.POINTER(U64), P], I),
                 "ts_batch_set_kernel": ([P, I, I], I),
-                "ts_batch_info": ([P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
-                                   ctypes.POINTER(I), ctypes.c_char_p, ctypes.c_size_t], I),
+                "ts_batch_info": ([P, I, ctypes.POINTER(BatchGroupInfo), ctypes.c_char_p,
+                                   ctypes.c_size_t], I),
                 "ts_batch_specialized_link": ([I, I, P, P, ctypes.POINTER(ctypes.c_size_t),
                                                ctypes.c_char_p, ctypes.c_size_t], I),
                 "ts_int_issue_peak": ([I, U64, ctypes.POINTER(ctypes.c_double),
@@ -341,15 +347,16 @@ class Batch:
         _check(_lib.ts_batch_set_kernel(self._h, int(d), int(kind)), "ts_batch_set_kernel")
 
     def info(self, d: int) -> dict:
-        """Kernel family and tile of the degree-d group (ts_batch_info)."""
-        k, t, c, sc = (ctypes.c_int() for _ in range(4))
+        """Kernel family, tile and launch resources of the degree-d group
+        (ts_batch_info)."""
+        x = BatchGroupInfo()
         buf = ctypes.create_string_buffer(1 << 14)
-        _check(_lib.ts_batch_info(self._h, int(d), ctypes.byref(k), ctypes.byref(t), ctypes.byref(c),
-                                  ctypes.byref(sc), buf, len(buf)), "ts_batch_info")
-        return {"kernel": {TS_KERNEL_TABLE: "table", TS_KERNEL_SPECIALIZED: "specialized"}[k.value],
-                "threads": t.value, "chunk": c.value,
-                "scratch": {TS_SCRATCH_SHARED: "shared", TS_SCRATCH_GLOBAL: "global"}[sc.value],
-                "log": buf.value.decode(errors="replace")}
+        _check(_lib.ts_batch_info(self._h, int(d), ctypes.byref(x), buf, len(buf)), "ts_batch_info")
+        out = {f: getattr(x, f) for f, _ in BatchGroupInfo._fields_}
+        out["kernel"] = {TS_KERNEL_TABLE: "table", TS_KERNEL_SPECIALIZED: "specialized"}[x.kernel]
+        out["scratch"] = {TS_SCRATCH_SHARED: "shared", TS_SCRATCH_GLOBAL: "global"}[x.scratch]
+        out["log"] = buf.value.decode(errors="replace")
+        return out
 
     def run(self, graph: bool = True, stream=None):
         _check(_lib.ts_batch_run(self._h, int(bool(graph)), _stream_handle(stream)), "ts_batch_run")

@@ -615,15 +615,30 @@ ts_status ts_batch_run(ts_batch *b, int use_graph, void *stream) {
   return cuda_st(cudaGraphLaunch(b->exec, st));
 }
 
-ts_status ts_batch_info(const ts_batch *b, int d, int *kernel, int *threads, int *chunk,
-                        int *scratch, char *log, size_t len) {
-  if (!b) return TS_EINVAL;
+ts_status ts_batch_info(const ts_batch *b, int d, ts_batch_group_info *info, char *log,
+                        size_t len) {
+  if (!b || !info) return TS_EINVAL;
   for (const auto &g : b->groups) {
     if (g.d != d) continue;
-    if (kernel) *kernel = g.jit ? TS_KERNEL_SPECIALIZED : TS_KERNEL_TABLE;
-    if (threads) *threads = g.threads;
-    if (chunk) *chunk = g.chunk;
-    if (scratch) *scratch = g.global ? TS_SCRATCH_GLOBAL : TS_SCRATCH_SHARED;
+    ts_batch_group_info x{};
+    x.kernel = g.jit ? TS_KERNEL_SPECIALIZED : TS_KERNEL_TABLE;
+    x.threads = g.threads;
+    x.chunk = g.chunk;
+    x.scratch = g.global ? TS_SCRATCH_GLOBAL : TS_SCRATCH_SHARED;
+    x.grid = (int)g.grid;
+    if (g.jit) {
+      jit_jobs_attrs(*g.jit, &x.registers, &x.local_bytes);
+      x.blocks_per_sm = jit_jobs_blocks_per_sm(*g.jit);
+    } else if (g.fn) {
+      cudaFuncAttributes fa{};
+      if (cudaFuncGetAttributes(&fa, (const void *)g.fn) == cudaSuccess) {
+        x.registers = fa.numRegs;
+        x.local_bytes = (int)fa.localSizeBytes;
+      }
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&x.blocks_per_sm, (const void *)g.fn, g.threads,
+                                                    g.smem);
+    }
+    *info = x;
     if (log && len) {
       const size_t n = std::min(len - 1, g.jit_log.size());
       std::memcpy(log, g.jit_log.data(), n);

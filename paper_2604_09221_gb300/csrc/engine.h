@@ -17,7 +17,7 @@ namespace tcurve {
 constexpr int kMaxDegree = 16;     // |A| <= 153: three sign words, four code words
 constexpr int kMaxSpecialized = 9;  // triangulation-specialised kernels: one sign word
 constexpr int kGlobalScratchFrom = 7;  // TS_SCRATCH_AUTO: table kernels use global scratch from here
-constexpr int kMaxBatchSpecialized = 12;  // TS_KERNEL_AUTO: largest degree of specialised batch groups
+constexpr int kMaxBatchSpecialized = 6;  // TS_KERNEL_AUTO: largest degree of specialised batch groups
 
 // Count words of multi-word histograms carry two flags in their top bits
 // (slot being written / key published); the count is the rest.
@@ -56,6 +56,9 @@ struct JitModule;  // compiled specialised kernels (jit.cpp)
 
 // Tables of the table-driven sweep (host.cpp; format in tc_runtime.cuh).
 bool pack_diamond_tables(const Diamond &D, std::vector<uint32_t> &tables, TableLayout &lay);
+// Label slot of every vertex in the table-driven sweep (a slot is reused once
+// its vertex has no later reader) and, in *nslots, how many slots are used.
+std::vector<int> lab_slots(const Diamond &D, int *nslots);
 
 // Most joins vertex v can push in a sweep: one per run of same-sign fan
 // entries after the first (a run starts at entry i when it has the vertex's
@@ -149,6 +152,7 @@ cudaError_t jit_jobs_build(const std::vector<std::vector<const Diamond *>> &grou
                            std::vector<std::shared_ptr<JitJobsModule>> *mods,
                            std::vector<std::string> *logs);
 int jit_jobs_threads();
+void jit_jobs_attrs(const JitJobsModule &m, int *regs, int *local_bytes);
 int jit_jobs_blocks_per_sm(const JitJobsModule &m);
 size_t jit_jobs_slab_bytes(const JitJobsModule &m);  // global scratch per block
 cudaError_t jit_jobs_launch(const JitJobsModule &m, unsigned grid, const void *jobs, uint32_t njobs,

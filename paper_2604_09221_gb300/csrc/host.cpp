@@ -206,29 +206,68 @@ std::vector<char> flush_schedule(const Diamond &D, int v0, int v1, int pcap) {
   return flush;
 }
 
+// Label slots of the table-driven sweep.  A vertex's label is written when
+// the sweep reaches it and read by later vertices: those whose fan holds it,
+// its antipodal partner and the far end of a boundary edge.  Its slot is
+// taken at its own step and freed after its last reader, and every vertex
+// takes the lowest free slot (greedy colouring of the live intervals in sweep
+// order), so the sweep touches only as many label slots as are live at once:
+// about two rows of T^diamond plus the boundary vertices that wait for their
+// partners, instead of one per vertex.
+std::vector<int> lab_slots(const Diamond &D, int *nslots) {
+  const int V = D.V;
+  std::vector<int> last(V);
+  for (int v = 0; v < V; ++v) last[v] = v;
+  for (int w = 0; w < V; ++w)
+    for (int u : D.fan[w]) last[u] = std::max(last[u], w);
+  for (auto &p : D.anti) last[p.first] = std::max(last[p.first], p.second);
+  for (auto &e : D.bedge) {
+    const int lo = std::min(e.first, e.second), hi = std::max(e.first, e.second);
+    last[lo] = std::max(last[lo], hi);
+  }
+  std::vector<int> slot(V), free_slots;
+  std::vector<std::vector<int>> release(V + 1);
+  int next = 0;
+  for (int v = 0; v < V; ++v) {
+    for (int u : release[v]) free_slots.push_back(slot[u]);
+    if (free_slots.empty()) {
+      slot[v] = next++;
+    } else {
+      auto it = std::min_element(free_slots.begin(), free_slots.end());
+      slot[v] = *it;
+      free_slots.erase(it);
+    }
+    release[last[v] + 1].push_back(v);
+  }
+  if (nslots) *nslots = next;
+  return slot;
+}
+
 // Pack the diamond into the tables the table-driven kernels stage into
 // shared memory and the specialised kernels keep in constant memory (format
 // in tc_runtime.cuh; bit 30 of vext[v]: apply the pending joins before v).
-// Returns false if a field does not fit: a vertex id (10 bits), a fan longer
-// than the join list of the kernels takes (tc_pcap), or a fan start beyond
-// 16 bits.
+// Vertex references (fan entries, antipodal and boundary-edge partners) are
+// label slots (lab_slots).  Returns false if a field does not fit: a vertex
+// id or slot (10 bits), a fan longer than the join list of the kernels takes
+// (tc_pcap), or more than 2^16 fan entries.
 bool pack_diamond_tables(const Diamond &D, std::vector<uint32_t> &tables, TableLayout &lay) {
   const int V = D.V;
   constexpr uint32_t kNone = 1023u;
   if (V > (int)kNone) return false;
+  const std::vector<int> slot = lab_slots(D, nullptr);
   std::vector<uint32_t> vdesc(V), fan, vext(V, kNone | (kNone << 10) | (kNone << 20));
   for (int v = 0; v < V; ++v) {
     const int m = (int)D.fan[v].size();
     if (m > 127 || m + 1 > tc_pcap(D.d) || fan.size() > 65535 || D.k[v] > 255) return false;
     vdesc[v] = (uint32_t)D.k[v] | ((uint32_t)D.c[v] << 8) | ((uint32_t)m << 9) |
-               ((uint32_t)fan.size() << 16);
+               ((uint32_t)slot[v] << 16);
     for (int n = 0; n < m; ++n) {
       int u = D.fan[v][n];
-      fan.push_back((uint32_t)u | ((uint32_t)D.k[u] << 10) | ((uint32_t)D.c[u] << 18) |
+      fan.push_back((uint32_t)slot[u] | ((uint32_t)D.k[u] << 10) | ((uint32_t)D.c[u] << 18) |
                     ((uint32_t)D.link[v][n] << 19));
     }
   }
-  for (auto &p : D.anti) vext[p.second] = (vext[p.second] & ~kNone) | (uint32_t)p.first;
+  for (auto &p : D.anti) vext[p.second] = (vext[p.second] & ~kNone) | (uint32_t)slot[p.first];
   const std::vector<char> flush = flush_schedule(D, 0, V, tc_pcap(D.d));
   for (int v = 0; v < V; ++v)
     if (flush[v]) vext[v] |= 1u << 30;
@@ -236,8 +275,8 @@ bool pack_diamond_tables(const Diamond &D, std::vector<uint32_t> &tables, TableL
     for (auto &e : D.bedge) {
       const int late = std::max(e.first, e.second), early = std::min(e.first, e.second);
       uint32_t &w = vext[late];
-      if (((w >> 10) & kNone) == kNone) w = (w & ~(kNone << 10)) | ((uint32_t)early << 10);
-      else if (((w >> 20) & kNone) == kNone) w = (w & ~(kNone << 20)) | ((uint32_t)early << 20);
+      if (((w >> 10) & kNone) == kNone) w = (w & ~(kNone << 10)) | ((uint32_t)slot[early] << 10);
+      else if (((w >> 20) & kNone) == kNone) w = (w & ~(kNone << 20)) | ((uint32_t)slot[early] << 20);
       else return false;
     }
   }

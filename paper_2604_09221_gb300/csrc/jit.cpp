@@ -106,6 +106,7 @@ struct Driver {
   decltype(&cuFuncSetAttribute) set_attr = nullptr;
   decltype(&cuOccupancyMaxActiveBlocksPerMultiprocessor) occupancy = nullptr;
   decltype(&cuLaunchKernel) launch = nullptr;
+  decltype(&cuFuncGetAttribute) get_attr = nullptr;
   bool ok = false;
 };
 
@@ -122,7 +123,8 @@ Driver &driver() {
            get("cuModuleGetFunction", (void **)&d.get) &&
            get("cuFuncSetAttribute", (void **)&d.set_attr) &&
            get("cuOccupancyMaxActiveBlocksPerMultiprocessor", (void **)&d.occupancy) &&
-           get("cuLaunchKernel", (void **)&d.launch);
+           get("cuLaunchKernel", (void **)&d.launch) &&
+           get("cuFuncGetAttribute", (void **)&d.get_attr);
   });
   return d;
 }
@@ -303,10 +305,11 @@ std::string jit_source(const Diamond &D, bool global, int min_blocks) {
     for (int i : anti_at[v]) used[D.anti[i].first] = 1;
     for (int i : bedge_at[v]) used[D.bedge[i].first] = used[D.bedge[i].second] = 1;
   }
+  const std::vector<int> slot = lab_slots(D, nullptr);  // where the table sweep left each label
   for (int u = 0; u < Vo; ++u)
     if (used[u])
       o << "  const u32 s" << u << " = TC_BIT(" << D.k[u] << ") ^ " << D.c[u] << "u, L" << u
-        << " = *S.lab(TcK::OFF_LAB, " << u << ") & TcS::LOW;\n";
+        << " = *S.lab(TcK::OFF_LAB, " << slot[u] << ") & TcS::LOW;\n";
   // snapshot of the half-diamonds' union-find: the first SNAPW words of the
   // parents and the first word of odd flags in registers, the rest (many
   // half labels at d >= 8) in the [snap] region
@@ -641,6 +644,20 @@ JitLink &jitlink() {
   return j;
 }
 
+// One job of a batch as the generated code sees it: the layout of the host's
+// job table (72 bytes, DevJob of batch.cu).
+const char kJobStructSrc[] = R"TCJS(
+struct TcjJob {
+  const unsigned *tab;
+  unsigned long long n, base;          // sign vectors; splitmix64 counter of the first
+  unsigned long long *codes;           // per-instance codes (or null)
+  unsigned long long *hkeys;           // the job's histogram
+  unsigned long long *hcnt;
+  unsigned long long hslots, chunk0;   // its slots; its first work item
+  unsigned fn, pad;                    // index of its specialised function
+};
+)TCJS";
+
 // Scratch layout of the batch kernels: one label per vertex (the wide back
 // end reuses that region), 128-thread blocks, global memory.
 Layout job_layout(int d) {
@@ -651,16 +668,15 @@ Layout job_layout(int d) {
 
 // Resident 128-thread blocks per SM the batch kernels of degree d are
 // compiled for (their register budget: 65536 / (128 x blocks) registers).
-int job_min_blocks(int d) { return d <= 7 ? 6 : d == 8 ? 5 : d <= 10 ? 4 : 3; }
+int job_min_blocks(int d) { return d <= 10 ? 4 : 3; }
 
 int job_max_registers(int d) {
   const int r = 65536 / (kJobThreads * job_min_blocks(d));
   return std::min(255, r / 8 * 8);
 }
 
-// Words of global scratch per block: the per-thread layout, then four u64
-// per thread (the slot where a batch function leaves its code words).
-size_t job_slab_words(const Layout &L) { return (size_t)L.words * L.threads + 8u * L.threads; }
+// Words of global scratch per block: the per-thread layout.
+size_t job_slab_words(const Layout &L) { return (size_t)L.words * L.threads; }
 
 }  // namespace
 
@@ -692,17 +708,58 @@ std::string jit_job_source(const Diamond &D, int idx) {
     o << "  tc_backend_wide(S, nl, nb, err, code);\n";
   else
     o << "  code[0] = tc_backend(S, nl, nb, err);\n";
-  o << "}\n}  // namespace tcj" << idx << "\n\n";
-  o << "extern \"C\" __device__ void tcj_" << idx
-    << "(unsigned long long sg0, unsigned long long sg1, unsigned long long sg2, unsigned int *scr,\n"
-    << "    unsigned int *gerr, unsigned long long *out) {\n"
-    << "  const tcj" << idx << "::TcS S{scr};\n"
-    << "  unsigned int err = 0;\n"
-    << "  unsigned long long code[tcj" << idx << "::TcK::CW];\n"
-    << "  tcj" << idx << "::classify(sg0, sg1, sg2, S, err, code);\n"
-    << "  if (err) atomicOr(gerr, err);\n"
-    << "#pragma unroll\n"
-    << "  for (unsigned w = 0; w < tcj" << idx << "::TcK::CW; ++w) out[w] = code[w];\n"
+  o << "}\n\n";
+  o << kJobStructSrc;
+  o << R"TCJF(
+// One work item of a job: sign vectors first .. first + chunk - 1 (those below
+// the job's count), drawn from the job's splitmix64 stream, classified by the
+// sweep above and added to the job's histogram (warp-aggregated); returns
+// the number of failed instances.
+__device__ __forceinline__ unsigned long long chunk_body(const TcjJob *J, unsigned long long first,
+                                                         unsigned chunk, unsigned *scr,
+                                                         unsigned *err_word) {
+  const TcS S{scr};
+  const u32 lane = threadIdx.x & 31u;
+  const u64 top = tc_top_mask(TcK::NPOINTS, TcK::W);
+  u32 err = 0;
+  unsigned long long failed = 0;
+  for (unsigned k = 0; k < chunk; k += TcK::THREADS) {
+    const u64 idx = first + k + threadIdx.x;
+    u64 code[TcK::CW];
+#pragma unroll
+    for (u32 w = 0; w < TcK::CW; ++w) code[w] = 0;
+    if (idx < J->n) {
+      u64 sg[3] = {0, 0, 0};
+#pragma unroll
+      for (u32 w = 0; w < TcK::W; ++w) sg[w] = tc_splitmix64((J->base + idx) * TcK::W + w);
+      sg[TcK::W - 1] &= top;
+      classify(sg[0], sg[1], sg[2], S, err, code);
+      u64 any = 0;
+#pragma unroll
+      for (u32 w = 0; w < TcK::CW; ++w) {
+        any |= code[w];
+        if (J->codes) J->codes[idx * TcK::CW + w] = code[w];
+      }
+      failed += any == 0;
+    }
+    if (TcK::CW == 1) {
+      const unsigned peers = __match_any_sync(0xffffffffu, code[0]);
+      if (code[0] != 0 && lane == (u32)(__ffs(peers) - 1))
+        tc_global_add(J->hkeys, J->hcnt, J->hslots, err_word, code[0], (u64)__popc(peers));
+    } else {
+      tc_hist_add_wide<TcK::CW>(code, J->hkeys, J->hcnt, J->hslots, err_word);
+    }
+  }
+  if (err) atomicOr(err_word, err);
+  return failed;
+}
+)TCJF";
+  o << "}  // namespace tcj" << idx << "\n\n";
+  o << "extern \"C\" __device__ unsigned long long tcj_" << idx
+    << "(const void *job, unsigned long long first, unsigned chunk, unsigned int *scr,\n"
+    << "    unsigned int *err_word) {\n"
+    << "  return tcj" << idx << "::chunk_body(static_cast<const tcj" << idx
+    << "::TcjJob *>(job), first, chunk, scr, err_word);\n"
     << "}\n";
   return o.str();
 }
@@ -712,37 +769,22 @@ std::string jit_jobs_kernel_source(int d, int nfn) {
   std::ostringstream o;
   o << "// T-curve batch kernel of degree " << d << " over " << nfn
     << " specialised functions (generated, relocatable)\n";
-  o << "namespace tcjk {\n";
-  emit_traits(o, L, d, 2 * d * d + 2 * d + 1, true, job_min_blocks(d));
-  o << "#define TC_HEAVY_FN __forceinline__\n" << kRuntimeSrc << "}  // namespace tcjk\n\n";
+  o << kJobStructSrc;
   for (int i = 0; i < nfn; ++i)
-    o << "extern \"C\" __device__ void tcj_" << i
-      << "(unsigned long long, unsigned long long, unsigned long long, unsigned int *, unsigned int *,"
-         " unsigned long long *);\n";
+    o << "extern \"C\" __device__ unsigned long long tcj_" << i
+      << "(const void *, unsigned long long, unsigned, unsigned int *, unsigned int *);\n";
+  o << "#define TCJ_THREADS " << L.threads << "u\n#define TCJ_SLAB " << (size_t)L.words * L.threads
+    << "ull\n#define TCJ_MINB " << job_min_blocks(d) << "\n";
   o << R"TCJOBS(
-// One job of the batch: the layout of the host's job table (72 bytes).
-struct TcjJob {
-  const unsigned *tab;
-  unsigned long long n, base;          // sign vectors; splitmix64 counter of the first
-  unsigned long long *codes;           // per-instance codes (or null)
-  unsigned long long *hkeys;           // the job's histogram
-  unsigned long long *hcnt;
-  unsigned long long hslots, chunk0;   // its slots; its first work item
-  unsigned fn, pad;                    // index of its specialised function
-};
-
-extern "C" __global__ void __launch_bounds__(tcjk::TcK::THREADS, tcjk::TcK::MINB)
+// Persistent kernel of the degree's jobs: blocks pull work items (job, chunk)
+// from a counter; the job's own function classifies the item's sign vectors.
+extern "C" __global__ void __launch_bounds__(TCJ_THREADS, TCJ_MINB)
     tcj_jobs(const TcjJob *__restrict__ jobs, unsigned njobs, unsigned long long total_items,
              unsigned chunk, unsigned long long *work, unsigned *err_word,
              unsigned long long *failed_word, unsigned *gscr) {
-  typedef tcjk::TcK K;
   typedef unsigned long long u64;
   __shared__ u64 slot;
-  const unsigned lane = threadIdx.x & 31u;
-  unsigned *slab = gscr + (u64)blockIdx.x * (K::WORDS * K::THREADS + 8u * K::THREADS);
-  unsigned *scr = slab + threadIdx.x;
-  u64 *out = reinterpret_cast<u64 *>(slab + K::WORDS * K::THREADS) + 4u * threadIdx.x;
-  const u64 top = tcjk::tc_top_mask(K::NPOINTS, K::W);
+  unsigned *scr = gscr + (u64)blockIdx.x * TCJ_SLAB + threadIdx.x;
   u64 failed = 0;
   for (;;) {
     if (threadIdx.x == 0) slot = atomicAdd(work, 1ull);
@@ -755,44 +797,14 @@ extern "C" __global__ void __launch_bounds__(tcjk::TcK::THREADS, tcjk::TcK::MINB
       const unsigned mid = (lo + hi) / 2;
       if (jobs[mid].chunk0 <= c) lo = mid; else hi = mid;
     }
-    const TcjJob J = jobs[lo];
-    const u64 first = (c - J.chunk0) * (u64)chunk;
-    for (unsigned k = 0; k < chunk; k += K::THREADS) {
-      const u64 idx = first + k + threadIdx.x;
-      u64 key[K::CW];
-#pragma unroll
-      for (unsigned w = 0; w < K::CW; ++w) key[w] = 0;
-      if (idx < J.n) {
-        // the sign vector of counter base + idx, as ts_splitmix_masks writes it
-        u64 s[3] = {0, 0, 0};
-#pragma unroll
-        for (unsigned w = 0; w < K::W; ++w) s[w] = tcjk::tc_splitmix64((J.base + idx) * K::W + w);
-        s[K::W - 1] &= top;
-        switch (J.fn) {
+    const TcjJob *J = jobs + lo;
+    const u64 first = (c - J->chunk0) * (u64)chunk;
+    switch (J->fn) {
 )TCJOBS";
   for (int i = 0; i < nfn; ++i)
-    o << "          case " << i << "u: tcj_" << i << "(s[0], s[1], s[2], scr, err_word, out); break;\n";
-  o << R"TCJOBS(          default:
-#pragma unroll
-            for (unsigned w = 0; w < K::CW; ++w) out[w] = 0;
-            atomicOr(err_word, tcjk::TC_ERR_INTERNAL);
-        }
-        u64 any = 0;
-#pragma unroll
-        for (unsigned w = 0; w < K::CW; ++w) {
-          key[w] = out[w];
-          any |= key[w];
-          if (J.codes) J.codes[idx * K::CW + w] = key[w];
-        }
-        failed += any == 0;
-      }
-      if (K::CW == 1) {
-        const unsigned peers = __match_any_sync(0xffffffffu, key[0]);
-        if (key[0] != 0 && lane == (unsigned)(__ffs(peers) - 1))
-          tcjk::tc_global_add(J.hkeys, J.hcnt, J.hslots, err_word, key[0], (u64)__popc(peers));
-      } else {
-        tcjk::tc_hist_add_wide<K::CW>(key, J.hkeys, J.hcnt, J.hslots, err_word);
-      }
+    o << "      case " << i << "u: failed += tcj_" << i << "(J, first, chunk, scr, err_word); break;\n";
+  o << R"TCJOBS(      default:
+        if (threadIdx.x == 0) atomicOr(err_word, 1u);  // no function: an internal error
     }
   }
   if (failed) atomicAdd(failed_word, failed);
@@ -976,6 +988,11 @@ cudaError_t jit_jobs_build(const std::vector<std::vector<const Diamond *>> &grou
 }
 
 int jit_jobs_threads() { return kJobThreads; }
+void jit_jobs_attrs(const JitJobsModule &m, int *regs, int *local_bytes) {
+  *regs = *local_bytes = 0;
+  driver().get_attr(regs, CU_FUNC_ATTRIBUTE_NUM_REGS, m.fn);
+  driver().get_attr(local_bytes, CU_FUNC_ATTRIBUTE_LOCAL_SIZE_BYTES, m.fn);
+}
 int jit_jobs_blocks_per_sm(const JitJobsModule &m) { return m.bpsm; }
 size_t jit_jobs_slab_bytes(const JitJobsModule &m) { return m.slab_words * 4; }
 

@@ -630,18 +630,20 @@ __device__ __noinline__ void tc_backend_wide(const TcScratch<K> &S, u32 nl, u32 
 
 // ------------------------------------------------ table-driven sweep ----
 //
-// The triangulation tables of host.cpp (32-bit words, vertex ids are
-// positions in the sweep order of T^diamond):
+// The triangulation tables of host.cpp (32-bit words, vertices in the sweep
+// order of T^diamond; a vertex's label lives in a label slot, reused once no
+// later vertex reads it, so the sweep touches only the slots live at once):
 //   vdesc[V]  bits 0-7 lattice index k(v), bit 8 Eq. 2 parity constant c(v)
 //             (sign(v) = sigma_k ^ c), bits 9-15 fan length m, bits 16-31
-//             first fan entry
-//   fan[NF]   bits 0-9 earlier neighbour u, bits 10-17 k(u), bit 18 c(u),
-//             bit 19 "u and the previous entry span a triangle with v"
-//   vext[V]   bits 0-9 the antipodal partner x < v of v, bits 10-19 and
-//             20-29 the other end b < v of up to two boundary edges kept for
-//             root detection (1023: none), bit 30 "apply the pending joins
-//             before v" (a static schedule from the most joins each vertex
-//             can push, the same in every instance)
+//             v's label slot; v's fan entries follow those of v - 1
+//   fan[NF]   bits 0-9 label slot of the earlier neighbour u, bits 10-17
+//             k(u), bit 18 c(u), bit 19 "u and the previous entry span a
+//             triangle with v"
+//   vext[V]   bits 0-9 the label slot of the antipodal partner x < v of v,
+//             bits 10-19 and 20-29 those of the other end b < v of up to two
+//             boundary edges kept for root detection (1023: none), bit 30
+//             "apply the pending joins before v" (a static schedule from the
+//             most joins each vertex can push, the same in every instance)
 #define TC_TAB_NONE 1023u
 
 // Sweep vertices [v0, v1) (Alg. 1, lines 3-4): every vertex takes the label
@@ -658,10 +660,12 @@ __device__ __forceinline__ void tc_sweep_table(const SIG &sig, const u32 *__rest
                                                const u32 *__restrict__ vext, u32 v0, u32 v1,
                                                const TcScratch<K> &S, u32 &nl, u32 &nb, u32 &np) {
   typedef TcScratch<K> TS;
+  u32 fs = 0;  // the first fan entry of v: fans are stored in sweep order
+  for (u32 v = 0; v < v0; ++v) fs += (vdesc[v] >> 9) & 127u;
   for (u32 v = v0; v < v1; ++v) {
     const u32 desc = vdesc[v];
     const u32 sv = sig.bit(desc & 255u) ^ ((desc >> 8) & 1u);
-    const u32 m = (desc >> 9) & 127u, fs = desc >> 16;
+    const u32 m = (desc >> 9) & 127u;
     const u32 x = vext[v];
     if ((x >> 30) & 1u) {  // the schedule's flush: the same vertex in every lane
       tc_unions(S, np);
@@ -689,7 +693,8 @@ __device__ __forceinline__ void tc_sweep_table(const SIG &sig, const u32 *__rest
       tc_newlab(S, nl, l0);
       ++nl;
     }
-    *S.lab(K::OFF_LAB, v) = (typename TS::lab_t)(lv | (sv << SB));
+    *S.lab(K::OFF_LAB, desc >> 16) = (typename TS::lab_t)(lv | (sv << SB));
+    fs += m;
     if ((x & 1023u) != TC_TAB_NONE) {  // the antipodal partner, reached earlier
       S.word(K::OFF_PEND, np) =
           ((u32)*S.lab(K::OFF_LAB, x & 1023u) & TS::LOW) | (lv << 16) | 0x80000000u;

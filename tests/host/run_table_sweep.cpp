@@ -40,7 +40,10 @@ cudaError_t launch_enumerate_jit(ts_tri *, uint64_t, uint64_t, uint32_t, ts_hist
 cudaError_t launch_enumerate(const ts_tri *, uint64_t, uint64_t, uint32_t, ts_hist *, cudaStream_t, bool) { return cudaErrorNotSupported; }
 void jit_release(ts_tri *) {}
 std::string jit_source(const Diamond &, bool, int) { return ""; }
-std::string jit_compile_cubin(const std::string &, std::string *) { return ""; }
+std::string jit_compile_cubin(const std::string &, std::string *, const std::vector<std::string> &) {
+  return "";
+}
+std::string jit_jobs_link(const std::vector<const Diamond *> &, std::string *) { return ""; }
 void jit_config(int, int, int, bool *, int *) {}
 }  // namespace tcurve
 

@@ -109,8 +109,8 @@ def test_autotuner_picks_tiles_that_run(eng, jobs, tmp_path):
 def test_mixed_batch_full_size(eng, orc):
     """The mixed-degree batch workload at its full size: 32 seeded regular
     triangulations for each d in 5..10, 2^U(10,24) splitmix64 sign vectors
-    per triangulation (about 3.3e8 in all), one graph launch, every degree
-    group on specialised code.  Every job's
+    per triangulation (about 3.3e8 in all), one graph launch, the groups of
+    d = 5 and 6 on specialised code and the others table-driven.  Every job's
     histogram accounts for all its sign vectors, none failed, and every
     scheme satisfies the classical restrictions; one job per degree also
     stores its codes, and 1024 sampled rows of each equal the oracle's codes
@@ -130,8 +130,9 @@ def test_mixed_batch_full_size(eng, orc):
     outs = [torch.zeros((counts[j], tris[j].code_words), dtype=torch.int64, device="cuda")
             if j in sampled else None for j in range(len(tris))]
     batch = eng.Batch(tris, counts, bases, code_outputs=outs)
-    for d in degrees:   # every group is large enough for specialised code
-        assert batch.info(d)["kernel"] == "specialized", batch.info(d)["log"][-2000:]
+    for d in degrees:   # specialised code up to d = 6 (every group is large enough)
+        assert batch.info(d)["kernel"] == ("specialized" if d <= 6 else "table"), \
+            batch.info(d)["log"][-2000:]
     batch.run(graph=True)
     torch.cuda.synchronize()
     checked = set()
@@ -225,19 +226,21 @@ def test_specialised_batch_matches_oracle(eng, orc):
 
 
 def test_specialised_batch_by_size(eng):
-    """TS_KERNEL_AUTO at creation: a degree group of at least 2^22 sign
-    vectors runs specialised code, a smaller one the table-driven kernel, and
-    a group with a triangulation set to TS_KERNEL_TABLE stays table-driven;
-    the large groups count all their sign vectors."""
-    t9 = [eng.Triangulation(9, e) for e in ti.regular_triangulations(9, 2, seed=909)]
+    """TS_KERNEL_AUTO at creation: a degree group of d <= 6 with at least
+    2^22 sign vectors runs specialised code; a smaller one, one of higher
+    degree, and one with a triangulation set to TS_KERNEL_TABLE run the
+    table-driven kernel; the large groups count all their sign vectors."""
+    t5 = [eng.Triangulation(5, e) for e in ti.regular_triangulations(5, 2, seed=505)]
     t6 = eng.Triangulation(6, ti.regular_triangulation(6, seed=606))
     t8 = eng.Triangulation(8, ti.regular_triangulation(8, seed=808))
-    t8.set_kernel(eng.TS_KERNEL_TABLE)
-    counts = [1 << 21, 1 << 21, 5000, 1 << 23]
-    batch = eng.Batch(t9 + [t6, t8], counts, [1, 2, 3, 4])
-    assert batch.info(9)["kernel"] == "specialized", batch.info(9)["log"][-2000:]
+    t9 = eng.Triangulation(9, ti.regular_triangulation(9, seed=909))
+    t9.set_kernel(eng.TS_KERNEL_TABLE)
+    counts = [1 << 21, 1 << 21, 5000, 1 << 23, 1 << 22]
+    batch = eng.Batch(t5 + [t6, t8, t9], counts, [1, 2, 3, 4, 5])
+    assert batch.info(5)["kernel"] == "specialized", batch.info(5)["log"][-2000:]
     assert batch.info(6)["kernel"] == "table"
     assert batch.info(8)["kernel"] == "table"
+    assert batch.info(9)["kernel"] == "table"
     batch.run()
     for j, n in enumerate(counts):
         codes, cnt, failed = batch.read(j)
