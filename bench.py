@@ -195,10 +195,12 @@ def main():
     ap.add_argument("--splitmix", action="store_true")
     ap.add_argument("--occupancy", type=int, default=0)
     ap.add_argument("--query", action="store_true")
+    ap.add_argument("--batch", action="store_true")
     ap.add_argument("--trips", type=int, default=1 << 15)
     ap.add_argument("--no-stretch", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--families", action="store_true")
+    ap.add_argument("--occupancies", default="0")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -427,6 +429,28 @@ def profile_case(args):
     if args.kernel != "table" and d <= 9:
         tri.prepare()
     n = 1 << args.log2n
+    if args.batch:  # a one-degree batch of 8 triangulations, n sign vectors in all
+        tris8 = [eng.Triangulation(d, e) for e in ti.regular_triangulations(d, 8, seed=31 + d)]
+        batch = eng.Batch(tris8, [n // 8] * 8, [job_base(3100 + d, k) for k in range(8)])
+        batch.set_kernel(d, {"auto": eng.TS_KERNEL_AUTO, "table": eng.TS_KERNEL_TABLE,
+                             "specialized": eng.TS_KERNEL_SPECIALIZED}[args.kernel])
+        ms = []
+        for _ in range(2):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            batch.run(graph=False)
+            b.record()
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        for j in range(8):
+            codes, cnt, failed = batch.read(j)
+            assert failed == 0 and int(cnt.sum()) == n // 8
+        info = batch.info(d)
+        info.pop("log")
+        print(json.dumps({"profile_case": True, "batch": True, "degree": d, "n": n, "ms": ms,
+                          "info": info, "schemes_per_s": n / (min(ms) / 1e3)}), flush=True)
+        return 0
     if args.query:  # the plain query kernel on n materialised sign vectors
         masks = eng.splitmix_masks(d, 0, n)
         out = torch.empty((n, tri.code_words), dtype=torch.int64, device="cuda")
@@ -667,9 +691,11 @@ def mixed_run(steps, warmup, degrees=(5, 6, 7, 8, 9, 10), per_degree=32, seed=31
             "gpu_launches_per_step": len(degrees)}
 
 
-def mixed_families(reps=3, degrees=(5, 6, 7, 8, 9, 10), per_degree=32, seed=31):
+def mixed_families(reps=3, degrees=(5, 6, 7, 8, 9, 10), per_degree=32, seed=31, occupancies=(0,)):
     """Each degree group of the mixed batch alone, table-driven and
-    specialised (default tiles): schemes/s and the launch's resources."""
+    specialised (default tiles; for each register budget in `occupancies`,
+    resident blocks per SM, 0 the default): schemes/s and the launch's
+    resources."""
     import numpy as np
     import torch
 
@@ -685,7 +711,11 @@ def mixed_families(reps=3, degrees=(5, 6, 7, 8, 9, 10), per_degree=32, seed=31):
             bases.append(job_base(seed * 100 + d, k))
         batch = eng.Batch(tris, counts, bases)
         row = {}
-        for fam in (eng.TS_KERNEL_TABLE, eng.TS_KERNEL_SPECIALIZED):
+        runs = [(eng.TS_KERNEL_TABLE, 0)] + [(eng.TS_KERNEL_SPECIALIZED, o) for o in occupancies]
+        for fam, occ in runs:
+            for t in tris:
+                t.set_occupancy(occ)
+            batch.set_kernel(d, eng.TS_KERNEL_TABLE)
             batch.set_kernel(d, fam)
             batch.run(graph=False)
             torch.cuda.synchronize()
@@ -700,7 +730,8 @@ def mixed_families(reps=3, degrees=(5, 6, 7, 8, 9, 10), per_degree=32, seed=31):
                 best = min(best, a.elapsed_time(b))
             info = batch.info(d)
             info.pop("log")
-            row[info["kernel"]] = dict(info, schemes_per_s=sum(counts) / (best / 1e3), ms=best)
+            key = info["kernel"] + (f"_occ{occ}" if occ else "")
+            row[key] = dict(info, schemes_per_s=sum(counts) / (best / 1e3), ms=best)
         out[str(d)] = row
         batch.close()
     return out
@@ -715,7 +746,8 @@ def mixed_workload(args):
     _b.build()
     import paper_2604_09221_gb300 as eng
     if args.families:
-        print(json.dumps({"mixed_families": mixed_families()}), flush=True)
+        occ = tuple(int(x) for x in args.occupancies.split(","))
+        print(json.dumps({"mixed_families": mixed_families(occupancies=occ)}), flush=True)
         return 0
     peak = measure_int_peak(eng, args.trips)
     r = mixed_run(args.steps, args.warmup)

@@ -137,7 +137,10 @@ ts_status ts_set_scratch(ts_tri *tri, int where);
 /* Resident blocks per SM the specialised kernels are compiled for (their
  * register budget): 1..16, or 0 for the default (with global scratch 6, 5
  * and 4 blocks of 128 threads for d = 7, 8, 9 and 4 otherwise; 2 with shared
- * scratch).  Drops kernels already built for tri. */
+ * scratch).  Drops kernels already built for tri.  A batch's specialised
+ * code (ts_batch_info) takes the largest value over its group's
+ * triangulations when it is built (default: 4 blocks of 128 threads up to
+ * d = 10, 3 above). */
 ts_status ts_set_occupancy(ts_tri *tri, int blocks_per_sm);
 
 /* Build the specialised kernels now (NVRTC compile and module load on the

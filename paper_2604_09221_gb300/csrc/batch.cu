@@ -399,11 +399,14 @@ bool wants_specialised(const ts_batch *b, const ts_batch::Group &g) {
 bool make_specialised(ts_batch *b, const std::vector<int> &gids) {
   if (gids.empty()) return true;
   std::vector<std::vector<const Diamond *>> want;
+  std::vector<int> min_blocks;
   for (int gi : gids) {
     auto &g = b->groups[gi];
     std::map<const ts_tri *, uint32_t> fn;
     std::vector<const Diamond *> dias;
+    int occ = 0;  // a register budget asked for with ts_set_occupancy
     for (int j : g.jobs) {
+      occ = std::max(occ, b->tris[j]->occupancy);
       auto it = fn.find(b->tris[j]);
       if (it == fn.end()) {
         it = fn.emplace(b->tris[j], (uint32_t)dias.size()).first;
@@ -412,10 +415,11 @@ bool make_specialised(ts_batch *b, const std::vector<int> &gids) {
       b->jobs[j].fn = it->second;
     }
     want.push_back(dias);
+    min_blocks.push_back(occ);
   }
   std::vector<std::shared_ptr<JitJobsModule>> mods;
   std::vector<std::string> logs;
-  jit_jobs_build(want, &mods, &logs);
+  jit_jobs_build(want, min_blocks, &mods, &logs);
   bool all = true;
   for (size_t k = 0; k < gids.size(); ++k) {
     auto &g = b->groups[gids[k]];

@@ -141,14 +141,17 @@ void jit_release(ts_tri *tri);
 // code, exported as tcj_<i>) and one persistent kernel tcj_jobs that calls
 // them, compiled in parallel and linked with nvJitLink.
 struct JitJobsModule;
-std::string jit_job_source(const Diamond &D, int idx);
-std::string jit_jobs_kernel_source(int d, int nfn);
+std::string jit_job_source(const Diamond &D, int idx, int min_blocks);
+std::string jit_jobs_kernel_source(int d, int nfn, int min_blocks);
 // Compile and link without a device (the linked cubin, or empty and the log).
 std::string jit_jobs_link(const std::vector<const Diamond *> &tris, std::string *log);
 // Build the modules of several degree groups (each group: the diamonds of
-// its distinct triangulations, function i = group[i]) on the current device;
-// a group whose module cannot be built gets null and a log.
+// its distinct triangulations, function i = group[i]; min_blocks[g]: the
+// resident 128-thread blocks per SM its register budget is set for, 0 for
+// the default) on the current device; a group whose module cannot be built
+// gets null and a log.
 cudaError_t jit_jobs_build(const std::vector<std::vector<const Diamond *>> &groups,
+                           const std::vector<int> &min_blocks,
                            std::vector<std::shared_ptr<JitJobsModule>> *mods,
                            std::vector<std::string> *logs);
 int jit_jobs_threads();

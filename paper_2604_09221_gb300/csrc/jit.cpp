@@ -668,10 +668,11 @@ Layout job_layout(int d) {
 
 // Resident 128-thread blocks per SM the batch kernels of degree d are
 // compiled for (their register budget: 65536 / (128 x blocks) registers).
-int job_min_blocks(int d) { return d <= 10 ? 4 : 3; }
+int job_min_blocks(int d) { return d <= 5 ? 6 : d <= 10 ? 4 : 3; }
 
-int job_max_registers(int d) {
-  const int r = 65536 / (kJobThreads * job_min_blocks(d));
+// Registers per thread for `blocks` resident 128-thread blocks per SM.
+int job_max_registers(int blocks) {
+  const int r = 65536 / (kJobThreads * blocks);
   return std::min(255, r / 8 * 8);
 }
 
@@ -680,7 +681,7 @@ size_t job_slab_words(const Layout &L) { return (size_t)L.words * L.threads; }
 
 }  // namespace
 
-std::string jit_job_source(const Diamond &D, int idx) {
+std::string jit_job_source(const Diamond &D, int idx, int min_blocks) {
   const Layout L = job_layout(D.d);
   const int d = D.d, V = D.V;
   if (L.sw > 3 || L.cw > 4) return std::string();
@@ -688,7 +689,7 @@ std::string jit_job_source(const Diamond &D, int idx) {
   o << "// T-curve real-scheme function for one triangulation of " << d
     << "*Delta_2 in a batch (generated, relocatable)\n";
   o << "namespace tcj" << idx << " {\n";
-  emit_traits(o, L, d, V, true, job_min_blocks(d));
+  emit_traits(o, L, d, V, true, min_blocks);
   o << "#define TC_HEAVY_FN __forceinline__\n";
   o << kRuntimeSrc;
   o << "#define TC_BIT(k) ((((k) < 32 ? w0 : (k) < 64 ? w1 : (k) < 96 ? w2 : (k) < 128 ? w3 : "
@@ -764,7 +765,7 @@ __device__ __forceinline__ unsigned long long chunk_body(const TcjJob *J, unsign
   return o.str();
 }
 
-std::string jit_jobs_kernel_source(int d, int nfn) {
+std::string jit_jobs_kernel_source(int d, int nfn, int min_blocks) {
   const Layout L = job_layout(d);
   std::ostringstream o;
   o << "// T-curve batch kernel of degree " << d << " over " << nfn
@@ -774,7 +775,7 @@ std::string jit_jobs_kernel_source(int d, int nfn) {
     o << "extern \"C\" __device__ unsigned long long tcj_" << i
       << "(const void *, unsigned long long, unsigned, unsigned int *, unsigned int *);\n";
   o << "#define TCJ_THREADS " << L.threads << "u\n#define TCJ_SLAB " << (size_t)L.words * L.threads
-    << "ull\n#define TCJ_MINB " << job_min_blocks(d) << "\n";
+    << "ull\n#define TCJ_MINB " << min_blocks << "\n";
   o << R"TCJOBS(
 // Persistent kernel of the degree's jobs: blocks pull work items (job, chunk)
 // from a counter; the job's own function classifies the item's sign vectors.
@@ -906,16 +907,17 @@ std::string jit_jobs_link(const std::vector<const Diamond *> &tris, std::string 
   const int d = tris[0]->d;
   std::vector<std::string> srcs;
   std::vector<std::vector<std::string>> opts;
-  const std::vector<std::string> o = {"-rdc=true", "-maxrregcount=" + std::to_string(job_max_registers(d))};
+  const int mb = job_min_blocks(d);
+  const std::vector<std::string> o = {"-rdc=true", "-maxrregcount=" + std::to_string(job_max_registers(mb))};
   for (size_t i = 0; i < tris.size(); ++i) {
-    srcs.push_back(jit_job_source(*tris[i], (int)i));
+    srcs.push_back(jit_job_source(*tris[i], (int)i, mb));
     if (srcs.back().empty()) {
       if (log) *log = "no batch source for this degree";
       return {};
     }
     opts.push_back(o);
   }
-  srcs.push_back(jit_jobs_kernel_source(d, (int)tris.size()));
+  srcs.push_back(jit_jobs_kernel_source(d, (int)tris.size(), mb));
   opts.push_back(o);
   std::vector<std::string> cubins;
   std::string clog;
@@ -932,6 +934,7 @@ std::string jit_jobs_link(const std::vector<const Diamond *> &tris, std::string 
 }
 
 cudaError_t jit_jobs_build(const std::vector<std::vector<const Diamond *>> &groups,
+                           const std::vector<int> &min_blocks,
                            std::vector<std::shared_ptr<JitJobsModule>> *mods,
                            std::vector<std::string> *logs) {
   mods->assign(groups.size(), nullptr);
@@ -948,13 +951,14 @@ cudaError_t jit_jobs_build(const std::vector<std::vector<const Diamond *>> &grou
     first[g] = srcs.size();
     if (groups[g].empty()) continue;
     const int d = groups[g][0]->d;
+    const int mb = g < min_blocks.size() && min_blocks[g] > 0 ? min_blocks[g] : job_min_blocks(d);
     const std::vector<std::string> o = {"-rdc=true",
-                                        "-maxrregcount=" + std::to_string(job_max_registers(d))};
+                                        "-maxrregcount=" + std::to_string(job_max_registers(mb))};
     for (size_t i = 0; i < groups[g].size(); ++i) {
-      srcs.push_back(jit_job_source(*groups[g][i], (int)i));
+      srcs.push_back(jit_job_source(*groups[g][i], (int)i, mb));
       opts.push_back(o);
     }
-    srcs.push_back(jit_jobs_kernel_source(d, (int)groups[g].size()));
+    srcs.push_back(jit_jobs_kernel_source(d, (int)groups[g].size(), mb));
     opts.push_back(o);
   }
   first[groups.size()] = srcs.size();
