@@ -258,7 +258,9 @@ bool pack_diamond_tables(const Diamond &D, std::vector<uint32_t> &tables, TableL
   std::vector<uint32_t> vdesc(V), fan, vext(V, kNone | (kNone << 10) | (kNone << 20));
   for (int v = 0; v < V; ++v) {
     const int m = (int)D.fan[v].size();
-    if (m > 127 || m + 1 > tc_pcap(D.d) || fan.size() > 65535 || D.k[v] > 255) return false;
+    if (m > 127 || m + 1 > tc_pcap(D.d) || fan.size() > 65535 || D.k[v] > 255 ||
+        slot[v] >= (int)kNone)
+      return false;
     vdesc[v] = (uint32_t)D.k[v] | ((uint32_t)D.c[v] << 8) | ((uint32_t)m << 9) |
                ((uint32_t)slot[v] << 16);
     for (int n = 0; n < m; ++n) {
@@ -280,6 +282,10 @@ bool pack_diamond_tables(const Diamond &D, std::vector<uint32_t> &tables, TableL
       else return false;
     }
   }
+  // bit 26 of vdesc: vext[v] says something (a flush, an antipodal partner,
+  // a boundary edge); interior vertices skip it
+  for (int v = 0; v < V; ++v)
+    if (vext[v] != (kNone | (kNone << 10) | (kNone << 20))) vdesc[v] |= 1u << 26;
   TableLayout L{};
   L.V = V;
   L.NF = (uint32_t)fan.size();

@@ -634,8 +634,9 @@ __device__ __noinline__ void tc_backend_wide(const TcScratch<K> &S, u32 nl, u32 
 // order of T^diamond; a vertex's label lives in a label slot, reused once no
 // later vertex reads it, so the sweep touches only the slots live at once):
 //   vdesc[V]  bits 0-7 lattice index k(v), bit 8 Eq. 2 parity constant c(v)
-//             (sign(v) = sigma_k ^ c), bits 9-15 fan length m, bits 16-31
-//             v's label slot; v's fan entries follow those of v - 1
+//             (sign(v) = sigma_k ^ c), bits 9-15 fan length m, bits 16-25
+//             v's label slot, bit 26 "vext[v] is not empty"; v's fan
+//             entries follow those of v - 1
 //   fan[NF]   bits 0-9 label slot of the earlier neighbour u, bits 10-17
 //             k(u), bit 18 c(u), bit 19 "u and the previous entry span a
 //             triangle with v"
@@ -666,8 +667,9 @@ __device__ __forceinline__ void tc_sweep_table(const SIG &sig, const u32 *__rest
     const u32 desc = vdesc[v];
     const u32 sv = sig.bit(desc & 255u) ^ ((desc >> 8) & 1u);
     const u32 m = (desc >> 9) & 127u;
-    const u32 x = vext[v];
-    if ((x >> 30) & 1u) {  // the schedule's flush: the same vertex in every lane
+    const bool ext = (desc >> 26) & 1u;  // warp-uniform: most vertices are interior
+    const u32 x = ext ? vext[v] : TC_TAB_NONE | (TC_TAB_NONE << 10) | (TC_TAB_NONE << 20);
+    if (ext && ((x >> 30) & 1u)) {  // the schedule's flush: the same vertex in every lane
       tc_unions(S, np);
       np = 0;
     }
@@ -693,8 +695,9 @@ __device__ __forceinline__ void tc_sweep_table(const SIG &sig, const u32 *__rest
       tc_newlab(S, nl, l0);
       ++nl;
     }
-    *S.lab(K::OFF_LAB, desc >> 16) = (typename TS::lab_t)(lv | (sv << SB));
+    *S.lab(K::OFF_LAB, (desc >> 16) & 1023u) = (typename TS::lab_t)(lv | (sv << SB));
     fs += m;
+    if (!ext) continue;
     if ((x & 1023u) != TC_TAB_NONE) {  // the antipodal partner, reached earlier
       S.word(K::OFF_PEND, np) =
           ((u32)*S.lab(K::OFF_LAB, x & 1023u) & TS::LOW) | (lv << 16) | 0x80000000u;
