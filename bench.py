@@ -199,6 +199,7 @@ def main():
     ap.add_argument("--trips", type=int, default=1 << 15)
     ap.add_argument("--no-stretch", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-configs", action="store_true")
     ap.add_argument("--families", action="store_true")
     ap.add_argument("--occupancies", default="0")
     args = ap.parse_args()
@@ -344,6 +345,8 @@ def main():
         line["plain"] = plain_kernel(eng, tri, ti, stream)
     if not args.no_stretch:
         line["stretch"] = stretch_sweep(eng, tri, stream)
+    if not args.no_configs:
+        line["configs"] = configs_run(eng, ti, stream)
     if not args.no_mixed:
         mx = mixed_run(args.steps, args.warmup)
         mx["alg_frac"] = mx["alg_tops"] * 1e12 / int_peak["peak"]
@@ -356,6 +359,57 @@ def main():
     if pg:
         pg.destroy_process_group()
     return 0
+
+
+def configs_run(eng, ti, stream):
+    """The two plain query configurations, timed with CUDA events:
+    d4_plain: all 2^15 sign vectors of the anti-diagonal triangulation of
+    4*Delta_2 (one u64 word each; bit 1 = a -1 coefficient) in one
+    ts_real_schemes launch (median of 5); d6_plain: 64 seeded regular
+    triangulations of 6*Delta_2, 2^20 materialised splitmix64 sign vectors
+    each (512 MiB of sign words in all), one table-driven ts_real_schemes
+    launch per triangulation, all 64 timed together (median of 3)."""
+    import torch
+
+    def med(fn, reps):
+        out = []
+        for _ in range(reps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            out.append(a.elapsed_time(b))
+        return statistics.median(out)
+
+    t4 = eng.Triangulation(4, ti.standard_triangulation(4))
+    n4 = 1 << 15
+    m4 = torch.arange(n4, dtype=torch.int64, device="cuda")
+    o4 = torch.empty((n4, 1), dtype=torch.int64, device="cuda")
+    f4 = lambda: t4.real_schemes(m4, out=o4, stream=stream, sync=False)  # noqa: E731
+    f4()
+    ms4 = med(f4, 5)
+    t4.sync(stream)
+    tris = [eng.Triangulation(6, e) for e in ti.regular_triangulations(6, 64, seed=6)]
+    n6 = 1 << 20
+    masks = [eng.splitmix_masks(6, k << 20, n6, stream=stream) for k in range(64)]
+    outs = [torch.empty((n6, 1), dtype=torch.int64, device="cuda") for _ in range(64)]
+    for t in tris:
+        t.set_kernel(eng.TS_KERNEL_TABLE)
+
+    def f6():
+        for t, m, o in zip(tris, masks, outs):
+            t.real_schemes(m, out=o, stream=stream, sync=False)
+    f6()
+    ms6 = med(f6, 3)
+    for t in tris:
+        t.sync(stream)
+    return {"d4_plain": {"sign_vectors": n4, "ms": ms4, "value": n4 / (ms4 / 1e3),
+                         "unit": "schemes/s", "launches": 1},
+            "d6_plain": {"triangulations": 64, "sign_vectors": 64 * n6, "ms": ms6,
+                         "value": 64 * n6 / (ms6 / 1e3), "unit": "schemes/s", "launches": 64,
+                         "hbm_bytes": 64 * n6 * 16, "kernel": "table-driven"}}
 
 
 def measure_int_peak(eng, trips):
