@@ -315,10 +315,17 @@ std::string jit_source(const Diamond &D, bool global, int min_blocks) {
   // half labels at d >= 8) in the [snap] region
   for (int w = 0; w < L.snapw; ++w)
     o << "  const u32 snap" << w << " = S.word(TcK::OFF_LPAR, " << w << ");\n";
-  o << "  const u32 osnap = S.word(TcK::OFF_ODD, 0);\n"
-    << "  const u32 nw = (nl_o + TcK::EPW - 1u) / TcK::EPW, nwo = (nl_o + 31u) / 32u;\n"
-    << "  for (u32 w = TcK::SNAPW; w < nw; ++w) S.word(TcK::OFF_SNAP, w) = S.word(TcK::OFF_LPAR, w);\n"
-    << "  for (u32 w = 1; w < nwo; ++w) S.word(TcK::OFF_SNAP + TcK::WLAB, w) = S.word(TcK::OFF_ODD, w);\n";
+  const bool even = d % 2 == 0;  // only even degrees keep odd-cycle flags
+  o << "  const u32 nw = (nl_o + TcK::EPW - 1u) / TcK::EPW;\n"
+    << "  for (u32 w = TcK::SNAPW; w < nw; ++w) S.word(TcK::OFF_SNAP, w) = S.word(TcK::OFF_LPAR, w);\n";
+  if (even)
+    o << "  const u32 osnap = S.word(TcK::OFF_ODD, 0), nwo = (nl_o + 31u) / 32u;\n"
+      << "  for (u32 w = 1; w < nwo; ++w) S.word(TcK::OFF_SNAP + TcK::WLAB, w) = S.word(TcK::OFF_ODD, w);\n";
+  else  // the half-diamonds' crossed boundary edges by their roots: one lookup each per instance
+    o << "  for (u32 i = 0; i < nb_o; ++i) {\n"
+      << "    const u32 e = S.word(TcK::OFF_BPAIR, i);\n"
+      << "    S.word(TcK::OFF_BPAIR, i) = (S.lpar(e & 0xFFFFu) & TcS::LOW) | ((S.lpar(e >> 16) & TcS::LOW) << 16);\n"
+      << "  }\n";
   // The per-lane loop: every instance restores the snapshot, sweeps the
   // middle row and classifies.  Emitted twice: warps whose half-diamonds left
   // at most 32 labels restore from registers only (the common case below
@@ -330,12 +337,14 @@ std::string jit_source(const Diamond &D, bool global, int min_blocks) {
       o << in2 << "S.word(TcK::OFF_LPAR, " << w << ") = snap" << w << ";\n";
     if (with_snap)
       o << in2 << "for (u32 w = TcK::SNAPW; w < nw; ++w) S.word(TcK::OFF_LPAR, w) = S.word(TcK::OFF_SNAP, w);\n";
-    o << in2 << "S.word(TcK::OFF_ODD, 0) = osnap;\n";
-    if (with_snap)
-      o << in2 << "for (u32 w = 1; w < TcK::WODD; ++w)\n"
-        << in2 << "  S.word(TcK::OFF_ODD, w) = w < nwo ? S.word(TcK::OFF_SNAP + TcK::WLAB, w) : 0u;\n";
-    else
-      o << in2 << "for (u32 w = 1; w < TcK::WODD; ++w) S.word(TcK::OFF_ODD, w) = 0u;\n";
+    if (even) {
+      o << in2 << "S.word(TcK::OFF_ODD, 0) = osnap;\n";
+      if (with_snap)
+        o << in2 << "for (u32 w = 1; w < TcK::WODD; ++w)\n"
+          << in2 << "  S.word(TcK::OFF_ODD, w) = w < nwo ? S.word(TcK::OFF_SNAP + TcK::WLAB, w) : 0u;\n";
+      else
+        o << in2 << "for (u32 w = 1; w < TcK::WODD; ++w) S.word(TcK::OFF_ODD, w) = 0u;\n";
+    }
     o << in2 << "nl = nl_o; nb = nb_o; np = 0;\n"
       << in2 << "const u32 sm = slo | ((lane + 32u * j) << ishift);\n";
     // the middle row starts from an empty join list

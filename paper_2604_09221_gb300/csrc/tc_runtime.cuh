@@ -94,7 +94,21 @@ __device__ __forceinline__ u32 tc_find(const TcScratch<K> &S, u32 x, u32 &par) {
   return x;
 }
 
+// Root of x without the parity (odd degrees, where no parity is read).
+template <class K>
+__device__ __forceinline__ u32 tc_find_root(const TcScratch<K> &S, u32 x) {
+  u32 e = S.lpar(x);
+  while ((e & TcScratch<K>::LOW) != x) {
+    x = e & TcScratch<K>::LOW;
+    e = S.lpar(x);
+  }
+  return x;
+}
+
 // Odd-cycle flags of the label sets (valid at set roots), one bit per label.
+// Only even degrees read them (the non-orientable region is the root there);
+// for odd d the root comes from the pseudoline, and neither flags nor the
+// parities of the links are kept.
 template <class K>
 __device__ __forceinline__ u32 tc_odd(const TcScratch<K> &S, u32 l) {
   return (S.word(K::OFF_ODD, l >> 5) >> (l & 31u)) & 1u;
@@ -105,13 +119,20 @@ __device__ __forceinline__ void tc_set_odd(const TcScratch<K> &S, u32 l) {
 }
 template <class K>
 __device__ __forceinline__ void tc_clear_odd(const TcScratch<K> &S) {
+  if constexpr (K::D % 2 == 0) {
 #pragma unroll
-  for (u32 w = 0; w < K::WODD; ++w) S.word(K::OFF_ODD, w) = 0;
+    for (u32 w = 0; w < K::WODD; ++w) S.word(K::OFF_ODD, w) = 0;
+  }
 }
 
 // Join labels a and b with relative orientation parity p.
 template <class K>
 __device__ __forceinline__ void tc_unite(const TcScratch<K> &S, u32 a, u32 b, u32 p) {
+  if constexpr (K::D % 2 == 1) {  // no parity, no odd flags
+    const u32 ra = tc_find_root(S, a), rb = tc_find_root(S, b);
+    if (ra != rb) S.set_lpar(ra < rb ? rb : ra, ra < rb ? ra : rb);
+    return;
+  }
   u32 pa, pb;
   const u32 ra = tc_find(S, a, pa), rb = tc_find(S, b, pb);
   const u32 q = (pa ^ pb ^ p) & 1u;
