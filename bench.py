@@ -716,18 +716,29 @@ def mixed_run(steps, warmup, degrees=(5, 6, 7, 8, 9, 10), per_degree=32, seed=31
     tiles = autotune.autotune(tris, counts, bases, reps=1)
     autotune.apply(batch, tiles)
     stream = torch.cuda.current_stream()
-    for _ in range(max(warmup, 1)):
-        batch.run(graph=True, stream=stream)
+
+    def timed_runs(k):
+        out = []
+        for _ in range(k):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            batch.run(graph=True, stream=stream)
+            b.record(stream)
+            b.synchronize()
+            out.append(a.elapsed_time(b))
+        return out
+    # the degree groups concurrently (forked streams) or one after the other:
+    # the faster order, measured on two runs each, is the one timed
+    order = {}
+    for serial in (False, True):
+        batch.set_serial(serial)
+        timed_runs(max(warmup, 1))
+        order[serial] = min(timed_runs(2))
+    serial = order[True] < order[False]
+    batch.set_serial(serial)
     torch.cuda.synchronize()
-    times = []
-    for _ in range(steps):
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        batch.run(graph=True, stream=stream)
-        b.record(stream)
-        b.synchronize()
-        times.append(a.elapsed_time(b))
+    times = timed_runs(steps)
     for j in range(len(tris)):
         codes, cnt, failed = batch.read(j)
         assert failed == 0 and int(cnt.sum()) == counts[j]
@@ -742,6 +753,8 @@ def mixed_run(steps, warmup, degrees=(5, 6, 7, 8, 9, 10), per_degree=32, seed=31
             "kernels": {str(d): fam[d]["kernel"] for d in degrees},
             "tiles": {str(d): [fam[d]["threads"], fam[d]["chunk"], fam[d]["scratch"]] for d in degrees},
             "build_s": build_s, "alg_tops": ops / (ms / 1e3) / 1e12,
+            "groups": "one after the other" if serial else "concurrent streams",
+            "order_ms": {"concurrent": order[False], "serial": order[True]},
             "gpu_launches_per_step": len(degrees)}
 
 

@@ -238,6 +238,12 @@ void ts_batch_free(ts_batch *batch);
  * all work on the device first (runs already launched use the tile's tables
  * and scratch); the next ts_batch_run with use_graph captures a new graph. */
 ts_status ts_batch_set_tile(ts_batch *batch, int d, int threads, int chunk, int scratch);
+/* How ts_batch_run orders the degree groups' persistent kernels: serial = 0
+ * (default) forks them onto streams of their own, so they run concurrently;
+ * serial = 1 runs them one after the other on the run's stream, each
+ * filling the whole GPU.  Takes effect at the next run (a new graph is
+ * captured).  TS_EINVAL for other values. */
+ts_status ts_batch_set_serial(ts_batch *batch, int serial);
 /* Clear the histograms and run every job, asynchronously on stream.  With
  * use_graph the work (clears, fork, per-degree kernels, join) is captured
  * into a CUDA graph on the first call (and after a tile change) and the graph

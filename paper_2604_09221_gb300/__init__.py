@@ -94,6 +94,7 @@ def _load():
                 "ts_batch_run": ([P, I, P], I),
                 "ts_batch_read": ([P, I, P, P, U64, ctypes.POINTER(U64), ctypes.POINTER(U64), P], I),
                 "ts_batch_set_kernel": ([P, I, I], I),
+                "ts_batch_set_serial": ([P, I], I),
                 "ts_batch_info": ([P, I, ctypes.POINTER(BatchGroupInfo), ctypes.c_char_p,
                                    ctypes.c_size_t], I),
                 "ts_batch_specialized_link": ([I, I, P, P, ctypes.POINTER(ctypes.c_size_t),
@@ -345,6 +346,11 @@ class Batch:
         """Kernel family of the degree-d group (ts_batch_set_kernel): TS_KERNEL_TABLE,
         TS_KERNEL_SPECIALIZED (compiled now if needed) or TS_KERNEL_AUTO."""
         _check(_lib.ts_batch_set_kernel(self._h, int(d), int(kind)), "ts_batch_set_kernel")
+
+    def set_serial(self, serial: bool):
+        """Run the degree groups one after the other (True) or concurrently on
+        streams of their own (False, the default): ts_batch_set_serial."""
+        _check(_lib.ts_batch_set_serial(self._h, int(bool(serial))), "ts_batch_set_serial")
 
     def info(self, d: int) -> dict:
         """Kernel family, tile and launch resources of the degree-d group

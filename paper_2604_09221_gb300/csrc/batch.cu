@@ -277,6 +277,7 @@ struct ts_batch {
   cudaGraphExec_t exec = nullptr;
   int device = 0;
   std::vector<ts_tri *> tris;  // triangulation of every job
+  bool serial = false;         // degree groups one after the other (else concurrent streams)
 };
 
 namespace {
@@ -353,11 +354,15 @@ cudaError_t launch_group(ts_batch *b, ts_batch::Group &g, cudaStream_t st) {
 
 // The whole batch as stream work on `st`: clear, fork, one kernel per degree, join.
 cudaError_t enqueue(ts_batch *b, cudaStream_t st) {
-  const size_t nj = b->jobs.size();
   cudaError_t e = cudaMemsetAsync(b->d_keys, 0, b->key_words * 8, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counts, 0, b->count_words * 8, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, 4, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_failed, 0, 8, st);
+  if (b->serial) {  // one degree after the other, each persistent kernel on the whole GPU
+    for (auto &g : b->groups)
+      if (e == cudaSuccess) e = launch_group(b, g, st);
+    return e;
+  }
   if (e == cudaSuccess) e = cudaEventRecord(b->fork, st);
   for (auto &g : b->groups) {
     if (e == cudaSuccess) e = cudaStreamWaitEvent(g.stream, b->fork, 0);
@@ -595,6 +600,18 @@ ts_status ts_batch_set_kernel(ts_batch *b, int d, int kind) {
     return ok ? TS_OK : TS_ECUDA;
   }
   return TS_EINVAL;
+}
+
+ts_status ts_batch_set_serial(ts_batch *b, int serial) {
+  if (!b || serial < 0 || serial > 1) return TS_EINVAL;
+  if (b->serial != (serial != 0) && b->exec) {
+    cudaError_t e = cudaDeviceSynchronize();  // a graph launched before may still run
+    if (e != cudaSuccess) return cuda_st(e);
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  b->serial = serial != 0;
+  return TS_OK;
 }
 
 ts_status ts_batch_run(ts_batch *b, int use_graph, void *stream) {

@@ -89,6 +89,26 @@ def standard_triangulation(d: int) -> np.ndarray:
     return _edges_from_triangles(tris)
 
 
+def fan_triangulation(d: int) -> np.ndarray:
+    """A unimodular triangulation of d*Delta_2 (d >= 2) with a vertex of high
+    degree, as an (E, 4) int32 edge array: in the strip 0 <= i <= 1, (0, 0)
+    is joined to every (1, j), j < d, and to (0, 1), and (1, d - 1) to every
+    (0, j), j >= 1; the rest, (d-1)*Delta_2 shifted by (1, 0), is split by
+    anti-diagonals.  (0, 0) then has d + 1 neighbours in each quadrant of the
+    reflected triangulation, 4d in all."""
+    if d < 2:
+        raise ValueError("the fan triangulation needs d >= 2")
+    tris = [((0, 0), (1, j), (1, j + 1)) for j in range(d - 1)]
+    tris.append(((0, 0), (1, d - 1), (0, 1)))
+    tris += [((0, j), (1, d - 1), (0, j + 1)) for j in range(1, d)]
+    for j in range(d - 1):
+        for i in range(1, d - j):
+            tris.append(((i, j), (i + 1, j), (i, j + 1)))
+            if i + j + 2 <= d:
+                tris.append(((i + 1, j), (i + 1, j + 1), (i, j + 1)))
+    return _edges_from_triangles(tris)
+
+
 def _lifting(d: int, seed: int, tri_id: int, attempt: int) -> dict:
     base = splitmix64_int((seed * 1_000_003 + tri_id) & _MASK64)
     base = splitmix64_int(base ^ ((attempt * _GOLDEN) & _MASK64))

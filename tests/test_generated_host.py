@@ -124,11 +124,15 @@ def table_sweep_exe(tmp_path_factory):
 def test_table_sweep_on_the_host(table_sweep_exe, tmp_path, d):
     """The table-driven sweep (both back ends, multi-word sign vectors and
     codes) compiled for the host, on the tables host.cpp builds, against the
-    oracle: random and special sign vectors, the standard triangulation and
-    (d >= 3) a regular one."""
+    oracle: random and special sign vectors, the standard triangulation,
+    (d >= 3) a regular one and (d >= 2) the fan triangulation, whose origin
+    has 4d - 1 earlier neighbours in T^diamond (the entry-by-entry path for
+    fans longer than 32 from d = 9)."""
     cases = [("standard", ti.standard_triangulation(d))]
     if d >= 3:
         cases.append(("regular", ti.regular_triangulation(d, seed=100 + d)))
+    if d >= 2:
+        cases.append(("fan", ti.fan_triangulation(d)))
     for name, edges in cases:
         np.savetxt(tmp_path / "tri.txt", edges, fmt="%d")
         out = subprocess.run([str(table_sweep_exe), str(d), str(tmp_path / "tri.txt"), "600"],

@@ -175,7 +175,8 @@ def test_specialised_batch_matches_oracle(eng, orc):
     job's histogram and stored codes equal the oracle's on the same
     splitmix64 sign vectors, in one graph launch, on replay, after a chunk
     change, and after a switch to the table-driven kernel and back; a tile
-    of another block size is refused."""
+    of another block size is refused; the degree groups run one after the
+    other give the same results as run concurrently."""
     import torch
     degrees = (3, 5, 6, 7, 8, 9, 10, 11, 12)
     jobs = specialised_jobs(eng, degrees, 700, 6000)
@@ -222,6 +223,11 @@ def test_specialised_batch_matches_oracle(eng, orc):
     assert hists() == got
     batch.set_kernel(7, eng.TS_KERNEL_SPECIALIZED)
     batch.run(graph=True)
+    assert hists() == got
+    batch.set_serial(True)     # degree groups one after the other
+    batch.run(graph=True)
+    assert hists() == got
+    batch.run(graph=False)
     assert hists() == got
 
 

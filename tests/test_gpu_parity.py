@@ -84,6 +84,28 @@ def test_random_sign_vectors(eng, orc, d, kind):
 
 
 @pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("d", [8, 9])
+def test_fan_triangulation(eng, orc, d, kind):
+    """A triangulation whose origin has 4d - 1 earlier neighbours in
+    T^diamond (more than 32 from d = 9: the table-driven sweep's
+    entry-by-entry path), random sign vectors and a sweep of a range, both
+    kernel families, against the oracle."""
+    e = ti.fan_triangulation(d)
+    masks = ti.random_masks(20011, d, 77, stream=d)
+    tri = load(eng, d, e, kind)
+    got = gpu_codes(eng, tri, masks)
+    want = orc.real_schemes(d, orc.triangles(d, e), masks)
+    assert (got == want).all()
+    h = eng.Histogram(4096, tri.code_words)
+    lo = 123456
+    eng.enumerate_schemes(tri, lo, lo + 5000, h)
+    codes, counts, failed = h.read()
+    assert failed == 0
+    ref = orc.real_schemes(d, orc.triangles(d, e), np.arange(lo, lo + 5000, dtype=np.uint64).reshape(-1, 1))
+    assert dict(zip(codes[:, 0].tolist(), counts.tolist())) == dict(collections.Counter(ref[:, 0].tolist()))
+
+
+@pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("name", ["bow_tie", "rank016", "rank015"])
 def test_fig2_triangulations(eng, orc, name, kind):
     e = np.loadtxt(os.path.join(GOLDEN, f"fig2_{name}.edges"), dtype=np.int32, comments="#")
