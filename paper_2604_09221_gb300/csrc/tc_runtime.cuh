@@ -695,58 +695,26 @@ __device__ __forceinline__ void tc_sweep_table(const SIG &sig, const u32 *__rest
       np = 0;
     }
     constexpr u32 SB = 8u * K::LBYTES - 1u;  // the sign bit of a [lab] entry
-    u32 lv;
-    if (m <= 32u) {  // warp-uniform: every fan but the longest at high degree
-      // same-sign entries (bit i: entry i has v's sign) straight from the
-      // sign vector, and the fan's link bits; no label is read for them
-      u32 same = 0, link = 0;
-      for (u32 i = 0; i < m; ++i) {
-        const u32 f = fan[fs + i];
-        same |= ((sig.bit((f >> 10) & 255u) ^ (f >> 18) ^ sv ^ 1u) & 1u) << i;
-        link |= ((f >> 19) & 1u) << i;
-      }
-      // a run of same-sign entries starts at i unless entry i - 1 has the
-      // sign too and spans a triangle with i and v
-      const u32 runs = same & ~(link & (same << 1));
-      // v's label: that of its first same-sign entry, or a fresh one whose
-      // cand is entry 0's label
-      const u32 i0 = same ? (u32)__ffs(same) - 1u : 0u;
-      const u32 lu0 = m ? ((u32)*S.lab(K::OFF_LAB, fan[fs + i0] & 1023u) & TS::LOW) : TS::NONE;
-      lv = lu0;
-      if (!same) {
-        lv = nl;
-        tc_newlab(S, nl, lu0);
-        ++nl;
-      }
-      // every further run joins its label with v's
-      for (u32 r = runs & (runs - 1u); r; r &= r - 1u) {
-        const u32 lu = (u32)*S.lab(K::OFF_LAB, fan[fs + (u32)__ffs(r) - 1u] & 1023u) & TS::LOW;
-        S.word(K::OFF_PEND, np) = lv | (lu << 16);
-        ++np;
-      }
-    } else {  // a longer fan: entry by entry
-      u32 l0 = TS::NONE, any = 0, prev = 0;
-      lv = 0;
-      for (u32 i = 0; i < m; ++i) {
-        const u32 f = fan[fs + i];
-        const u32 raw = *S.lab(K::OFF_LAB, f & 1023u);
-        const u32 lu = raw & TS::LOW;
-        const u32 e = (raw >> SB) ^ sv ^ 1u;
-        const u32 st = e & ~(((f >> 19) & 1u) & prev) & 1u;  // e starts a run of the fan
-        l0 = i == 0 ? lu : l0;
-        // a run after the first: join its label with the vertex's label
-        // (a predicated store: no branch, and no write when nothing joins)
-        if (st & any) S.word(K::OFF_PEND, np) = lv | (lu << 16);
-        np += st & any;
-        lv = any ? lv : (st ? lu : lv);
-        any |= st;
-        prev = e;
-      }
-      if (!any) {
-        lv = nl;
-        tc_newlab(S, nl, l0);
-        ++nl;
-      }
+    u32 lv = 0, l0 = TS::NONE, any = 0, prev = 0;
+    for (u32 i = 0; i < m; ++i) {
+      const u32 f = fan[fs + i];
+      const u32 raw = *S.lab(K::OFF_LAB, f & 1023u);
+      const u32 lu = raw & TS::LOW;
+      const u32 e = (raw >> SB) ^ sv ^ 1u;
+      const u32 st = e & ~(((f >> 19) & 1u) & prev) & 1u;  // e starts a run of the fan
+      l0 = i == 0 ? lu : l0;
+      // a run after the first: join its label with the vertex's label
+      // (a predicated store: no branch, and no write when nothing joins)
+      if (st & any) S.word(K::OFF_PEND, np) = lv | (lu << 16);
+      np += st & any;
+      lv = any ? lv : (st ? lu : lv);
+      any |= st;
+      prev = e;
+    }
+    if (!any) {
+      lv = nl;
+      tc_newlab(S, nl, l0);
+      ++nl;
     }
     *S.lab(K::OFF_LAB, (desc >> 16) & 1023u) = (typename TS::lab_t)(lv | (sv << SB));
     fs += m;

@@ -126,8 +126,8 @@ def test_table_sweep_on_the_host(table_sweep_exe, tmp_path, d):
     codes) compiled for the host, on the tables host.cpp builds, against the
     oracle: random and special sign vectors, the standard triangulation,
     (d >= 3) a regular one and (d >= 2) the fan triangulation, whose origin
-    has 4d - 1 earlier neighbours in T^diamond (the entry-by-entry path for
-    fans longer than 32 from d = 9)."""
+    has 4d - 1 earlier neighbours in T^diamond (the longest fans the join
+    list's flush schedule has to fit)."""
     cases = [("standard", ti.standard_triangulation(d))]
     if d >= 3:
         cases.append(("regular", ti.regular_triangulation(d, seed=100 + d)))

@@ -87,9 +87,9 @@ def test_random_sign_vectors(eng, orc, d, kind):
 @pytest.mark.parametrize("d", [8, 9])
 def test_fan_triangulation(eng, orc, d, kind):
     """A triangulation whose origin has 4d - 1 earlier neighbours in
-    T^diamond (more than 32 from d = 9: the table-driven sweep's
-    entry-by-entry path), random sign vectors and a sweep of a range, both
-    kernel families, against the oracle."""
+    T^diamond (a fan far longer than a regular triangulation's), random sign
+    vectors and a sweep of a range, both kernel families, against the
+    oracle."""
     e = ti.fan_triangulation(d)
     masks = ti.random_masks(20011, d, 77, stream=d)
     tri = load(eng, d, e, kind)

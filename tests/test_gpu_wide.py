@@ -52,8 +52,8 @@ def hist_rows(hist):
 @pytest.mark.parametrize("d", WIDE)
 def test_random_sign_vectors_wide(eng, orc, d):
     """Random sign vectors of the standard, a regular and the fan
-    triangulation (its origin has 4d - 1 earlier neighbours: fans longer
-    than 32 take the sweep's entry-by-entry path) against the oracle."""
+    triangulation (its origin has 4d - 1 earlier neighbours) against the
+    oracle."""
     n = 20011 if d <= 12 else 4099   # several blocks and a ragged tail
     for idx, e in enumerate([ti.standard_triangulation(d), ti.regular_triangulation(d, seed=40 + d),
                              ti.fan_triangulation(d)]):
