@@ -135,7 +135,7 @@ ts_status ts_set_kernel(ts_tri *tri, int kind);
 ts_status ts_set_scratch(ts_tri *tri, int where);
 
 /* Resident blocks per SM the specialised kernels are compiled for (their
- * register budget): 1..16, or 0 for the default (with global scratch 6, 5
+ * register budget): 1..16, or 0 for the default (with global scratch 7, 6
  * and 4 blocks of 128 threads for d = 7, 8, 9 and 4 otherwise; 2 with shared
  * scratch).  Drops kernels already built for tri.  A batch's specialised
  * code (ts_batch_info) takes the largest value over its group's

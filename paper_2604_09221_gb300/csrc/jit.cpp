@@ -426,12 +426,12 @@ std::string jit_compile_uncached(const std::string &src, std::string *log,
 // Configuration of the specialised kernels of a triangulation.  Scratch:
 // global from d = 7 unless asked otherwise (TS_SCRATCH_*); blocks per SM from
 // ts_set_occupancy, else the register budget measured fastest on GB300 for
-// the degree (d = 7: 6 blocks of 128 threads, 80 registers; d = 8: 5, 96;
+// the degree (d = 7: 7 blocks of 128 threads, 72 registers; d = 8: 6, 80;
 // d = 9: 4, 128), 4 for other degrees with global scratch, 2 with shared.
 void jit_config(int d, int scratch, int occupancy, bool *global, int *min_blocks) {
   *global = scratch == TS_SCRATCH_GLOBAL || (scratch == TS_SCRATCH_AUTO && d >= kGlobalScratchFrom);
   int def = 2;
-  if (*global) def = d == 7 ? 6 : d == 8 ? 5 : 4;
+  if (*global) def = d == 7 ? 7 : d == 8 ? 6 : 4;
   *min_blocks = occupancy > 0 ? occupancy : def;
 }
 
