@@ -234,7 +234,10 @@ void ts_batch_free(ts_batch *batch);
  * with shared scratch the block's scratch must fit shared memory), sign
  * vectors per work item (a multiple of threads) and scratch placement
  * (TS_SCRATCH_*; global scratch is allocated here, grid x threads x
- * scratch words).  Returns TS_EINVAL for tiles that do not fit.  Waits for
+ * scratch words).  Returns TS_EINVAL for tiles that do not fit, and for a
+ * specialised group (ts_batch_info) any block size but 128 or shared
+ * scratch: its code is compiled for 128-thread blocks and global scratch.
+ * Waits for
  * all work on the device first (runs already launched use the tile's tables
  * and scratch); the next ts_batch_run with use_graph captures a new graph. */
 ts_status ts_batch_set_tile(ts_batch *batch, int d, int threads, int chunk, int scratch);

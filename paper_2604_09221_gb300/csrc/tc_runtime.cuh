@@ -696,9 +696,8 @@ __device__ __forceinline__ void tc_sweep_table(const SIG &sig, const u32 *__rest
     }
     constexpr u32 SB = 8u * K::LBYTES - 1u;  // the sign bit of a [lab] entry
     u32 lv = 0, l0 = TS::NONE, any = 0, prev = 0;
-    for (u32 i = 0; i < m; ++i) {
-      const u32 f = fan[fs + i];
-      const u32 raw = *S.lab(K::OFF_LAB, f & 1023u);
+    // one fan entry: its label and sign from the entry's label slot
+    auto entry = [&](u32 i, u32 f, u32 raw) {
       const u32 lu = raw & TS::LOW;
       const u32 e = (raw >> SB) ^ sv ^ 1u;
       const u32 st = e & ~(((f >> 19) & 1u) & prev) & 1u;  // e starts a run of the fan
@@ -710,6 +709,24 @@ __device__ __forceinline__ void tc_sweep_table(const SIG &sig, const u32 *__rest
       lv = any ? lv : (st ? lu : lv);
       any |= st;
       prev = e;
+    };
+    // from d = 12 (scratch-latency-bound) the first four entries' labels are
+    // loaded before any is used, so the loads overlap (m is the same in every
+    // lane); at lower degrees the extra registers cost more than that gains
+    constexpr u32 PRE = K::D >= 12 ? 4u : 0u;
+    u32 fpre[PRE > 0 ? PRE : 1], rpre[PRE > 0 ? PRE : 1];
+#pragma unroll
+    for (u32 i = 0; i < PRE; ++i)
+      if (i < m) {
+        fpre[i] = fan[fs + i];
+        rpre[i] = *S.lab(K::OFF_LAB, fpre[i] & 1023u);
+      }
+#pragma unroll
+    for (u32 i = 0; i < PRE; ++i)
+      if (i < m) entry(i, fpre[i], rpre[i]);
+    for (u32 i = PRE; i < m; ++i) {
+      const u32 f = fan[fs + i];
+      entry(i, f, *S.lab(K::OFF_LAB, f & 1023u));
     }
     if (!any) {
       lv = nl;
