@@ -106,18 +106,24 @@ int ts_code_words(const ts_tri *tri);
 ts_status ts_real_schemes(const ts_tri *tri, const uint64_t *signs, uint64_t n,
                           uint64_t *out_codes, void *stream);
 
-/* Kernel families (ts_set_kernel).  Both compute the same codes.
+/* Kernel families (ts_set_kernel).  All compute the same codes.
  *   TS_KERNEL_TABLE: one generic kernel per degree; the triangulation's
  *     tables are staged into shared memory by a bulk copy in every block.
  *   TS_KERNEL_SPECIALIZED: a kernel generated for this triangulation (its
  *     structure compiled into the instruction stream) with NVRTC on first use;
  *     d <= 9 only (one sign word), TS_EUNSUPPORTED above.
+ *   TS_KERNEL_WARP: one generic kernel per degree in which a whole warp
+ *     classifies one sign vector at a time (lock-free union-find over the
+ *     edges of T^diamond, region tree and code in the warp's shared memory;
+ *     no global scratch).  ts_real_schemes and ts_enumerate only; batches
+ *     and ts_enumerate_noalloc run the other families.
  *   TS_KERNEL_AUTO (default): specialised for ts_enumerate and for batches of
  *     at least 65536 instances when d <= 9, table-driven otherwise or if the
  *     specialised kernel cannot be built. */
 #define TS_KERNEL_AUTO 0
 #define TS_KERNEL_TABLE 1
 #define TS_KERNEL_SPECIALIZED 2
+#define TS_KERNEL_WARP 3
 ts_status ts_set_kernel(ts_tri *tri, int kind);
 
 /* Where the kernels keep their per-instance scratch (labels, union-find,

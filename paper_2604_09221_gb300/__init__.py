@@ -23,6 +23,7 @@ TS_ENUM_SPLITMIX = 4
 TS_KERNEL_AUTO = 0
 TS_KERNEL_TABLE = 1
 TS_KERNEL_SPECIALIZED = 2
+TS_KERNEL_WARP = 3
 TS_SCRATCH_AUTO = 0
 TS_SCRATCH_SHARED = 1
 TS_SCRATCH_GLOBAL = 2
@@ -178,7 +179,7 @@ class Triangulation:
             pass
 
     def set_kernel(self, kind: int):
-        """TS_KERNEL_AUTO / TS_KERNEL_TABLE / TS_KERNEL_SPECIALIZED."""
+        """TS_KERNEL_AUTO / TS_KERNEL_TABLE / TS_KERNEL_SPECIALIZED / TS_KERNEL_WARP."""
         _check(_lib.ts_set_kernel(self._h, int(kind)), "ts_set_kernel")
 
     def set_scratch(self, where: int):

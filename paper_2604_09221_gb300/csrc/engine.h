@@ -32,6 +32,17 @@ struct TableLayout {
   uint32_t words;  // padded to a multiple of 4 (16-byte TMA granule)
 };
 
+// Tables of the warp-per-instance kernels (32-bit words, vertex ids in the
+// sweep order of T^diamond): wv[V] = k(v) (8 bits) | c(v) << 8 | the first
+// earlier neighbour of v << 9 (10 bits, 1023: none); wedge[E] = u | v << 16
+// for every edge u < v; wanti[2d] and wbedge[2d] = a | b << 16 for the
+// antipodal pairs and one boundary edge of each antipodal pair of boundary
+// edges.
+struct WarpLayout {
+  uint32_t V, E, nanti, nbedge;
+  uint32_t off_v, off_e, off_anti, off_bedge;
+  uint32_t words;  // padded to a multiple of 4
+};
 // Device error word bits.
 enum : uint32_t {
   kErrInternal = 1u,   // invariant violated (root, tree, scratch)
@@ -56,6 +67,8 @@ struct JitModule;  // compiled specialised kernels (jit.cpp)
 
 // Tables of the table-driven sweep (host.cpp; format in tc_runtime.cuh).
 bool pack_diamond_tables(const Diamond &D, std::vector<uint32_t> &tables, TableLayout &lay);
+// Tables of the warp-per-instance kernels (host.cpp; format at WarpLayout).
+bool pack_warp_tables(const Diamond &D, std::vector<uint32_t> &tables, WarpLayout &lay);
 // Label slot of every vertex in the table-driven sweep (a slot is reused once
 // its vertex has no later reader) and, in *nslots, how many slots are used.
 std::vector<int> lab_slots(const Diamond &D, int *nslots);
@@ -77,6 +90,9 @@ struct ts_tri {
   tcurve::TableLayout lay{};
   std::vector<uint32_t> host_tables;
   uint32_t *d_tables = nullptr;  // lay.words words, 16-byte aligned
+  tcurve::WarpLayout wlay{};
+  std::vector<uint32_t> host_wtables;
+  uint32_t *d_wtables = nullptr;  // wlay.words words (warp-per-instance kernels)
   uint32_t *d_err = nullptr;     // device error word (scratch, owned here)
   tcurve::Diamond dia;
   int kernel = 0;                // TS_KERNEL_*
@@ -108,6 +124,12 @@ cudaError_t launch_real_schemes(const ts_tri *tri, const uint64_t *signs, uint64
 // allow_global = false keeps the scratch in shared memory (no allocation).
 cudaError_t launch_enumerate(const ts_tri *tri, uint64_t lo, uint64_t hi, uint32_t flags,
                              ts_hist *hist, cudaStream_t stream, bool allow_global = true);
+// Warp-per-instance kernels (warp_kernels.cu, TS_KERNEL_WARP): the whole
+// scratch in shared memory, so they allocate nothing either.
+cudaError_t launch_real_schemes_warp(const ts_tri *tri, const uint64_t *signs, uint64_t n,
+                                     uint64_t *codes, cudaStream_t stream);
+cudaError_t launch_enumerate_warp(const ts_tri *tri, uint64_t lo, uint64_t hi, uint32_t flags,
+                                  ts_hist *hist, cudaStream_t stream);
 cudaError_t launch_hist_clear(ts_hist *hist, cudaStream_t stream);
 cudaError_t launch_selftest_wait(unsigned long long iters, uint32_t *err, cudaStream_t stream);
 // Pack the occupied slots of the table into d_ckeys / d_ccnt (count flags

@@ -300,12 +300,42 @@ bool pack_diamond_tables(const Diamond &D, std::vector<uint32_t> &tables, TableL
   lay = L;
   return true;
 }
+bool pack_warp_tables(const Diamond &D, std::vector<uint32_t> &tables, WarpLayout &lay) {
+  const int V = D.V;
+  if (V > 1022) return false;
+  std::vector<uint32_t> wv(V), wedge;
+  for (int v = 0; v < V; ++v) {
+    const uint32_t first = D.fan[v].empty() ? 1023u : (uint32_t)D.fan[v][0];
+    wv[v] = (uint32_t)D.k[v] | ((uint32_t)D.c[v] << 8) | (first << 9);
+    for (int u : D.fan[v]) wedge.push_back((uint32_t)u | ((uint32_t)v << 16));
+  }
+  WarpLayout L{};
+  L.V = V;
+  L.E = (uint32_t)wedge.size();
+  L.nanti = (uint32_t)D.anti.size();
+  L.nbedge = (uint32_t)D.bedge.size();
+  L.off_v = 0;
+  L.off_e = L.off_v + V;
+  L.off_anti = L.off_e + L.E;
+  L.off_bedge = L.off_anti + L.nanti;
+  L.words = (L.off_bedge + L.nbedge + 3) & ~3u;
+  tables.assign(L.words, 0);
+  std::copy(wv.begin(), wv.end(), tables.begin() + L.off_v);
+  std::copy(wedge.begin(), wedge.end(), tables.begin() + L.off_e);
+  for (uint32_t i = 0; i < L.nanti; ++i)
+    tables[L.off_anti + i] = (uint32_t)D.anti[i].first | ((uint32_t)D.anti[i].second << 16);
+  for (uint32_t i = 0; i < L.nbedge; ++i)
+    tables[L.off_bedge + i] = (uint32_t)D.bedge[i].first | ((uint32_t)D.bedge[i].second << 16);
+  lay = L;
+  return true;
+}
 }  // namespace tcurve
 
 namespace {
 
 bool pack_tables(const Diamond &D, ts_tri *t) {
   if (!pack_diamond_tables(D, t->host_tables, t->lay)) return false;
+  if (!pack_warp_tables(D, t->host_wtables, t->wlay)) return false;
   t->V = D.V;
   return true;
 }
@@ -388,6 +418,10 @@ ts_status ts_load_triangulation(int d, const int32_t *edges_ij, int n_edges, ts_
   if (e == cudaSuccess)
     e = cudaMemcpy(t->d_tables, t->host_tables.data(), t->lay.words * sizeof(uint32_t),
                    cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&t->d_wtables, t->wlay.words * sizeof(uint32_t));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(t->d_wtables, t->host_wtables.data(), t->wlay.words * sizeof(uint32_t),
+                   cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&t->d_err, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemset(t->d_err, 0, sizeof(uint32_t));
   if (e != cudaSuccess) {
@@ -403,6 +437,7 @@ void ts_free_triangulation(ts_tri *t) {
   if (!t) return;
   jit_release(t);
   if (t->d_tables) cudaFree(t->d_tables);
+  if (t->d_wtables) cudaFree(t->d_wtables);
   if (t->d_err) cudaFree(t->d_err);
   delete t;
 }
@@ -416,7 +451,8 @@ namespace {
 // Kernel choice: the specialised kernel for sweeps and large batches (AUTO),
 // the table-driven kernel otherwise or when specialisation is unavailable.
 bool want_specialised(ts_tri *t, uint64_t n, bool sweep) {
-  if (t->kernel == TS_KERNEL_TABLE || t->d > kMaxSpecialized) return false;
+  if (t->kernel == TS_KERNEL_TABLE || t->kernel == TS_KERNEL_WARP || t->d > kMaxSpecialized)
+    return false;
   if (t->kernel == TS_KERNEL_SPECIALIZED) return true;
   if (!sweep && n < (1u << 16)) return false;
   return jit_prepare(t) == cudaSuccess;
@@ -428,13 +464,15 @@ ts_status ts_real_schemes(const ts_tri *tc, const uint64_t *signs, uint64_t n, u
   if (!tc || (n && (!signs || !codes))) return TS_EINVAL;
   if (n == 0) return TS_OK;
   ts_tri *t = const_cast<ts_tri *>(tc);  // only the lazily compiled kernel cache changes
+  if (t->kernel == TS_KERNEL_WARP)
+    return cuda_status(launch_real_schemes_warp(t, signs, n, codes, (cudaStream_t)stream));
   if (want_specialised(t, n, false))
     return cuda_status(launch_real_schemes_jit(t, signs, n, codes, (cudaStream_t)stream));
   return cuda_status(launch_real_schemes(t, signs, n, codes, (cudaStream_t)stream));
 }
 
 ts_status ts_set_kernel(ts_tri *t, int kind) {
-  if (!t || kind < TS_KERNEL_AUTO || kind > TS_KERNEL_SPECIALIZED) return TS_EINVAL;
+  if (!t || kind < TS_KERNEL_AUTO || kind > TS_KERNEL_WARP) return TS_EINVAL;
   if (kind == TS_KERNEL_SPECIALIZED && t->d > kMaxSpecialized) return TS_EUNSUPPORTED;
   t->kernel = kind;
   return TS_OK;
@@ -618,6 +656,8 @@ ts_status ts_enumerate(const ts_tri *t, uint64_t lo, uint64_t hi, uint32_t flags
   if (!(flags & TS_ENUM_SPLITMIX) && free_bits < 64 && hi > (1ull << free_bits)) return TS_EINVAL;
   if (lo == hi) return TS_OK;
   ts_tri *tm = const_cast<ts_tri *>(t);
+  if (tm->kernel == TS_KERNEL_WARP)
+    return cuda_status(launch_enumerate_warp(tm, lo, hi, flags, h, (cudaStream_t)stream));
   if (want_specialised(tm, hi - lo, true))
     return cuda_status(launch_enumerate_jit(tm, lo, hi, flags, h, (cudaStream_t)stream));
   return cuda_status(launch_enumerate(t, lo, hi, flags, h, (cudaStream_t)stream));

@@ -457,71 +457,20 @@ __device__ __forceinline__ int tc_cmp(const TcScratch<K> &S, u32 off, u32 pa, u3
   return 0;
 }
 
+// The canonical code of a region tree (wide back end, steps after the
+// parents): on entry wpar[r] (r = 1 .. R-1) is the parent of region r in the
+// tree hanging from region 0 (parent(r) < r) and root is the region the tree
+// is rooted at (the non-orientable region, or the pseudoline's); re-roots
+// the tree there, builds first-child / next-sibling links and writes the
+// AHU code of the rooted tree to code[0 .. CW-1] (all zero and err set on
+// failure).  Shared by tc_backend_wide and the warp-per-instance kernels.
 template <class K>
-__device__ __noinline__ void tc_backend_wide(const TcScratch<K> &S, u32 nl, u32 nb, u32 &err,
-                                             u64 *code) {
+__device__ __noinline__ void tc_wide_tree_code(const TcScratch<K> &S, u32 R, int root, u32 &err,
+                                               u64 *code) {
   constexpr u32 NONE8 = 0xFFu, ENT_CAP = K::RMAX / 2 + 2, ABITS = 32 * (K::WARENA - 3);
-  typedef TcScratch<K> TS;
 #pragma unroll
   for (u32 w = 0; w < K::CW; ++w) code[w] = 0;
-  // 1. region ids over lpar (label order), root flags, smallest labels
-  u32 R = 0, nodd = 0;
-  int root = -1;
-  for (u32 l = 0; l < nl; ++l) {
-    const u32 p = S.lpar(l) & TS::LOW;
-    const u32 is_root = p == l;
-    const u32 rp = S.lpar(p);
-    if (is_root) {
-      if (R >= K::RMAX) {
-        err |= TC_ERR_OVERFLOW;
-        return;
-      }
-      if (K::D % 2 == 0 && tc_odd(S, l)) {
-        ++nodd;
-        root = (int)R;
-      }
-      *S.half(K::OFF_RLAB, R) = (u16)l;
-    }
-    S.set_lpar(l, is_root ? R : rp);
-    R += is_root;
-  }
-  // 2. root
-  if (K::D % 2 == 0) {
-    if (nodd != 1) {
-      err |= TC_ERR_INTERNAL;
-      return;
-    }
-  } else {
-    for (u32 i = 0; i < nb; ++i) {
-      const u32 e = S.word(K::OFF_BPAIR, i);
-      const u32 ra = S.lpar(e & 0xFFFFu), rb = S.lpar(e >> 16);
-      if (ra != rb) continue;
-      if (root >= 0 && root != (int)ra) {
-        err |= TC_ERR_INTERNAL;
-        return;
-      }
-      root = (int)ra;
-    }
-    if (root < 0) {
-      err |= TC_ERR_INTERNAL;
-      return;
-    }
-  }
-  // 3. the tree hanging from region 0 (parent(r) < r), then re-rooted
   *S.byte(K::OFF_WPAR, 0) = (u8)NONE8;
-  for (u32 r = 1; r < R; ++r) {
-    const u32 c = S.cand(*S.half(K::OFF_RLAB, r)) & TS::LOW;
-    if (c == TS::NONE) {
-      err |= TC_ERR_INTERNAL;
-      return;
-    }
-    const u32 p = S.lpar(c);
-    if (p >= r) {
-      err |= TC_ERR_INTERNAL;
-      return;
-    }
-    *S.byte(K::OFF_WPAR, r) = (u8)p;
-  }
   for (u32 x = (u32)root, prev = NONE8, it = 0; it < R; ++it) {
     const u32 nx = *S.byte(K::OFF_WPAR, x);
     *S.byte(K::OFF_WPAR, x) = (u8)prev;
@@ -647,6 +596,74 @@ __device__ __noinline__ void tc_backend_wide(const TcScratch<K> &S, u32 nl, u32 
     else if (hiend > 0) code[j] = tc_get64(S, K::OFF_WTEMP, 0) >> (64 - hiend);
   }
   code[qroot >> 6] |= 1ull << (qroot & 63u);
+}
+
+template <class K>
+__device__ __noinline__ void tc_backend_wide(const TcScratch<K> &S, u32 nl, u32 nb, u32 &err,
+                                             u64 *code) {
+  constexpr u32 NONE8 = 0xFFu;
+  typedef TcScratch<K> TS;
+#pragma unroll
+  for (u32 w = 0; w < K::CW; ++w) code[w] = 0;
+  // 1. region ids over lpar (label order), root flags, smallest labels
+  u32 R = 0, nodd = 0;
+  int root = -1;
+  for (u32 l = 0; l < nl; ++l) {
+    const u32 p = S.lpar(l) & TS::LOW;
+    const u32 is_root = p == l;
+    const u32 rp = S.lpar(p);
+    if (is_root) {
+      if (R >= K::RMAX) {
+        err |= TC_ERR_OVERFLOW;
+        return;
+      }
+      if (K::D % 2 == 0 && tc_odd(S, l)) {
+        ++nodd;
+        root = (int)R;
+      }
+      *S.half(K::OFF_RLAB, R) = (u16)l;
+    }
+    S.set_lpar(l, is_root ? R : rp);
+    R += is_root;
+  }
+  // 2. root
+  if (K::D % 2 == 0) {
+    if (nodd != 1) {
+      err |= TC_ERR_INTERNAL;
+      return;
+    }
+  } else {
+    for (u32 i = 0; i < nb; ++i) {
+      const u32 e = S.word(K::OFF_BPAIR, i);
+      const u32 ra = S.lpar(e & 0xFFFFu), rb = S.lpar(e >> 16);
+      if (ra != rb) continue;
+      if (root >= 0 && root != (int)ra) {
+        err |= TC_ERR_INTERNAL;
+        return;
+      }
+      root = (int)ra;
+    }
+    if (root < 0) {
+      err |= TC_ERR_INTERNAL;
+      return;
+    }
+  }
+  // 3. the tree hanging from region 0 (parent(r) < r), then re-rooted
+  *S.byte(K::OFF_WPAR, 0) = (u8)NONE8;
+  for (u32 r = 1; r < R; ++r) {
+    const u32 c = S.cand(*S.half(K::OFF_RLAB, r)) & TS::LOW;
+    if (c == TS::NONE) {
+      err |= TC_ERR_INTERNAL;
+      return;
+    }
+    const u32 p = S.lpar(c);
+    if (p >= r) {
+      err |= TC_ERR_INTERNAL;
+      return;
+    }
+    *S.byte(K::OFF_WPAR, r) = (u8)p;
+  }
+  tc_wide_tree_code(S, R, root, err, code);
 }
 
 // ------------------------------------------------ table-driven sweep ----

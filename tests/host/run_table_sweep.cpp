@@ -1,9 +1,11 @@
 // Test infrastructure: the table-driven sweep (tc_table_sweep.cuh, both back
-// ends) compiled for the host, fed the tables that host.cpp builds, one
-// instance at a time, against the oracle.  Random sign vectors of a seeded
-// counter stream, then eight special ones (constant, Harnack's distribution,
-// parities).  Usage: run_table_sweep <d> <edges file> <n>; exit 0 when all
-// codes agree.
+// ends) or the warp-per-instance sweep (tc_warp_sweep.cuh, its 32 lanes run
+// one after another, forward for even instances and in reverse for odd ones)
+// compiled for the host, fed the tables that host.cpp builds, one instance
+// at a time, against the oracle.  Random sign vectors of a seeded counter
+// stream, then eight special ones (constant, Harnack's distribution,
+// parities).  Usage: run_table_sweep <d> <edges file> <n> [warp]; exit 0
+// when all codes agree.
 #include <cstdio>
 #include <cstdlib>
 #include <fstream>
@@ -24,6 +26,8 @@ static inline void __threadfence() {}
 #undef __noinline__
 #define __noinline__
 #include "tc_table_sweep.cuh"
+#define TC_WARP_EMULATE
+#include "tc_warp_sweep.cuh"
 extern "C" {
 #include "tcurve_oracle.h"
 }
@@ -38,6 +42,8 @@ cudaError_t launch_hist_compact(ts_hist *, cudaStream_t) { return cudaErrorNotSu
 cudaError_t launch_selftest_wait(unsigned long long, uint32_t *, cudaStream_t) { return cudaErrorNotSupported; }
 cudaError_t launch_enumerate_jit(ts_tri *, uint64_t, uint64_t, uint32_t, ts_hist *, cudaStream_t) { return cudaErrorNotSupported; }
 cudaError_t launch_enumerate(const ts_tri *, uint64_t, uint64_t, uint32_t, ts_hist *, cudaStream_t, bool) { return cudaErrorNotSupported; }
+cudaError_t launch_real_schemes_warp(const ts_tri *, const uint64_t *, uint64_t, uint64_t *, cudaStream_t) { return cudaErrorNotSupported; }
+cudaError_t launch_enumerate_warp(const ts_tri *, uint64_t, uint64_t, uint32_t, ts_hist *, cudaStream_t) { return cudaErrorNotSupported; }
 void jit_release(ts_tri *) {}
 std::string jit_source(const Diamond &, bool, int) { return ""; }
 std::string jit_compile_cubin(const std::string &, std::string *, const std::vector<std::string> &) {
@@ -60,8 +66,9 @@ static uint64_t mix64(uint64_t x) {  // splitmix64 finaliser, for the inputs onl
 }
 
 template <int D>
-int run(const char *edge_file, int n) {
+int run(const char *edge_file, int n, bool warp) {
   typedef HostK<D> K;
+  typedef TcWarpK<D> WK;
   std::vector<int32_t> e;
   {
     std::ifstream f(edge_file);
@@ -75,8 +82,9 @@ int run(const char *edge_file, int n) {
     return 2;
   std::vector<int32_t> otri(6 * D * D);
   if (orc_triangles_from_edges(D, ne, e.data(), otri.data(), D * D) != D * D) return 2;
-  std::vector<u32> scratch(K::WORDS, 0xA5A5A5A5u);
+  std::vector<u32> scratch(K::WORDS > WK::WORDS ? K::WORDS : WK::WORDS, 0xA5A5A5A5u);
   const TcScratch<K> S{scratch.data()};
+  const u32 *wt = t.host_wtables.data();
   const int cw = orc_code_words(D);
   int bad = 0;
   for (int i = 0; i < n + 8; ++i) {
@@ -103,7 +111,15 @@ int run(const char *edge_file, int n) {
     }
     sg.w[K::W - 1] &= tc_top_mask(K::NPOINTS, K::W);
     u32 err = 0;
-    const TcCodeOut<K> got = tc_table_classify<K>(sg, t.host_tables.data(), t.lay.off_fan, t.lay.off_vext, S, err);
+    TcCodeOut<K> got;
+    if (warp) {
+      tc_emu_reverse = i % 2 == 1;
+      err = tc_warp_classify<D>(sg, wt + t.wlay.off_v, wt + t.wlay.off_e, t.wlay.E,
+                                wt + t.wlay.off_anti, t.wlay.nanti, wt + t.wlay.off_bedge,
+                                t.wlay.nbedge, scratch.data(), got.w);
+    } else {
+      got = tc_table_classify<K>(sg, t.host_tables.data(), t.lay.off_fan, t.lay.off_vext, S, err);
+    }
     uint64_t want[4] = {0, 0, 0, 0};
     const int rc = orc_real_scheme(D, otri.data(), (const uint64_t *)sg.w, want, cw, nullptr);
     bool same = rc == 0 && !err;
@@ -113,29 +129,30 @@ int run(const char *edge_file, int n) {
       ++bad;
     }
   }
-  printf("d=%d instances=%d differing=%d\n", D, n + 8, bad);
+  printf("d=%d %s instances=%d differing=%d\n", D, warp ? "warp" : "table", n + 8, bad);
   return bad != 0;
 }
 
 int main(int argc, char **argv) {
   const int d = atoi(argv[1]), n = atoi(argv[3]);
+  const bool warp = argc > 4 && std::string(argv[4]) == "warp";
   switch (d) {
-    case 1: return run<1>(argv[2], n);
-    case 2: return run<2>(argv[2], n);
-    case 3: return run<3>(argv[2], n);
-    case 4: return run<4>(argv[2], n);
-    case 5: return run<5>(argv[2], n);
-    case 6: return run<6>(argv[2], n);
-    case 7: return run<7>(argv[2], n);
-    case 8: return run<8>(argv[2], n);
-    case 9: return run<9>(argv[2], n);
-    case 10: return run<10>(argv[2], n);
-    case 11: return run<11>(argv[2], n);
-    case 12: return run<12>(argv[2], n);
-    case 13: return run<13>(argv[2], n);
-    case 14: return run<14>(argv[2], n);
-    case 15: return run<15>(argv[2], n);
-    case 16: return run<16>(argv[2], n);
+    case 1: return run<1>(argv[2], n, warp);
+    case 2: return run<2>(argv[2], n, warp);
+    case 3: return run<3>(argv[2], n, warp);
+    case 4: return run<4>(argv[2], n, warp);
+    case 5: return run<5>(argv[2], n, warp);
+    case 6: return run<6>(argv[2], n, warp);
+    case 7: return run<7>(argv[2], n, warp);
+    case 8: return run<8>(argv[2], n, warp);
+    case 9: return run<9>(argv[2], n, warp);
+    case 10: return run<10>(argv[2], n, warp);
+    case 11: return run<11>(argv[2], n, warp);
+    case 12: return run<12>(argv[2], n, warp);
+    case 13: return run<13>(argv[2], n, warp);
+    case 14: return run<14>(argv[2], n, warp);
+    case 15: return run<15>(argv[2], n, warp);
+    case 16: return run<16>(argv[2], n, warp);
   }
   return 2;
 }

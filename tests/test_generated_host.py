@@ -140,6 +140,26 @@ def test_table_sweep_on_the_host(table_sweep_exe, tmp_path, d):
         assert out.returncode == 0, (name, out.stdout + out.stderr)
 
 
+@pytest.mark.parametrize("d", list(range(1, 17)))
+def test_warp_sweep_on_the_host(table_sweep_exe, tmp_path, d):
+    """The warp-per-instance sweep (tc_warp_sweep.cuh) compiled for the host,
+    its 32 lanes run one after another (forward for even instances, in
+    reverse for odd ones: no phase may depend on the order of the lanes), on
+    the tables host.cpp builds, against the oracle: standard, regular and fan
+    triangulations, random and special sign vectors."""
+    cases = [("standard", ti.standard_triangulation(d))]
+    if d >= 3:
+        cases.append(("regular", ti.regular_triangulation(d, seed=200 + d)))
+    if d >= 2:
+        cases.append(("fan", ti.fan_triangulation(d)))
+    for name, edges in cases:
+        np.savetxt(tmp_path / "tri.txt", edges, fmt="%d")
+        out = subprocess.run([str(table_sweep_exe), str(d), str(tmp_path / "tri.txt"), "400", "warp"],
+                             capture_output=True, text=True)
+        assert out.returncode == 0, (name, out.stdout + out.stderr)
+        assert "warp" in out.stdout
+
+
 @pytest.mark.skipif(shutil.which("g++") is None, reason="needs g++")
 def test_histogram_inserts_on_the_host(tmp_path):
     """The device histogram inserts (one-word, block-private with spill,
