@@ -33,9 +33,11 @@ struct TableLayout {
 };
 
 // Tables of the warp-per-instance kernels (32-bit words, vertex ids in the
-// sweep order of T^diamond): wv[V] = k(v) (8 bits) | c(v) << 8 | the first
-// earlier neighbour of v << 9 (10 bits, 1023: none); wedge[E] = u | v << 16
-// for every edge u < v; wanti[2d] and wbedge[2d] = a | b << 16 for the
+// sweep order of T^diamond): wv[V] = k(v) (8 bits) | c(v) << 8 | the length
+// of v's fan (earlier neighbours) << 9 (7 bits) | the position of its first
+// entry in wedge << 16; wedge[E] = u | link << 15 | v << 16 for the fan
+// entries u of every vertex v in angular order (link: u, the entry before it
+// and v span a triangle); wanti[2d] and wbedge[2d] = a | b << 16 for the
 // antipodal pairs and one boundary edge of each antipodal pair of boundary
 // edges.
 struct WarpLayout {

@@ -305,9 +305,12 @@ bool pack_warp_tables(const Diamond &D, std::vector<uint32_t> &tables, WarpLayou
   if (V > 1022) return false;
   std::vector<uint32_t> wv(V), wedge;
   for (int v = 0; v < V; ++v) {
-    const uint32_t first = D.fan[v].empty() ? 1023u : (uint32_t)D.fan[v][0];
-    wv[v] = (uint32_t)D.k[v] | ((uint32_t)D.c[v] << 8) | (first << 9);
-    for (int u : D.fan[v]) wedge.push_back((uint32_t)u | ((uint32_t)v << 16));
+    const size_t f = D.fan[v].size();
+    if (f > 64 || wedge.size() + f > 0xFFFF) return false;
+    wv[v] = (uint32_t)D.k[v] | ((uint32_t)D.c[v] << 8) | ((uint32_t)f << 9) |
+            ((uint32_t)wedge.size() << 16);
+    for (size_t n = 0; n < f; ++n)
+      wedge.push_back((uint32_t)D.fan[v][n] | ((uint32_t)D.link[v][n] << 15) | ((uint32_t)v << 16));
   }
   WarpLayout L{};
   L.V = V;

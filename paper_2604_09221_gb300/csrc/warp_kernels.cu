@@ -28,6 +28,7 @@ namespace {
 constexpr u32 kWarpThreads = 256;  // 8 warps per block, one instance each at a time
 constexpr u32 kWarps = kWarpThreads / 32;
 constexpr u32 kGrab = 128;         // instances a warp takes from the work counter at once
+constexpr int kWarpMinBlocks = 4;  // register budget: 4 resident blocks (64 registers)
 
 template <int D>
 struct WarpSmem {
@@ -67,7 +68,7 @@ __device__ __forceinline__ u32 warp_classify(const TcSig<TcWarpK<D>::W> &sg, con
 }
 
 template <int D>
-__global__ void __launch_bounds__(kWarpThreads)
+__global__ void __launch_bounds__(kWarpThreads, kWarpMinBlocks)
     warp_real_schemes_kernel(WarpLayout L, const u32 *__restrict__ gtab,
                              const uint64_t *__restrict__ signs, uint64_t n, uint64_t *codes,
                              uint32_t *err_word) {
@@ -93,7 +94,7 @@ __global__ void __launch_bounds__(kWarpThreads)
 }
 
 template <int D>
-__global__ void __launch_bounds__(kWarpThreads)
+__global__ void __launch_bounds__(kWarpThreads, kWarpMinBlocks)
     warp_enumerate_kernel(WarpLayout L, const u32 *__restrict__ gtab, uint64_t lo, uint64_t total,
                           uint32_t flags, ts_hist h) {
   typedef TcWarpK<D> K;
