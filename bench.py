@@ -190,7 +190,7 @@ def main():
     # the small case of --workload profile (for ncu captures; not a bench value)
     ap.add_argument("--degree", type=int, default=D)
     ap.add_argument("--log2n", type=int, default=26)
-    ap.add_argument("--kernel", default="auto", choices=["auto", "table", "specialized"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "table", "specialized", "warp"])
     ap.add_argument("--scratch", default="auto", choices=["auto", "shared", "global"])
     ap.add_argument("--splitmix", action="store_true")
     ap.add_argument("--occupancy", type=int, default=0)
@@ -476,11 +476,11 @@ def profile_case(args):
     d = args.degree
     tri = eng.Triangulation(d, ti.regular_triangulation(d, seed=TRI_SEED if d == D else d))
     tri.set_kernel({"auto": eng.TS_KERNEL_AUTO, "table": eng.TS_KERNEL_TABLE,
-                    "specialized": eng.TS_KERNEL_SPECIALIZED}[args.kernel])
+                    "specialized": eng.TS_KERNEL_SPECIALIZED, "warp": eng.TS_KERNEL_WARP}[args.kernel])
     tri.set_scratch({"auto": eng.TS_SCRATCH_AUTO, "shared": eng.TS_SCRATCH_SHARED,
                      "global": eng.TS_SCRATCH_GLOBAL}[args.scratch])
     tri.set_occupancy(args.occupancy)
-    if args.kernel != "table" and d <= 9:
+    if args.kernel in ("auto", "specialized") and d <= 9:
         tri.prepare()
     n = 1 << args.log2n
     if args.batch:  # a one-degree batch of 8 triangulations, n sign vectors in all
@@ -694,8 +694,9 @@ def alg_ops(d: int) -> float:
 def mixed_run(steps, warmup, degrees=(5, 6, 7, 8, 9, 10), per_degree=32, seed=31):
     """The mixed-degree batch: 32 seeded triangulations per d in 5..10,
     2^U(10,24) splitmix64 sign vectors each, one CUDA-graph launch per step
-    (one persistent kernel per degree), tiles from the autotuner; every job's
-    histogram is checked to count all its sign vectors."""
+    (one fused persistent kernel for all degrees, or one per degree: the
+    faster plan), tiles from the autotuner; every job's histogram is checked
+    to count all its sign vectors."""
     import numpy as np
     import torch
 
@@ -728,15 +729,21 @@ def mixed_run(steps, warmup, degrees=(5, 6, 7, 8, 9, 10), per_degree=32, seed=31
             b.synchronize()
             out.append(a.elapsed_time(b))
         return out
-    # the degree groups concurrently (forked streams) or one after the other:
-    # the faster order, measured on two runs each, is the one timed
+    # three launch plans, each measured on two runs; the fastest is the one
+    # timed: the degree groups concurrently (forked streams), one after the
+    # other, or every job of every degree in one fused persistent launch
+    # (fused tiles from the autotuner)
+    ftiles = autotune.autotune_fused(tris, counts, bases, reps=1)
+    autotune.apply_fused(batch, ftiles)
     order = {}
-    for serial in (False, True):
-        batch.set_serial(serial)
+    for plan in ("concurrent", "serial", "fused"):
+        batch.set_fused(plan == "fused")
+        batch.set_serial(plan == "serial")
         timed_runs(max(warmup, 1))
-        order[serial] = min(timed_runs(2))
-    serial = order[True] < order[False]
-    batch.set_serial(serial)
+        order[plan] = min(timed_runs(2))
+    plan = min(order, key=order.get)
+    batch.set_fused(plan == "fused")
+    batch.set_serial(plan == "serial")
     torch.cuda.synchronize()
     times = timed_runs(steps)
     for j in range(len(tris)):
@@ -753,9 +760,13 @@ def mixed_run(steps, warmup, degrees=(5, 6, 7, 8, 9, 10), per_degree=32, seed=31
             "kernels": {str(d): fam[d]["kernel"] for d in degrees},
             "tiles": {str(d): [fam[d]["threads"], fam[d]["chunk"], fam[d]["scratch"]] for d in degrees},
             "build_s": build_s, "alg_tops": ops / (ms / 1e3) / 1e12,
-            "groups": "one after the other" if serial else "concurrent streams",
-            "order_ms": {"concurrent": order[False], "serial": order[True]},
-            "gpu_launches_per_step": len(degrees)}
+            "launch": {"concurrent": "one persistent kernel per degree, concurrent streams",
+                       "serial": "one persistent kernel per degree, one after the other",
+                       "fused": "one fused persistent kernel for all degrees"}[plan],
+            "plan_ms": order,
+            "fused_tiles": {str(d): [{1: "thread", 3: "warp"}.get(k, k), c]
+                            for d, (k, c) in sorted(ftiles.items())},
+            "gpu_launches_per_step": 1 if plan == "fused" else len(degrees)}
 
 
 def mixed_families(reps=3, degrees=(5, 6, 7, 8, 9, 10), per_degree=32, seed=31, occupancies=(0,)):
@@ -825,6 +836,7 @@ def mixed_workload(args):
             "config": {k: r[k] for k in ("workload", "degrees", "triangulations_per_degree", "jobs",
                                          "sign_vectors", "counts", "kernels", "tiles")},
             "alg_frac": r["alg_tops"] * 1e12 / peak["peak"], "build_s": r["build_s"],
+            "launch": r["launch"], "plan_ms": r["plan_ms"], "fused_tiles": r["fused_tiles"],
             "gpu_launches": r["gpu_launches_per_step"] * args.steps}
     print(json.dumps(line), flush=True)
     return 0

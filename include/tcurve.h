@@ -115,8 +115,9 @@ ts_status ts_real_schemes(const ts_tri *tri, const uint64_t *signs, uint64_t n,
  *   TS_KERNEL_WARP: one generic kernel per degree in which a whole warp
  *     classifies one sign vector at a time (lock-free union-find over the
  *     edges of T^diamond, region tree and code in the warp's shared memory;
- *     no global scratch).  ts_real_schemes and ts_enumerate only; batches
- *     and ts_enumerate_noalloc run the other families.
+ *     no global scratch).  ts_real_schemes and ts_enumerate; batches run
+ *     it as the warp tile of their fused launch (ts_batch_set_fused_tile);
+ *     ts_enumerate_noalloc runs the table-driven family.
  *   TS_KERNEL_AUTO (default): specialised for ts_enumerate and for batches of
  *     at least 65536 instances when d <= 9, table-driven otherwise or if the
  *     specialised kernel cannot be built. */
@@ -253,6 +254,34 @@ ts_status ts_batch_set_tile(ts_batch *batch, int d, int threads, int chunk, int 
  * filling the whole GPU.  Takes effect at the next run (a new graph is
  * captured).  TS_EINVAL for other values. */
 ts_status ts_batch_set_serial(ts_batch *batch, int serial);
+/* One persistent launch for the whole batch (an engine facility against the
+ * kernel-dispatch overhead that Sec. 3 names as a cost at scale): with
+ * fused = 1, ts_batch_run launches a single kernel that pulls the work items
+ * of every job of every degree from one counter (jobs in degree order, so
+ * the degrees follow one another without a gap), stages a job's tables with
+ * cp.async.bulk when it moves to another triangulation, and runs each job
+ * with its degree's fused tile (ts_batch_set_fused_tile).  The kernel is
+ * compiled per range of degrees with the register budget of that range's
+ * table-driven sweep (degrees up to 6, 9, 11, 16: 40, 48, 64, 80
+ * registers); a batch takes the range of its largest degree, or the widest
+ * one when a degree has a warp tile.  Specialised groups do not apply in
+ * this mode.  fused = 0 (default) returns to one persistent kernel per
+ * degree group (ts_batch_set_serial).  Allocates the job table and global
+ * scratch of the launch here (grid x 128 threads x scratch words), after
+ * waiting for all work on the device; the next run with use_graph captures
+ * a new graph.  TS_EINVAL for other values. */
+ts_status ts_batch_set_fused(ts_batch *batch, int fused);
+/* Tile of degree d in the fused launch: kind TS_KERNEL_TABLE or
+ * TS_KERNEL_AUTO (default: one thread per sign vector, the table-driven
+ * sweep, per-thread scratch in global memory) or TS_KERNEL_WARP (d >= 7:
+ * the 32 lanes of a warp classify one sign vector together, the state in
+ * shared memory), and chunk sign vectors per work item (a multiple of 128,
+ * at most 2^24; default 1024).  May be set in either mode; in fused mode it
+ * waits for all work on the device and re-plans the launch (the next run
+ * with use_graph captures a new graph).  TS_EINVAL for other values, a
+ * degree the batch does not hold, or a tile whose launch does not fit (the
+ * previous tile is kept). */
+ts_status ts_batch_set_fused_tile(ts_batch *batch, int d, int kind, int chunk);
 /* Clear the histograms and run every job, asynchronously on stream.  With
  * use_graph the work (clears, fork, per-degree kernels, join) is captured
  * into a CUDA graph on the first call (and after a tile change) and the graph
@@ -270,7 +299,11 @@ ts_status ts_batch_run(ts_batch *batch, int use_graph, void *stream);
  * one of them was set to TS_KERNEL_TABLE, and not if the code cannot be
  * built (log then says why); ts_batch_set_kernel changes it later.
  * Specialised groups have 128-thread blocks and global scratch
- * (ts_batch_set_tile accepts only those; the chunk may vary).
+ * (ts_batch_set_tile accepts only those; the chunk may vary).  In fused
+ * mode (ts_batch_set_fused) info describes the degree's fused tile instead:
+ * kernel TS_KERNEL_TABLE or TS_KERNEL_WARP, 128 threads, its chunk, scratch
+ * TS_SCRATCH_GLOBAL (thread tiles) or TS_SCRATCH_SHARED (warp tiles), and
+ * the registers, resident blocks and grid of the one fused kernel.
  *   info  receives kernel (TS_KERNEL_*), threads per block, chunk (sign
  *         vectors per work item), scratch (TS_SCRATCH_*), registers per
  *         thread, local_bytes (per-thread local memory: spills, call

@@ -96,6 +96,8 @@ def _load():
                 "ts_batch_read": ([P, I, P, P, U64, ctypes.POINTER(U64), ctypes.POINTER(U64), P], I),
                 "ts_batch_set_kernel": ([P, I, I], I),
                 "ts_batch_set_serial": ([P, I], I),
+                "ts_batch_set_fused": ([P, I], I),
+                "ts_batch_set_fused_tile": ([P, I, I, I], I),
                 "ts_batch_info": ([P, I, ctypes.POINTER(BatchGroupInfo), ctypes.c_char_p,
                                    ctypes.c_size_t], I),
                 "ts_batch_specialized_link": ([I, I, P, P, ctypes.POINTER(ctypes.c_size_t),
@@ -316,6 +318,7 @@ class Batch:
                                        int(hist_capacity), ctypes.byref(h)), "ts_batch_create")
         self._h = h
         self.njobs = n
+        self.fused = False
         self.counts = cnt
         self.capacity = int(hist_capacity)
         self.degrees = sorted({t.d for t in tris})
@@ -353,14 +356,28 @@ class Batch:
         streams of their own (False, the default): ts_batch_set_serial."""
         _check(_lib.ts_batch_set_serial(self._h, int(bool(serial))), "ts_batch_set_serial")
 
+    def set_fused(self, fused: bool):
+        """One persistent launch for every job of every degree (True) or one
+        per degree group (False, the default): ts_batch_set_fused."""
+        _check(_lib.ts_batch_set_fused(self._h, int(bool(fused))), "ts_batch_set_fused")
+        self.fused = bool(fused)
+
+    def set_fused_tile(self, d: int, kind: int, chunk: int):
+        """Tile of degree d in the fused launch (ts_batch_set_fused_tile):
+        TS_KERNEL_TABLE (one thread per sign vector) or TS_KERNEL_WARP (one warp
+        per sign vector, d >= 7), and sign vectors per work item."""
+        _check(_lib.ts_batch_set_fused_tile(self._h, int(d), int(kind), int(chunk)),
+               "ts_batch_set_fused_tile")
+
     def info(self, d: int) -> dict:
         """Kernel family, tile and launch resources of the degree-d group
-        (ts_batch_info)."""
+        (ts_batch_info; in fused mode, the degree's fused tile)."""
         x = BatchGroupInfo()
         buf = ctypes.create_string_buffer(1 << 14)
         _check(_lib.ts_batch_info(self._h, int(d), ctypes.byref(x), buf, len(buf)), "ts_batch_info")
         out = {f: getattr(x, f) for f, _ in BatchGroupInfo._fields_}
-        out["kernel"] = {TS_KERNEL_TABLE: "table", TS_KERNEL_SPECIALIZED: "specialized"}[x.kernel]
+        out["kernel"] = {TS_KERNEL_TABLE: "table", TS_KERNEL_SPECIALIZED: "specialized",
+                         TS_KERNEL_WARP: "warp"}[x.kernel]
         out["scratch"] = {TS_SCRATCH_SHARED: "shared", TS_SCRATCH_GLOBAL: "global"}[x.scratch]
         out["log"] = buf.value.decode(errors="replace")
         return out

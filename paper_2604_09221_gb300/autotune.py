@@ -10,6 +10,11 @@ The tuner times candidate tiles on the batch's own jobs of that degree (a
 sub-batch, so degrees are tuned independently), keeps the fastest, and can
 store the choice in a JSON cache keyed by GPU name, degree and kernel family
 (path from the argument or the TCURVE_TILE_CACHE environment variable).
+
+In the fused launch (ts_batch_set_fused: one kernel for all degrees) a
+degree's tile is the kind (one thread or, from d = 7, one warp per sign
+vector) and the sign vectors per work item; autotune_fused times those the
+same way, on fused sub-batches of one degree.
 """
 from __future__ import annotations
 
@@ -121,3 +126,78 @@ def apply(batch, tiles: Dict[int, Tuple[int, ...]]):
     for d, tile in tiles.items():
         if d in batch.degrees:
             batch.set_tile(d, *tile)
+
+
+# fused launch: work items of 128 x c sign vectors; warp tiles from d = 7
+FUSED_THREAD_CHUNKS = (4, 8, 16, 64)
+FUSED_WARP_CHUNKS = (2, 8)
+FUSED_WARP_FROM = 7
+
+
+def fused_candidates(d: int, thread_chunks=FUSED_THREAD_CHUNKS, warp_chunks=FUSED_WARP_CHUNKS):
+    from . import TS_KERNEL_TABLE, TS_KERNEL_WARP
+    out = [(TS_KERNEL_TABLE, 128 * c) for c in thread_chunks]
+    if d >= FUSED_WARP_FROM:
+        out += [(TS_KERNEL_WARP, 128 * c) for c in warp_chunks]
+    return out
+
+
+def tune_fused_degree(tris, counts, bases, reps: int = 3, thread_chunks=FUSED_THREAD_CHUNKS,
+                      warp_chunks=FUSED_WARP_CHUNKS) -> Tuple[int, int, float]:
+    """Fastest fused tile (kind, chunk, ms) for jobs of one degree, timed in
+    a fused sub-batch of exactly these jobs."""
+    from . import Batch, TSError
+    d = tris[0].d
+    assert all(t.d == d for t in tris)
+    sub = Batch(tris, counts, bases)
+    sub.set_fused(True)
+    best = None
+    for kind, chunk in fused_candidates(d, thread_chunks, warp_chunks):
+        try:
+            sub.set_fused_tile(d, kind, chunk)
+        except TSError:
+            continue  # the launch does not fit
+        ms = _time_batch(sub, reps)
+        if best is None or ms < best[2]:
+            best = (kind, chunk, ms)
+    sub.close()
+    if best is None:
+        raise RuntimeError(f"no fused tile fits degree {d}")
+    return best
+
+
+def autotune_fused(tris, counts, bases, cache: Optional[str] = None, reps: int = 3,
+                   thread_chunks=FUSED_THREAD_CHUNKS, warp_chunks=FUSED_WARP_CHUNKS
+                   ) -> Dict[int, Tuple[int, int]]:
+    """Fused-launch tile per degree of the batch {d: (kind, chunk)}; cached
+    choices are reused, new ones stored."""
+    cache = cache or os.environ.get("TCURVE_TILE_CACHE")
+    store = {}
+    if cache and os.path.exists(cache):
+        with open(cache) as f:
+            store = json.load(f)
+    gpu = _gpu_name()
+    tiles: Dict[int, Tuple[int, int]] = {}
+    for d in sorted({t.d for t in tris}):
+        idx = [i for i, t in enumerate(tris) if t.d == d]
+        key = f"{gpu}|d={d}|fused|tile2"
+        if key in store:
+            tiles[d] = tuple(store[key][:2])
+        else:
+            kind, chunk, ms = tune_fused_degree([tris[i] for i in idx], [counts[i] for i in idx],
+                                                [bases[i] for i in idx], reps, thread_chunks,
+                                                warp_chunks)
+            tiles[d] = (kind, chunk)
+            store[key] = [kind, chunk, ms]
+    if cache:
+        tmp = cache + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump(store, f, indent=1, sort_keys=True)
+        os.replace(tmp, cache)
+    return tiles
+
+
+def apply_fused(batch, tiles: Dict[int, Tuple[int, int]]):
+    for d, (kind, chunk) in tiles.items():
+        if d in batch.degrees:
+            batch.set_fused_tile(d, kind, chunk)

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libtcurve.so")
-SOURCES = ["host.cpp", "kernels.cu", "warp_kernels.cu", "jit.cpp", "noalloc.cu", "batch.cu",
+SOURCES = ["host.cpp", "kernels.cu", "warp_kernels.cu", "jit.cpp", "noalloc.cu", "batch.cu", "fused.cu",
            "int_peak.cu"]
 HEADERS = ["engine.h", "tc_layout.h", "tc_runtime.cuh", "tc_table_sweep.cuh", "tc_warp_sweep.cuh",
            "tc_stage.cuh", "jit_kernels.cuh",

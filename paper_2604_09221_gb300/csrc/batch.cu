@@ -261,6 +261,8 @@ struct ts_batch {
     unsigned long long *d_work = nullptr;
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
+    int fwarp = 0;              // fused launch: warp (1) or thread (0) per instance
+    int fchunk = kFusedThreads * 8;  // fused launch: sign vectors per work item
   };
   std::vector<DevJob> jobs;  // host copies (chunk0 per group)
   std::vector<int> degree, cws;       // degree and code words of every job
@@ -278,6 +280,17 @@ struct ts_batch {
   int device = 0;
   std::vector<ts_tri *> tris;  // triangulation of every job
   bool serial = false;         // degree groups one after the other (else concurrent streams)
+  // fused launch (ts_batch_set_fused): one persistent kernel over all jobs
+  bool fused = false;
+  FusedJob *d_fjobs = nullptr;  // jobs sorted by degree
+  uint64_t fitems = 0;
+  int ftier = -1;
+  unsigned fgrid = 1;
+  size_t fsmem = 0;
+  uint32_t ftoff = 0, fws = 0;
+  uint32_t *fscratch = nullptr;
+  size_t fscratch_bytes = 0;
+  unsigned long long *d_fwork = nullptr;
 };
 
 namespace {
@@ -352,12 +365,110 @@ cudaError_t launch_group(ts_batch *b, ts_batch::Group &g, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// The whole batch as stream work on `st`: clear, fork, one kernel per degree, join.
+// Job table, kernel tier, shared memory, persistent grid and global scratch
+// of the fused launch (host work only, never while a stream is captured):
+// the jobs in degree order, each with its degree's tile; the tier of the
+// largest degree, or the warp tier when a degree has a warp tile.
+cudaError_t prepare_fused(ts_batch *b) {
+  std::vector<const ts_batch::Group *> gs;
+  for (const auto &g : b->groups) gs.push_back(&g);
+  std::sort(gs.begin(), gs.end(), [](const ts_batch::Group *x, const ts_batch::Group *y) {
+    return x->d < y->d;
+  });
+  std::vector<FusedJob> fj;
+  uint64_t items = 0;
+  uint32_t maxtab = 0, wsw = 0;
+  int dmax = 0;
+  bool anywarp = false;
+  for (const ts_batch::Group *g : gs) {
+    for (int j : g->jobs) {
+      const DevJob &dj = b->jobs[j];
+      const ts_tri *t = b->tris[j];
+      FusedJob x{};
+      x.n = dj.n;
+      x.base = dj.base;
+      x.codes = dj.codes;
+      x.hkeys = dj.hkeys;
+      x.hcnt = dj.hcnt;
+      x.hslots = dj.hslots;
+      x.item0 = items;
+      x.d = (uint32_t)g->d;
+      x.chunk = (uint32_t)g->fchunk;
+      x.warp = (uint32_t)g->fwarp;
+      if (x.warp) {
+        x.tab = t->d_wtables;
+        x.tab_words = t->wlay.words;
+        x.wl = t->wlay;
+        wsw = std::max(wsw, fused_warp_words(g->d));
+        anywarp = true;
+      } else {
+        x.tab = t->d_tables;
+        x.tab_words = t->lay.words;
+        x.off_fan = t->lay.off_fan;
+        x.off_vext = t->lay.off_vext;
+      }
+      maxtab = std::max(maxtab, x.tab_words);
+      items += (x.n + x.chunk - 1) / x.chunk;
+      dmax = std::max(dmax, g->d);
+      fj.push_back(x);
+    }
+  }
+  const int tier = anywarp ? kFusedWarpTier : fused_tier(dmax);
+  if (tier < 0 || fj.empty()) return cudaErrorInvalidConfiguration;
+  const uint32_t toff = (maxtab * 4 + 127) / 128 * 128;
+  const size_t smem = (size_t)toff + 128 + (anywarp ? (size_t)4 * wsw * 4 : 0);
+  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  int per_sm = 0, sms = 0, dev = 0;
+  cudaError_t e = fused_occupancy(tier, smem, &per_sm);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const uint64_t cap = (uint64_t)per_sm * sms;
+  const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(cap, items));
+  const size_t need = (size_t)grid * kFusedThreads * fused_slab_words(tier) * 4;
+  if (need > b->fscratch_bytes) {
+    if (b->fscratch) cudaFree(b->fscratch);
+    b->fscratch = nullptr;
+    b->fscratch_bytes = 0;
+    e = cudaMalloc(&b->fscratch, need);
+    if (e != cudaSuccess) return e;
+    b->fscratch_bytes = need;
+  }
+  if (!b->d_fjobs) {
+    e = cudaMalloc(&b->d_fjobs, sizeof(FusedJob) * fj.size());
+    if (e != cudaSuccess) return e;
+  }
+  if (!b->d_fwork) {
+    e = cudaMalloc(&b->d_fwork, sizeof(unsigned long long));
+    if (e != cudaSuccess) return e;
+  }
+  e = cudaMemcpy(b->d_fjobs, fj.data(), sizeof(FusedJob) * fj.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return e;
+  b->fitems = items;
+  b->ftier = tier;
+  b->fgrid = grid;
+  b->fsmem = smem;
+  b->ftoff = toff;
+  b->fws = wsw;
+  return cudaSuccess;
+}
+
+// The whole batch as stream work on `st`: clear, then either the fused
+// launch or fork, one kernel per degree, join.
 cudaError_t enqueue(ts_batch *b, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(b->d_keys, 0, b->key_words * 8, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counts, 0, b->count_words * 8, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, 4, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_failed, 0, 8, st);
+  if (b->fused) {  // one persistent kernel for every job of every degree
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_fwork, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess)
+      e = fused_launch(b->ftier, b->fgrid, b->fsmem, b->ftoff, b->fws, b->d_fjobs,
+                       (uint32_t)b->jobs.size(), b->fitems, b->d_fwork, b->d_err, b->d_failed,
+                       b->fscratch, st);
+    return e;
+  }
   if (b->serial) {  // one degree after the other, each persistent kernel on the whole GPU
     for (auto &g : b->groups)
       if (e == cudaSuccess) e = launch_group(b, g, st);
@@ -540,6 +651,9 @@ void ts_batch_free(ts_batch *b) {
     if (g.done) cudaEventDestroy(g.done);
   }
   if (b->fork) cudaEventDestroy(b->fork);
+  if (b->d_fjobs) cudaFree(b->d_fjobs);
+  if (b->fscratch) cudaFree(b->fscratch);
+  if (b->d_fwork) cudaFree(b->d_fwork);
   if (b->d_keys) cudaFree(b->d_keys);
   if (b->d_counts) cudaFree(b->d_counts);
   if (b->d_err) cudaFree(b->d_err);
@@ -614,6 +728,53 @@ ts_status ts_batch_set_serial(ts_batch *b, int serial) {
   return TS_OK;
 }
 
+ts_status ts_batch_set_fused(ts_batch *b, int fused) {
+  if (!b || fused < 0 || fused > 1) return TS_EINVAL;
+  if (b->fused == (fused != 0)) return TS_OK;
+  cudaError_t e = cudaDeviceSynchronize();  // a run launched before may still read the tables
+  if (e != cudaSuccess) return cuda_st(e);
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  if (fused) {
+    e = prepare_fused(b);
+    if (e != cudaSuccess) return cuda_st(e);
+  }
+  b->fused = fused != 0;
+  return TS_OK;
+}
+
+ts_status ts_batch_set_fused_tile(ts_batch *b, int d, int kind, int chunk) {
+  if (!b || chunk < kFusedThreads || chunk % kFusedThreads || chunk > (1 << 24) ||
+      (kind != TS_KERNEL_AUTO && kind != TS_KERNEL_TABLE && kind != TS_KERNEL_WARP) ||
+      (kind == TS_KERNEL_WARP && d < kFusedWarpFrom))
+    return TS_EINVAL;
+  for (auto &g : b->groups) {
+    if (g.d != d) continue;
+    cudaError_t e = cudaDeviceSynchronize();  // runs already launched read the job table
+    if (e != cudaSuccess) return cuda_st(e);
+    if (b->exec) {
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
+    const int ow = g.fwarp, oc = g.fchunk;
+    g.fwarp = kind == TS_KERNEL_WARP ? 1 : 0;
+    g.fchunk = chunk;
+    if (b->fused) {
+      e = prepare_fused(b);
+      if (e != cudaSuccess) {  // keep the previous, prepared tile
+        g.fwarp = ow;
+        g.fchunk = oc;
+        const cudaError_t e2 = prepare_fused(b);
+        return e2 != cudaSuccess ? cuda_st(e2) : TS_EINVAL;
+      }
+    }
+    return TS_OK;
+  }
+  return TS_EINVAL;
+}
+
 ts_status ts_batch_run(ts_batch *b, int use_graph, void *stream) {
   if (!b) return TS_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
@@ -642,6 +803,18 @@ ts_status ts_batch_info(const ts_batch *b, int d, ts_batch_group_info *info, cha
   for (const auto &g : b->groups) {
     if (g.d != d) continue;
     ts_batch_group_info x{};
+    if (b->fused) {  // the degree's tile in the one fused launch
+      x.kernel = g.fwarp ? TS_KERNEL_WARP : TS_KERNEL_TABLE;
+      x.threads = kFusedThreads;
+      x.chunk = g.fchunk;
+      x.scratch = g.fwarp ? TS_SCRATCH_SHARED : TS_SCRATCH_GLOBAL;
+      x.grid = (int)b->fgrid;
+      fused_attrs(b->ftier, &x.registers, &x.local_bytes);
+      fused_occupancy(b->ftier, b->fsmem, &x.blocks_per_sm);
+      *info = x;
+      if (log && len) log[0] = 0;
+      return TS_OK;
+    }
     x.kernel = g.jit ? TS_KERNEL_SPECIALIZED : TS_KERNEL_TABLE;
     x.threads = g.threads;
     x.chunk = g.chunk;

@@ -185,4 +185,39 @@ size_t jit_jobs_slab_bytes(const JitJobsModule &m);  // global scratch per block
 cudaError_t jit_jobs_launch(const JitJobsModule &m, unsigned grid, const void *jobs, uint32_t njobs,
                             uint64_t items, uint32_t chunk, unsigned long long *work, uint32_t *err,
                             unsigned long long *failed, uint32_t *scratch, cudaStream_t st);
+
+// Fused batch kernel (fused.cu): one persistent launch over the jobs of all
+// degrees of a batch, each degree with its own tile (one thread or one warp
+// per sign vector, sign vectors per work item).
+constexpr int kFusedThreads = 128;  // threads per block (4 warps)
+constexpr int kFusedTiers = 4;      // register tiers: degrees up to 6, 9, 11, 16
+constexpr int kFusedWarpTier = 4;   // the tier-3 kernel with warp-per-instance bodies
+constexpr int kFusedWarpFrom = 7;   // warp-per-instance bodies from this degree
+struct FusedJob {
+  const uint32_t *tab;   // tables staged for the job: table-driven or warp layout (tile)
+  uint64_t n, base;      // sign vectors, splitmix64 counter base
+  unsigned long long *codes;  // per-instance codes or null
+  unsigned long long *hkeys;  // the job's histogram
+  unsigned long long *hcnt;
+  uint64_t hslots;
+  uint64_t item0;        // first work item of the job
+  uint32_t d, chunk;     // degree; sign vectors per work item (a multiple of kFusedThreads)
+  uint32_t warp;         // 1: warp per instance (warp tables), 0: thread per instance
+  uint32_t tab_words;    // words staged (a multiple of 4)
+  uint32_t off_fan, off_vext;  // table-driven layout
+  WarpLayout wl;               // warp layout
+  uint32_t pad;
+};
+int fused_tier(int dmax);          // tier of a batch whose largest degree is dmax (-1: none)
+int fused_tier_degree(int tier);   // largest degree of a tier
+uint32_t fused_slab_words(int tier);  // global scratch words per thread of a tier's kernel
+uint32_t fused_warp_words(int d);     // shared words of one warp of a degree-d warp tile
+cudaError_t fused_occupancy(int tier, size_t smem, int *blocks_per_sm);
+cudaError_t fused_attrs(int tier, int *regs, int *local_bytes);
+// smem = toff (the tables, 128-byte aligned) + 128 + 4 x ws_stride words
+// (warp tiles); scratch: grid x kFusedThreads x fused_slab_words(tier) words.
+cudaError_t fused_launch(int tier, unsigned grid, size_t smem, uint32_t toff, uint32_t ws_stride,
+                         const FusedJob *jobs, uint32_t njobs, uint64_t items,
+                         unsigned long long *work, uint32_t *err, unsigned long long *failed,
+                         uint32_t *scratch, cudaStream_t st);
 }  // namespace tcurve

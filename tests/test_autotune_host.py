@@ -126,3 +126,62 @@ def test_apply_sets_only_the_degrees_of_the_batch():
     b = FakeBatch([FakeTri(6), FakeTri(9)], [1, 1], [0, 0])
     autotune.apply(b, {6: (64, 256, 1), 9: (128, 2048, 2), 12: (32, 32, 2)})
     assert b.tiles == {6: (64, 256, 1), 9: (128, 2048, 2)}
+
+
+class FakeFusedBatch(FakeBatch):
+    """A fused sub-batch: records fused tiles; refuses chunks above 4096
+    like a launch that does not fit."""
+
+    def __init__(self, tris, counts, bases):
+        super().__init__(tris, counts, bases)
+        self.fused = False
+
+    def set_fused(self, fused):
+        self.fused = bool(fused)
+
+    def set_fused_tile(self, d, kind, chunk):
+        if chunk > 4096:
+            raise eng.TSError(1, "ts_batch_set_fused_tile")
+        self.tile = (kind, chunk)
+        self.tiles[d] = self.tile
+
+
+def fused_ms(batch, reps):
+    """Warp tiles fastest at d = 13, thread tiles with 1024 per item below."""
+    assert batch.fused
+    kind, chunk = batch.tile
+    d = batch.degrees[0]
+    if d >= 13:
+        return 1.0 + (0.0 if kind == eng.TS_KERNEL_WARP else 3.0) + abs(chunk - 256) / 1e4
+    return 1.0 + (0.0 if kind == eng.TS_KERNEL_TABLE else 3.0) + abs(chunk - 1024) / 1e4
+
+
+def test_fused_tiles_per_degree_with_cache(monkeypatch, tmp_path):
+    """autotune_fused: each degree tuned alone in a fused sub-batch; warp
+    tiles offered from d = 7 only; refused tiles skipped; the cache is keyed
+    by the fused family and reused without timing."""
+    FakeBatch.made = []
+    timed = []
+
+    def timer(batch, reps):
+        timed.append((batch.degrees[0], batch.tile))
+        return fused_ms(batch, reps)
+
+    monkeypatch.setattr(eng, "Batch", FakeFusedBatch)
+    monkeypatch.setattr(autotune, "_time_batch", timer)
+    monkeypatch.setattr(autotune, "_gpu_name", lambda: "FakeGPU")
+    tris = [FakeTri(5), FakeTri(13), FakeTri(5)]
+    cache = str(tmp_path / "tiles.json")
+    tiles = autotune.autotune_fused(tris, [10, 20, 30], [0, 1, 2], cache=cache, reps=1)
+    assert tiles == {5: (eng.TS_KERNEL_TABLE, 1024), 13: (eng.TS_KERNEL_WARP, 256)}
+    assert all(b.degrees in ([5], [13]) and b.fused for b in FakeBatch.made)
+    assert all(k == eng.TS_KERNEL_TABLE for d, (k, c) in timed if d == 5)
+    assert all(c <= 4096 for _, (k, c) in timed)          # 128 x 64 was refused
+    stored = json.load(open(cache))
+    assert set(stored) == {"FakeGPU|d=5|fused|tile2", "FakeGPU|d=13|fused|tile2"}
+    n = len(timed)
+    assert autotune.autotune_fused(tris, [10, 20, 30], [0, 1, 2], cache=cache) == tiles
+    assert len(timed) == n                                # served from the cache
+    applied = FakeFusedBatch(tris, [1, 1, 1], [0, 0, 0])
+    autotune.apply_fused(applied, tiles)
+    assert applied.tiles == tiles
