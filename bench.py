@@ -25,8 +25,9 @@ continuous-batching server, p50/p99 job latency).  Other workloads:
 
   --workload profile  a small sweep for profiler captures (--degree, --log2n,
                       --kernel, --scratch, --splitmix; --query: the plain query
-                      kernel on materialised masks instead); prints its rate,
-                      which is not a bench value
+                      kernel on materialised masks instead; --batch: a batch of
+                      8 triangulations of that degree, --fused in one fused
+                      launch); prints its rate, which is not a bench value
   --workload intpeak  the integer-issue microbenchmark alone (all instruction
                       kinds; --trips), for profiler captures
 
@@ -196,6 +197,7 @@ def main():
     ap.add_argument("--occupancy", type=int, default=0)
     ap.add_argument("--query", action="store_true")
     ap.add_argument("--batch", action="store_true")
+    ap.add_argument("--fused", action="store_true")
     ap.add_argument("--trips", type=int, default=1 << 15)
     ap.add_argument("--no-stretch", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
@@ -488,6 +490,8 @@ def profile_case(args):
         batch = eng.Batch(tris8, [n // 8] * 8, [job_base(3100 + d, k) for k in range(8)])
         batch.set_kernel(d, {"auto": eng.TS_KERNEL_AUTO, "table": eng.TS_KERNEL_TABLE,
                              "specialized": eng.TS_KERNEL_SPECIALIZED}[args.kernel])
+        if args.fused:  # the fused launch, thread tiles of 1024 sign vectors
+            batch.set_fused(True)
         ms = []
         for _ in range(2):
             a = torch.cuda.Event(enable_timing=True)
@@ -502,7 +506,8 @@ def profile_case(args):
             assert failed == 0 and int(cnt.sum()) == n // 8
         info = batch.info(d)
         info.pop("log")
-        print(json.dumps({"profile_case": True, "batch": True, "degree": d, "n": n, "ms": ms,
+        print(json.dumps({"profile_case": True, "batch": True, "fused": args.fused, "degree": d,
+                          "n": n, "ms": ms,
                           "info": info, "schemes_per_s": n / (min(ms) / 1e3)}), flush=True)
         return 0
     if args.query:  # the plain query kernel on n materialised sign vectors

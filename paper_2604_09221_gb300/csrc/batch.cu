@@ -89,6 +89,8 @@ __global__ void __launch_bounds__(T)
   const TcScratch<K> S{(G ? gscratch + (size_t)blockIdx.x * K::WORDS * T
                          : reinterpret_cast<u32 *>(smem + toff + 128)) +
                         threadIdx.x};
+  // global scratch: the label slots of the sweep in shared memory
+  u32 *const ls = G ? reinterpret_cast<u32 *>(smem + toff + 128) + threadIdx.x : nullptr;
   if (threadIdx.x == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(1u));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -153,7 +155,7 @@ __global__ void __launch_bounds__(T)
 #pragma unroll
         for (u32 w = 0; w < K::W; ++w) sg.w[w] = tc_splitmix64((J.base + idx) * K::W + w);
         sg.w[K::W - 1] &= tc_top_mask(K::NPOINTS, K::W);
-        key = tc_table_classify<K>(sg, tab, off_fan, off_vext, S, err);
+        key = tc_table_classify<K>(sg, tab, off_fan, off_vext, S, err, ls);
         u64 any = 0;
 #pragma unroll
         for (u32 w = 0; w < K::CW; ++w) {
@@ -226,9 +228,11 @@ JobsFn jobs_fn_dt(int d, int t, bool g) {
   }
 }
 
-size_t jobs_smem(int d, int t, uint32_t table_words, bool g) {
+// ls_words: label-slot words per thread (global scratch: kept in shared memory)
+size_t jobs_smem(int d, int t, uint32_t table_words, uint32_t ls_words, bool g) {
   const TcLayout L = tc_layout(d, true, t);
-  return ((size_t)table_words * 4 + 127) / 128 * 128 + 128 + (g ? 0 : (size_t)L.words * 4 * t);
+  return ((size_t)table_words * 4 + 127) / 128 * 128 + 128 +
+         (g ? (size_t)ls_words * 4 * t : (size_t)L.words * 4 * t);
 }
 
 size_t scratch_words(int d, int t) { return (size_t)tc_layout(d, true, t).words * t; }
@@ -255,6 +259,7 @@ struct ts_batch {
     u32 *scratch = nullptr;     // global scratch (grid x threads x words)
     size_t scratch_bytes = 0;
     uint32_t table_words = 0, off_fan = 0, off_vext = 0;
+    uint32_t ls_words = 0;      // label-slot words per thread (largest of the group's tables)
     std::vector<int> jobs;      // indices into the batch's job list
     DevJob *d_jobs = nullptr;   // device job table (sorted as `jobs`)
     uint64_t items = 0;
@@ -287,7 +292,7 @@ struct ts_batch {
   int ftier = -1;
   unsigned fgrid = 1;
   size_t fsmem = 0;
-  uint32_t ftoff = 0, fws = 0;
+  uint32_t ftoff = 0, fls = 0, fws = 0;
   uint32_t *fscratch = nullptr;
   size_t fscratch_bytes = 0;
   unsigned long long *d_fwork = nullptr;
@@ -325,7 +330,7 @@ cudaError_t prepare_group(ts_batch::Group &g) {
   } else {
     g.fn = jobs_fn_dt(g.d, g.threads, g.global);
     if (!g.fn) return cudaErrorInvalidConfiguration;
-    g.smem = jobs_smem(g.d, g.threads, g.table_words, g.global);
+    g.smem = jobs_smem(g.d, g.threads, g.table_words, g.ls_words, g.global);
     e = cudaFuncSetAttribute((const void *)g.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)g.smem);
     if (e != cudaSuccess) return e;
@@ -377,7 +382,7 @@ cudaError_t prepare_fused(ts_batch *b) {
   });
   std::vector<FusedJob> fj;
   uint64_t items = 0;
-  uint32_t maxtab = 0, wsw = 0;
+  uint32_t maxtab = 0, wsw = 0, lsw = 0;
   int dmax = 0;
   bool anywarp = false;
   for (const ts_batch::Group *g : gs) {
@@ -406,6 +411,8 @@ cudaError_t prepare_fused(ts_batch *b) {
         x.tab_words = t->lay.words;
         x.off_fan = t->lay.off_fan;
         x.off_vext = t->lay.off_vext;
+        const uint32_t epw = tc_layout(g->d, true, kFusedThreads).epw;
+        lsw = std::max(lsw, (t->lay.nslots + epw - 1) / epw);
       }
       maxtab = std::max(maxtab, x.tab_words);
       items += (x.n + x.chunk - 1) / x.chunk;
@@ -416,7 +423,8 @@ cudaError_t prepare_fused(ts_batch *b) {
   const int tier = anywarp ? kFusedWarpTier : fused_tier(dmax);
   if (tier < 0 || fj.empty()) return cudaErrorInvalidConfiguration;
   const uint32_t toff = (maxtab * 4 + 127) / 128 * 128;
-  const size_t smem = (size_t)toff + 128 + (anywarp ? (size_t)4 * wsw * 4 : 0);
+  const size_t smem = (size_t)toff + 128 + (size_t)kFusedThreads * lsw * 4 +
+                      (anywarp ? (size_t)4 * wsw * 4 : 0);
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   int per_sm = 0, sms = 0, dev = 0;
   cudaError_t e = fused_occupancy(tier, smem, &per_sm);
@@ -450,6 +458,7 @@ cudaError_t prepare_fused(ts_batch *b) {
   b->fgrid = grid;
   b->fsmem = smem;
   b->ftoff = toff;
+  b->fls = lsw;
   b->fws = wsw;
   return cudaSuccess;
 }
@@ -464,7 +473,7 @@ cudaError_t enqueue(ts_batch *b, cudaStream_t st) {
   if (b->fused) {  // one persistent kernel for every job of every degree
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_fwork, 0, sizeof(unsigned long long), st);
     if (e == cudaSuccess)
-      e = fused_launch(b->ftier, b->fgrid, b->fsmem, b->ftoff, b->fws, b->d_fjobs,
+      e = fused_launch(b->ftier, b->fgrid, b->fsmem, b->ftoff, b->fls, b->fws, b->d_fjobs,
                        (uint32_t)b->jobs.size(), b->fitems, b->d_fwork, b->d_err, b->d_failed,
                        b->fscratch, st);
     return e;
@@ -617,7 +626,11 @@ ts_status ts_batch_create(int njobs, ts_tri *const *tris, const uint64_t *counts
       table_defaults(g);
       b->groups.push_back(g);
     }
-    b->groups[gi[t->d]].jobs.push_back(j);
+    auto &grp = b->groups[gi[t->d]];
+    grp.jobs.push_back(j);
+    grp.table_words = std::max(grp.table_words, t->lay.words);
+    const uint32_t epw = (uint32_t)tc_layout(t->d, true, 32).epw;
+    grp.ls_words = std::max(grp.ls_words, (t->lay.nslots + epw - 1) / epw);
   }
   if (e == cudaSuccess) {
     std::vector<int> spec;

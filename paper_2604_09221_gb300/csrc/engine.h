@@ -29,7 +29,8 @@ constexpr uint64_t kCountMask = (1ull << 62) - 1;
 struct TableLayout {
   uint32_t V, NF;
   uint32_t off_vdesc, off_fan, off_vext;
-  uint32_t words;  // padded to a multiple of 4 (16-byte TMA granule)
+  uint32_t words;   // padded to a multiple of 4 (16-byte TMA granule)
+  uint32_t nslots;  // label slots the sweep uses (lab_slots)
 };
 
 // Tables of the warp-per-instance kernels (32-bit words, vertex ids in the
@@ -214,10 +215,11 @@ uint32_t fused_slab_words(int tier);  // global scratch words per thread of a ti
 uint32_t fused_warp_words(int d);     // shared words of one warp of a degree-d warp tile
 cudaError_t fused_occupancy(int tier, size_t smem, int *blocks_per_sm);
 cudaError_t fused_attrs(int tier, int *regs, int *local_bytes);
-// smem = toff (the tables, 128-byte aligned) + 128 + 4 x ws_stride words
+// smem = toff (the tables, 128-byte aligned) + 128 + kFusedThreads x
+// ls_words words (label slots of the thread tiles) + 4 x ws_stride words
 // (warp tiles); scratch: grid x kFusedThreads x fused_slab_words(tier) words.
-cudaError_t fused_launch(int tier, unsigned grid, size_t smem, uint32_t toff, uint32_t ws_stride,
-                         const FusedJob *jobs, uint32_t njobs, uint64_t items,
+cudaError_t fused_launch(int tier, unsigned grid, size_t smem, uint32_t toff, uint32_t ls_words,
+                         uint32_t ws_stride, const FusedJob *jobs, uint32_t njobs, uint64_t items,
                          unsigned long long *work, uint32_t *err, unsigned long long *failed,
                          uint32_t *scratch, cudaStream_t st);
 }  // namespace tcurve

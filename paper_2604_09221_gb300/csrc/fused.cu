@@ -55,10 +55,13 @@ struct FusedSlab {
   static constexpr u32 WORDS = slab_words_upto(DHI);
 };
 
-// Thread per instance: chunk sign vectors of job J from index `first`.
+// Thread per instance: chunk sign vectors of job J from index `first`.  The
+// label slots of the sweep (one load per fan entry) sit in shared memory
+// (ls: this thread's word 0, word i at ls[i * 128]); the rest of the
+// scratch in global memory.
 template <int D>
 __device__ __forceinline__ void thread_item(const FusedJob &__restrict__ J, u64 first, const u32 *tab,
-                                            u32 *gslab, u32 *err_word, u32 &err,
+                                            u32 *gslab, u32 *ls, u32 *err_word, u32 &err,
                                             unsigned long long &failed) {
   typedef TcTableK<D, (int)kFT, true> K;
   const TcScratch<K> S{gslab + threadIdx.x};
@@ -71,7 +74,7 @@ __device__ __forceinline__ void thread_item(const FusedJob &__restrict__ J, u64 
 #pragma unroll
       for (u32 w = 0; w < K::W; ++w) sg.w[w] = tc_splitmix64((J.base + idx) * K::W + w);
       sg.w[K::W - 1] &= tc_top_mask(K::NPOINTS, K::W);
-      key = tc_table_classify<K>(sg, tab, J.off_fan, J.off_vext, S, err);
+      key = tc_table_classify<K>(sg, tab, J.off_fan, J.off_vext, S, err, ls);
       u64 any = 0;
 #pragma unroll
       for (u32 w = 0; w < K::CW; ++w) {
@@ -145,7 +148,7 @@ __device__ __forceinline__ void warp_item(const FusedJob &__restrict__ J, u64 fi
 // made the narrower tiers spill.
 template <int D, int DHI, bool WARP>
 __device__ __forceinline__ void run_item(const FusedJob &__restrict__ J, u64 first, const u32 *tab,
-                                         u32 *gslab, u32 *ws, u32 *err_word, u32 &err,
+                                         u32 *gslab, u32 *ls, u32 *ws, u32 *err_word, u32 &err,
                                          unsigned long long &failed) {
   if constexpr (D <= DHI) {
     if constexpr (WARP && D >= kFusedWarpFrom) {
@@ -154,23 +157,26 @@ __device__ __forceinline__ void run_item(const FusedJob &__restrict__ J, u64 fir
         return;
       }
     }
-    thread_item<D>(J, first, tab, gslab, err_word, err, failed);
+    thread_item<D>(J, first, tab, gslab, ls, err_word, err, failed);
   }
 }
 
-// smem: [tables (toff bytes)] [mbarrier | work slot (128 bytes)] [warp
-// states: 4 x ws_stride words, warp tiles only].
+// smem: [tables (toff bytes)] [mbarrier | work slot (128 bytes)] [label
+// slots: ls_words x 128 words] [warp states: 4 x ws_stride words, warp
+// tiles only].
 template <int DHI, int MINB, bool WARP>
 __global__ void __launch_bounds__(kFT, MINB)
     fused_jobs_kernel(const FusedJob *__restrict__ jobs, u32 njobs, u64 total_items,
                       unsigned long long *work, u32 *err_word, unsigned long long *failed_word,
-                      u32 *gscratch, u32 toff, u32 ws_stride) {
+                      u32 *gscratch, u32 toff, u32 ls_words, u32 ws_stride) {
   extern __shared__ __align__(128) uint8_t smem[];
   constexpr u32 SLAB = FusedSlab<DHI>::WORDS;
   u32 *tab = reinterpret_cast<u32 *>(smem);
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + toff);
   unsigned long long *slot = reinterpret_cast<unsigned long long *>(smem + toff + 64);
-  u32 *ws = reinterpret_cast<u32 *>(smem + toff + 128) + (threadIdx.x >> 5) * ws_stride;
+  u32 *ls = reinterpret_cast<u32 *>(smem + toff + 128) + threadIdx.x;
+  u32 *ws = reinterpret_cast<u32 *>(smem + toff + 128) + ls_words * kFT +
+            (threadIdx.x >> 5) * ws_stride;
   u32 *gslab = gscratch + (size_t)blockIdx.x * SLAB * kFT;
   if (threadIdx.x == 0) mbar_init(bar, 1);
   __syncthreads();
@@ -208,7 +214,7 @@ __global__ void __launch_bounds__(kFT, MINB)
     const u64 first = (c - J.item0) * (u64)J.chunk;
     switch (J.d) {
 #define TC_FUSED_CASE(d) \
-  case d: run_item<d, DHI, WARP>(J, first, tab, gslab, ws, err_word, err, failed); break;
+  case d: run_item<d, DHI, WARP>(J, first, tab, gslab, ls, ws, err_word, err, failed); break;
       TC_FUSED_CASE(1) TC_FUSED_CASE(2) TC_FUSED_CASE(3) TC_FUSED_CASE(4) TC_FUSED_CASE(5)
       TC_FUSED_CASE(6) TC_FUSED_CASE(7) TC_FUSED_CASE(8) TC_FUSED_CASE(9) TC_FUSED_CASE(10)
       TC_FUSED_CASE(11) TC_FUSED_CASE(12) TC_FUSED_CASE(13) TC_FUSED_CASE(14)
@@ -222,7 +228,7 @@ __global__ void __launch_bounds__(kFT, MINB)
 }
 
 typedef void (*FusedFn)(const FusedJob *, u32, u64, unsigned long long *, u32 *,
-                        unsigned long long *, u32 *, u32, u32);
+                        unsigned long long *, u32 *, u32, u32, u32);
 
 // Tiers 0..3 thread per instance only; kFusedWarpTier: the widest tier
 // with warp bodies (any batch with a warp tile runs it).
@@ -298,13 +304,14 @@ cudaError_t fused_attrs(int tier, int *regs, int *local_bytes) {
   return cudaSuccess;
 }
 
-cudaError_t fused_launch(int tier, unsigned grid, size_t smem, uint32_t toff, uint32_t ws_stride,
-                         const FusedJob *jobs, uint32_t njobs, uint64_t items,
+cudaError_t fused_launch(int tier, unsigned grid, size_t smem, uint32_t toff, uint32_t ls_words,
+                         uint32_t ws_stride, const FusedJob *jobs, uint32_t njobs, uint64_t items,
                          unsigned long long *work, uint32_t *err, unsigned long long *failed,
                          uint32_t *scratch, cudaStream_t st) {
   const FusedFn fn = tier_fn(tier);
   if (!fn) return cudaErrorInvalidValue;
-  fn<<<grid, kFT, smem, st>>>(jobs, njobs, items, work, err, failed, scratch, toff, ws_stride);
+  fn<<<grid, kFT, smem, st>>>(jobs, njobs, items, work, err, failed, scratch, toff, ls_words,
+                              ws_stride);
   return cudaGetLastError();
 }
 

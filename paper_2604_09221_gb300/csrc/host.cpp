@@ -254,7 +254,8 @@ bool pack_diamond_tables(const Diamond &D, std::vector<uint32_t> &tables, TableL
   const int V = D.V;
   constexpr uint32_t kNone = 1023u;
   if (V > (int)kNone) return false;
-  const std::vector<int> slot = lab_slots(D, nullptr);
+  int nslots = 0;
+  const std::vector<int> slot = lab_slots(D, &nslots);
   std::vector<uint32_t> vdesc(V), fan, vext(V, kNone | (kNone << 10) | (kNone << 20));
   for (int v = 0; v < V; ++v) {
     const int m = (int)D.fan[v].size();
@@ -293,6 +294,7 @@ bool pack_diamond_tables(const Diamond &D, std::vector<uint32_t> &tables, TableL
   L.off_fan = L.off_vdesc + V;
   L.off_vext = L.off_fan + L.NF;
   L.words = (L.off_vext + V + 3) & ~3u;
+  L.nslots = (uint32_t)nslots;
   tables.assign(L.words, 0);
   std::copy(vdesc.begin(), vdesc.end(), tables.begin() + L.off_vdesc);
   std::copy(fan.begin(), fan.end(), tables.begin() + L.off_fan);

@@ -40,10 +40,19 @@ namespace {
 template <int D, bool G>
 using TableK = TcTableK<D, G ? 128 : 256, G>;
 
+// With global scratch the label slots of the sweep (one load per fan
+// entry) stay in shared memory: ceil(nslots / labels per word) words per
+// thread, interleaved like the scratch.
+template <class K>
+__host__ __device__ constexpr uint32_t slot_words(uint32_t nslots) {
+  return (nslots + TcScratch<K>::EPW - 1) / TcScratch<K>::EPW;
+}
+
 template <class K, bool G>
-constexpr size_t smem_bytes(uint32_t table_words, bool with_hash) {
+constexpr size_t smem_bytes(uint32_t table_words, uint32_t nslots, bool with_hash) {
   return ((size_t)table_words * 4 + 127) / 128 * 128 + 128 +
-         (G ? 0 : (size_t)K::WORDS * 4 * K::THREADS) + (with_hash ? (size_t)K::HASH * 16 : 0);
+         (G ? (size_t)slot_words<K>(nslots) * 4 * K::THREADS : (size_t)K::WORDS * 4 * K::THREADS) +
+         (with_hash ? (size_t)K::HASH * 16 : 0);
 }
 
 struct SmemLayout {
@@ -51,12 +60,13 @@ struct SmemLayout {
   uint64_t *bar;
   unsigned long long *chunk;  // work-chunk broadcast slot (inside the barrier line)
   u32 *scratch;
+  u32 *slots;  // label slots in shared memory (global scratch), else null
   u64 *hkeys;
   unsigned long long *hcnt;
 };
 
 template <class K, bool G>
-__device__ SmemLayout carve(uint8_t *smem, uint32_t table_words, u32 *gscratch) {
+__device__ SmemLayout carve(uint8_t *smem, uint32_t table_words, uint32_t nslots, u32 *gscratch) {
   SmemLayout s;
   size_t off = 0;
   s.tab = reinterpret_cast<uint32_t *>(smem);
@@ -66,8 +76,11 @@ __device__ SmemLayout carve(uint8_t *smem, uint32_t table_words, u32 *gscratch) 
   off += 128;
   if (G) {
     s.scratch = gscratch + (size_t)blockIdx.x * K::WORDS * K::THREADS;
+    s.slots = reinterpret_cast<u32 *>(smem + off);
+    off += (size_t)slot_words<K>(nslots) * 4 * K::THREADS;
   } else {
     s.scratch = reinterpret_cast<u32 *>(smem + off);
+    s.slots = nullptr;
     off += (size_t)K::WORDS * 4 * K::THREADS;
   }
   s.hkeys = reinterpret_cast<u64 *>(smem + off);
@@ -84,14 +97,16 @@ __global__ void __launch_bounds__(TableK<D, G>::THREADS)
                         uint32_t *err_word, u32 *gscratch) {
   typedef TableK<D, G> K;
   extern __shared__ __align__(128) uint8_t smem[];
-  SmemLayout M = carve<K, G>(smem, L.words, gscratch);
+  SmemLayout M = carve<K, G>(smem, L.words, L.nslots, gscratch);
   if (!stage_tables(M.tab, gtab, L.words * 4, M.bar, err_word)) return;
   const TcScratch<K> S{M.scratch + threadIdx.x};
+  u32 *const ls = G ? M.slots + threadIdx.x : nullptr;
   const u64 *sg = reinterpret_cast<const u64 *>(signs);
   uint32_t err = 0;
   for (uint64_t i = (uint64_t)blockIdx.x * K::THREADS + threadIdx.x; i < n;
        i += (uint64_t)gridDim.x * K::THREADS) {
-    const TcCodeOut<K> c = tc_table_classify<K>(tc_load_sig<K>(sg, i), M.tab, L.off_fan, L.off_vext, S, err);
+    const TcCodeOut<K> c =
+        tc_table_classify<K>(tc_load_sig<K>(sg, i), M.tab, L.off_fan, L.off_vext, S, err, ls);
 #pragma unroll
     for (u32 w = 0; w < K::CW; ++w) codes[i * K::CW + w] = c.w[w];
   }
@@ -107,13 +122,14 @@ __global__ void __launch_bounds__(TableK<D, G>::THREADS)
   typedef TableK<D, G> K;
   constexpr uint32_t kChunk = K::THREADS * 16;
   extern __shared__ __align__(128) uint8_t smem[];
-  SmemLayout M = carve<K, G>(smem, L.words, gscratch);
+  SmemLayout M = carve<K, G>(smem, L.words, L.nslots, gscratch);
   for (int s = threadIdx.x; s < (int)K::HASH; s += K::THREADS) {
     M.hkeys[s] = 0;
     M.hcnt[s] = 0;
   }
   if (!stage_tables(M.tab, gtab, L.words * 4, M.bar, h.d_err)) return;
   const TcScratch<K> S{M.scratch + threadIdx.x};
+  u32 *const ls = G ? M.slots + threadIdx.x : nullptr;
   uint32_t err = 0;
   unsigned long long failed = 0;
   for (;;) {
@@ -127,7 +143,7 @@ __global__ void __launch_bounds__(TableK<D, G>::THREADS)
       TcCodeOut<K> key{};
       if (idx < total) {
         key = tc_table_classify<K>(tc_enum_sig<K::W>(lo + idx, flags, D), M.tab, L.off_fan,
-                                   L.off_vext, S, err);
+                                   L.off_vext, S, err, ls);
         u64 any = 0;
 #pragma unroll
         for (u32 w = 0; w < K::CW; ++w) any |= key.w[w];
@@ -249,7 +265,7 @@ template <int D, bool G>
 cudaError_t real_schemes_dg(const ts_tri *t, const uint64_t *signs, uint64_t n, uint64_t *codes,
                             cudaStream_t st) {
   typedef TableK<D, G> K;
-  const size_t smem = smem_bytes<K, G>(t->lay.words, false);
+  const size_t smem = smem_bytes<K, G>(t->lay.words, t->lay.nslots, false);
   unsigned grid = 0;
   cudaError_t e = persistent_grid(real_schemes_kernel<D, G>, K::THREADS, smem,
                                   (n + K::THREADS - 1) / K::THREADS, &grid);
@@ -265,7 +281,7 @@ template <int D, bool G>
 cudaError_t enumerate_dg(const ts_tri *t, uint64_t lo, uint64_t hi, uint32_t flags, ts_hist *h,
                          cudaStream_t st) {
   typedef TableK<D, G> K;
-  const size_t smem = smem_bytes<K, G>(t->lay.words, true);
+  const size_t smem = smem_bytes<K, G>(t->lay.words, t->lay.nslots, true);
   const uint64_t total = hi - lo;
   const uint64_t chunk = (uint64_t)K::THREADS * 16;
   unsigned grid = 0;

@@ -693,12 +693,19 @@ __device__ __noinline__ void tc_backend_wide(const TcScratch<K> &S, u32 nl, u32 
 // vertices are stored in the scratch's [lab] region with the vertex's sign in
 // the top bit (labels need at most 15 of 16 / 7 of 8 bits), so a fan entry
 // reads its neighbour's label and sign in one load.
+// lw: word 0 of this thread's label slots, word i at lw[i * THREADS] (by
+// default the scratch's [lab] region; a kernel may keep them in shared
+// memory while the rest of the scratch is in global memory).
 template <class K, class SIG>
 __device__ __forceinline__ void tc_sweep_table(const SIG &sig, const u32 *__restrict__ vdesc,
                                                const u32 *__restrict__ fan,
                                                const u32 *__restrict__ vext, u32 v0, u32 v1,
-                                               const TcScratch<K> &S, u32 &nl, u32 &nb, u32 &np) {
+                                               const TcScratch<K> &S, u32 *lw, u32 &nl, u32 &nb,
+                                               u32 &np) {
   typedef TcScratch<K> TS;
+  auto slot = [&](u32 i) -> typename TS::lab_t * {
+    return reinterpret_cast<typename TS::lab_t *>(lw + (i / TS::EPW) * K::THREADS) + (i % TS::EPW);
+  };
   u32 fs = 0;  // the first fan entry of v: fans are stored in sweep order
   for (u32 v = 0; v < v0; ++v) fs += (vdesc[v] >> 9) & 127u;
   for (u32 v = v0; v < v1; ++v) {
@@ -736,26 +743,26 @@ __device__ __forceinline__ void tc_sweep_table(const SIG &sig, const u32 *__rest
     for (u32 i = 0; i < PRE; ++i)
       if (i < m) {
         fpre[i] = fan[fs + i];
-        rpre[i] = *S.lab(K::OFF_LAB, fpre[i] & 1023u);
+        rpre[i] = *slot(fpre[i] & 1023u);
       }
 #pragma unroll
     for (u32 i = 0; i < PRE; ++i)
       if (i < m) entry(i, fpre[i], rpre[i]);
     for (u32 i = PRE; i < m; ++i) {
       const u32 f = fan[fs + i];
-      entry(i, f, *S.lab(K::OFF_LAB, f & 1023u));
+      entry(i, f, *slot(f & 1023u));
     }
     if (!any) {
       lv = nl;
       tc_newlab(S, nl, l0);
       ++nl;
     }
-    *S.lab(K::OFF_LAB, (desc >> 16) & 1023u) = (typename TS::lab_t)(lv | (sv << SB));
+    *slot((desc >> 16) & 1023u) = (typename TS::lab_t)(lv | (sv << SB));
     fs += m;
     if (!ext) continue;
     if ((x & 1023u) != TC_TAB_NONE) {  // the antipodal partner, reached earlier
       S.word(K::OFF_PEND, np) =
-          ((u32)*S.lab(K::OFF_LAB, x & 1023u) & TS::LOW) | (lv << 16) | 0x80000000u;
+          ((u32)*slot(x & 1023u) & TS::LOW) | (lv << 16) | 0x80000000u;
       ++np;
     }
     if (K::D % 2) {  // crossed boundary edges, for the pseudoline's region
@@ -763,7 +770,7 @@ __device__ __forceinline__ void tc_sweep_table(const SIG &sig, const u32 *__rest
       for (u32 sh = 10; sh <= 20; sh += 10) {
         const u32 b = (x >> sh) & 1023u;
         if (b == TC_TAB_NONE) continue;
-        const u32 rb = *S.lab(K::OFF_LAB, b);
+        const u32 rb = *slot(b);
         if ((rb >> SB) != sv) {
           tc_bpair(S, nb, rb & TS::LOW, lv);
           ++nb;
@@ -771,6 +778,15 @@ __device__ __forceinline__ void tc_sweep_table(const SIG &sig, const u32 *__rest
       }
     }
   }
+}
+
+// The same with the label slots in the scratch's [lab] region.
+template <class K, class SIG>
+__device__ __forceinline__ void tc_sweep_table(const SIG &sig, const u32 *__restrict__ vdesc,
+                                               const u32 *__restrict__ fan,
+                                               const u32 *__restrict__ vext, u32 v0, u32 v1,
+                                               const TcScratch<K> &S, u32 &nl, u32 &nb, u32 &np) {
+  tc_sweep_table(sig, vdesc, fan, vext, v0, v1, S, S.w + K::OFF_LAB * K::THREADS, nl, nb, np);
 }
 
 // ------------------------------------------------------------ histogram ----

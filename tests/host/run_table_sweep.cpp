@@ -84,6 +84,7 @@ int run(const char *edge_file, int n, bool warp) {
   if (orc_triangles_from_edges(D, ne, e.data(), otri.data(), D * D) != D * D) return 2;
   std::vector<u32> scratch(K::WORDS > WK::WORDS ? K::WORDS : WK::WORDS, 0xA5A5A5A5u);
   const TcScratch<K> S{scratch.data()};
+  std::vector<u32> slots((t.lay.nslots + TcScratch<K>::EPW - 1) / TcScratch<K>::EPW, 0x5A5A5A5Au);
   const u32 *wt = t.host_wtables.data();
   const int cw = orc_code_words(D);
   int bad = 0;
@@ -118,7 +119,11 @@ int run(const char *edge_file, int n, bool warp) {
                                 wt + t.wlay.off_anti, t.wlay.nanti, wt + t.wlay.off_bedge,
                                 t.wlay.nbedge, scratch.data(), got.w);
     } else {
-      got = tc_table_classify<K>(sg, t.host_tables.data(), t.lay.off_fan, t.lay.off_vext, S, err);
+      // odd instances keep the label slots apart from the scratch, as the
+      // kernels with global scratch do (slots in shared memory); the slot
+      // buffer holds exactly the words the table's slots need
+      got = tc_table_classify<K>(sg, t.host_tables.data(), t.lay.off_fan, t.lay.off_vext, S, err,
+                                 i % 2 ? slots.data() : nullptr);
     }
     uint64_t want[4] = {0, 0, 0, 0};
     const int rc = orc_real_scheme(D, otri.data(), (const uint64_t *)sg.w, want, cw, nullptr);
