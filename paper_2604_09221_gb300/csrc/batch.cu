@@ -143,6 +143,11 @@ __global__ void __launch_bounds__(T)
       }
       phase ^= 1u;
       cur = j;
+      if (G) {  // label slots in shared memory, found by the fan entries' offsets
+        tc_fan_to_offsets(tab + off_fan, off_vext - off_fan, TcScratch<K>::EPW, K::LBYTES, T,
+                          threadIdx.x, T);
+        __syncthreads();
+      }
     }
     const DevJob J = jobs[j];
     const u64 first = (c - J.chunk0) * (u64)chunk;
@@ -155,7 +160,7 @@ __global__ void __launch_bounds__(T)
 #pragma unroll
         for (u32 w = 0; w < K::W; ++w) sg.w[w] = tc_splitmix64((J.base + idx) * K::W + w);
         sg.w[K::W - 1] &= tc_top_mask(K::NPOINTS, K::W);
-        key = tc_table_classify<K>(sg, tab, off_fan, off_vext, S, err, ls);
+        key = tc_table_classify<K, G>(sg, tab, off_fan, off_vext, S, err, ls);
         u64 any = 0;
 #pragma unroll
         for (u32 w = 0; w < K::CW; ++w) {

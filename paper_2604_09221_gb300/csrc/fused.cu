@@ -57,8 +57,9 @@ struct FusedSlab {
 
 // Thread per instance: chunk sign vectors of job J from index `first`.  The
 // label slots of the sweep (one load per fan entry) sit in shared memory
-// (ls: this thread's word 0, word i at ls[i * 128]); the rest of the
-// scratch in global memory.
+// (ls: this thread's word 0, word i at ls[i * 128]), and the staged fan
+// entries carry their slots' byte offsets; the rest of the scratch is in
+// global memory.
 template <int D>
 __device__ __forceinline__ void thread_item(const FusedJob &__restrict__ J, u64 first, const u32 *tab,
                                             u32 *gslab, u32 *ls, u32 *err_word, u32 &err,
@@ -74,7 +75,7 @@ __device__ __forceinline__ void thread_item(const FusedJob &__restrict__ J, u64 
 #pragma unroll
       for (u32 w = 0; w < K::W; ++w) sg.w[w] = tc_splitmix64((J.base + idx) * K::W + w);
       sg.w[K::W - 1] &= tc_top_mask(K::NPOINTS, K::W);
-      key = tc_table_classify<K>(sg, tab, J.off_fan, J.off_vext, S, err, ls);
+      key = tc_table_classify<K, true>(sg, tab, J.off_fan, J.off_vext, S, err, ls);
       u64 any = 0;
 #pragma unroll
       for (u32 w = 0; w < K::CW; ++w) {
@@ -210,6 +211,12 @@ __global__ void __launch_bounds__(kFT, MINB)
       }
       phase ^= 1u;
       cur = J.tab;
+      if (!J.warp) {  // thread tiles find a fan entry's label slot by its offset
+        const u32 d = J.d, lb = 2 * d * d + 2 * d + 1 <= 126 ? 1u : 2u;  // tc_layout's lbytes
+        tc_fan_to_offsets(tab + J.off_fan, J.off_vext - J.off_fan, 4u / lb, lb, kFT, threadIdx.x,
+                          kFT);
+        __syncthreads();
+      }
     }
     const u64 first = (c - J.item0) * (u64)J.chunk;
     switch (J.d) {

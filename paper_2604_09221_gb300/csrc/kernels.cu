@@ -88,6 +88,16 @@ __device__ SmemLayout carve(uint8_t *smem, uint32_t table_words, uint32_t nslots
   return s;
 }
 
+// With global scratch the label slots are in shared memory and the staged
+// fan entries are rewritten to their slots' byte offsets (the whole block,
+// then a barrier).
+template <class K>
+__device__ __forceinline__ void fan_offsets(u32 *tab, const TableLayout &L) {
+  tc_fan_to_offsets(tab + L.off_fan, L.NF, TcScratch<K>::EPW, K::LBYTES, K::THREADS, threadIdx.x,
+                    K::THREADS);
+  __syncthreads();
+}
+
 // ----------------------------------------------------- query kernel ----
 
 template <int D, bool G>
@@ -101,12 +111,13 @@ __global__ void __launch_bounds__(TableK<D, G>::THREADS)
   if (!stage_tables(M.tab, gtab, L.words * 4, M.bar, err_word)) return;
   const TcScratch<K> S{M.scratch + threadIdx.x};
   u32 *const ls = G ? M.slots + threadIdx.x : nullptr;
+  if (G) fan_offsets<K>(M.tab, L);
   const u64 *sg = reinterpret_cast<const u64 *>(signs);
   uint32_t err = 0;
   for (uint64_t i = (uint64_t)blockIdx.x * K::THREADS + threadIdx.x; i < n;
        i += (uint64_t)gridDim.x * K::THREADS) {
     const TcCodeOut<K> c =
-        tc_table_classify<K>(tc_load_sig<K>(sg, i), M.tab, L.off_fan, L.off_vext, S, err, ls);
+        tc_table_classify<K, G>(tc_load_sig<K>(sg, i), M.tab, L.off_fan, L.off_vext, S, err, ls);
 #pragma unroll
     for (u32 w = 0; w < K::CW; ++w) codes[i * K::CW + w] = c.w[w];
   }
@@ -130,6 +141,7 @@ __global__ void __launch_bounds__(TableK<D, G>::THREADS)
   if (!stage_tables(M.tab, gtab, L.words * 4, M.bar, h.d_err)) return;
   const TcScratch<K> S{M.scratch + threadIdx.x};
   u32 *const ls = G ? M.slots + threadIdx.x : nullptr;
+  if (G) fan_offsets<K>(M.tab, L);
   uint32_t err = 0;
   unsigned long long failed = 0;
   for (;;) {
@@ -142,8 +154,8 @@ __global__ void __launch_bounds__(TableK<D, G>::THREADS)
       const uint64_t idx = base + j + threadIdx.x;
       TcCodeOut<K> key{};
       if (idx < total) {
-        key = tc_table_classify<K>(tc_enum_sig<K::W>(lo + idx, flags, D), M.tab, L.off_fan,
-                                   L.off_vext, S, err, ls);
+        key = tc_table_classify<K, G>(tc_enum_sig<K::W>(lo + idx, flags, D), M.tab, L.off_fan,
+                                      L.off_vext, S, err, ls);
         u64 any = 0;
 #pragma unroll
         for (u32 w = 0; w < K::CW; ++w) any |= key.w[w];

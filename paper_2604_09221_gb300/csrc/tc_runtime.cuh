@@ -693,10 +693,30 @@ __device__ __noinline__ void tc_backend_wide(const TcScratch<K> &S, u32 nl, u32 
 // vertices are stored in the scratch's [lab] region with the vertex's sign in
 // the top bit (labels need at most 15 of 16 / 7 of 8 bits), so a fan entry
 // reads its neighbour's label and sign in one load.
+// Byte offset of label slot i from a thread's word 0 (slots interleaved by
+// word across `threads` threads, epw labels of lbytes bytes per word).
+__device__ __forceinline__ u32 tc_slot_offset(u32 i, u32 epw, u32 lbytes, u32 threads) {
+  return (i / epw) * threads * 4u + (i % epw) * lbytes;
+}
+
+// Rewrite staged fan entries (nf of them) for OFF sweeps: bits 0..18 (label
+// slot, k(u), c(u), which the sweep does not read) become the byte offset of
+// the neighbour's label slot; the link bit (19) stays.  Called by the
+// threads [t, t + stride) of a block right after staging, before a barrier.
+__device__ __forceinline__ void tc_fan_to_offsets(u32 *fan, u32 nf, u32 epw, u32 lbytes,
+                                                  u32 threads, u32 t, u32 stride) {
+  for (u32 i = t; i < nf; i += stride) {
+    const u32 f = fan[i];
+    fan[i] = (f & ~0x7FFFFu) | tc_slot_offset(f & 1023u, epw, lbytes, threads);
+  }
+}
+
 // lw: word 0 of this thread's label slots, word i at lw[i * THREADS] (by
 // default the scratch's [lab] region; a kernel may keep them in shared
-// memory while the rest of the scratch is in global memory).
-template <class K, class SIG>
+// memory while the rest of the scratch is in global memory).  OFF: the fan
+// entries carry byte offsets of their slots (tc_fan_to_offsets), so a fan
+// entry finds its neighbour's label with one mask and one add.
+template <class K, bool OFF = false, class SIG>
 __device__ __forceinline__ void tc_sweep_table(const SIG &sig, const u32 *__restrict__ vdesc,
                                                const u32 *__restrict__ fan,
                                                const u32 *__restrict__ vext, u32 v0, u32 v1,
@@ -705,6 +725,13 @@ __device__ __forceinline__ void tc_sweep_table(const SIG &sig, const u32 *__rest
   typedef TcScratch<K> TS;
   auto slot = [&](u32 i) -> typename TS::lab_t * {
     return reinterpret_cast<typename TS::lab_t *>(lw + (i / TS::EPW) * K::THREADS) + (i % TS::EPW);
+  };
+  // the label slot a fan entry names
+  auto fslot = [&](u32 f) -> typename TS::lab_t * {
+    if constexpr (OFF)
+      return reinterpret_cast<typename TS::lab_t *>(reinterpret_cast<u8 *>(lw) + (f & 0x7FFFFu));
+    else
+      return slot(f & 1023u);
   };
   u32 fs = 0;  // the first fan entry of v: fans are stored in sweep order
   for (u32 v = 0; v < v0; ++v) fs += (vdesc[v] >> 9) & 127u;
@@ -719,13 +746,12 @@ __device__ __forceinline__ void tc_sweep_table(const SIG &sig, const u32 *__rest
       np = 0;
     }
     constexpr u32 SB = 8u * K::LBYTES - 1u;  // the sign bit of a [lab] entry
-    u32 lv = 0, l0 = TS::NONE, any = 0, prev = 0;
+    u32 lv = 0, any = 0, prev = 0;
     // one fan entry: its label and sign from the entry's label slot
-    auto entry = [&](u32 i, u32 f, u32 raw) {
+    auto entry = [&](u32 f, u32 raw) {
       const u32 lu = raw & TS::LOW;
       const u32 e = (raw >> SB) ^ sv ^ 1u;
       const u32 st = e & ~(((f >> 19) & 1u) & prev) & 1u;  // e starts a run of the fan
-      l0 = i == 0 ? lu : l0;
       // a run after the first: join its label with the vertex's label
       // (a predicated store: no branch, and no write when nothing joins)
       if (st & any) S.word(K::OFF_PEND, np) = lv | (lu << 16);
@@ -743,16 +769,18 @@ __device__ __forceinline__ void tc_sweep_table(const SIG &sig, const u32 *__rest
     for (u32 i = 0; i < PRE; ++i)
       if (i < m) {
         fpre[i] = fan[fs + i];
-        rpre[i] = *slot(fpre[i] & 1023u);
+        rpre[i] = *fslot(fpre[i]);
       }
 #pragma unroll
     for (u32 i = 0; i < PRE; ++i)
-      if (i < m) entry(i, fpre[i], rpre[i]);
+      if (i < m) entry(fpre[i], rpre[i]);
     for (u32 i = PRE; i < m; ++i) {
       const u32 f = fan[fs + i];
-      entry(i, f, *slot(f & 1023u));
+      entry(f, *fslot(f));
     }
-    if (!any) {
+    if (!any) {  // a fresh label; its cand is the label of the first fan entry
+      const u32 l0 = m == 0 ? TS::NONE
+                            : ((PRE > 0 ? rpre[0] : (u32)*fslot(fan[fs])) & TS::LOW);
       lv = nl;
       tc_newlab(S, nl, l0);
       ++nl;
@@ -786,7 +814,8 @@ __device__ __forceinline__ void tc_sweep_table(const SIG &sig, const u32 *__rest
                                                const u32 *__restrict__ fan,
                                                const u32 *__restrict__ vext, u32 v0, u32 v1,
                                                const TcScratch<K> &S, u32 &nl, u32 &nb, u32 &np) {
-  tc_sweep_table(sig, vdesc, fan, vext, v0, v1, S, S.w + K::OFF_LAB * K::THREADS, nl, nb, np);
+  tc_sweep_table<K, false>(sig, vdesc, fan, vext, v0, v1, S, S.w + K::OFF_LAB * K::THREADS, nl,
+                           nb, np);
 }
 
 // ------------------------------------------------------------ histogram ----

@@ -34,16 +34,17 @@ struct TcCodeOut {
   u64 w[K::CW];
 };
 
-// lw: the label slots (tc_sweep_table), null for the scratch's [lab] region.
-template <class K>
+// lw: the label slots (tc_sweep_table), null for the scratch's [lab] region;
+// OFF: the tables' fan entries carry slot offsets (tc_fan_to_offsets).
+template <class K, bool OFF = false>
 __device__ __forceinline__ TcCodeOut<K> tc_table_classify(const TcSig<K::W> &sig,
                                                           const u32 *__restrict__ tab, u32 off_fan,
                                                           u32 off_vext, const TcScratch<K> &S,
                                                           u32 &err, u32 *lw = nullptr) {
   u32 nl = 0, nb = 0, np = 0;
   tc_clear_odd(S);
-  tc_sweep_table(sig, tab, tab + off_fan, tab + off_vext, 0, K::V, S,
-                 lw ? lw : S.w + K::OFF_LAB * K::THREADS, nl, nb, np);
+  tc_sweep_table<K, OFF>(sig, tab, tab + off_fan, tab + off_vext, 0, K::V, S,
+                         lw ? lw : S.w + K::OFF_LAB * K::THREADS, nl, nb, np);
   tc_unions(S, np);
   TcCodeOut<K> out;
   if constexpr (K::WIDE) {

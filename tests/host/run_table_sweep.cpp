@@ -85,6 +85,9 @@ int run(const char *edge_file, int n, bool warp) {
   std::vector<u32> scratch(K::WORDS > WK::WORDS ? K::WORDS : WK::WORDS, 0xA5A5A5A5u);
   const TcScratch<K> S{scratch.data()};
   std::vector<u32> slots((t.lay.nslots + TcScratch<K>::EPW - 1) / TcScratch<K>::EPW, 0x5A5A5A5Au);
+  std::vector<u32> offtab(t.host_tables);
+  tc_fan_to_offsets(offtab.data() + t.lay.off_fan, t.lay.NF, TcScratch<K>::EPW, K::LBYTES,
+                    K::THREADS, 0, 1);
   const u32 *wt = t.host_wtables.data();
   const int cw = orc_code_words(D);
   int bad = 0;
@@ -121,9 +124,15 @@ int run(const char *edge_file, int n, bool warp) {
     } else {
       // odd instances keep the label slots apart from the scratch, as the
       // kernels with global scratch do (slots in shared memory); the slot
-      // buffer holds exactly the words the table's slots need
-      got = tc_table_classify<K>(sg, t.host_tables.data(), t.lay.off_fan, t.lay.off_vext, S, err,
-                                 i % 2 ? slots.data() : nullptr);
+      // buffer holds exactly the words the table's slots need.  Every fourth
+      // instance also reads the tables with the fan entries rewritten to
+      // their slots' byte offsets, as those kernels stage them.
+      if (i % 4 == 3)
+        got = tc_table_classify<K, true>(sg, offtab.data(), t.lay.off_fan, t.lay.off_vext, S, err,
+                                         slots.data());
+      else
+        got = tc_table_classify<K>(sg, t.host_tables.data(), t.lay.off_fan, t.lay.off_vext, S, err,
+                                   i % 2 ? slots.data() : nullptr);
     }
     uint64_t want[4] = {0, 0, 0, 0};
     const int rc = orc_real_scheme(D, otri.data(), (const uint64_t *)sg.w, want, cw, nullptr);

@@ -129,7 +129,9 @@ def test_table_sweep_on_the_host(table_sweep_exe, tmp_path, d):
     has 4d - 1 earlier neighbours in T^diamond (the longest fans the join
     list's flush schedule has to fit).  Every other instance keeps its label
     slots in a buffer of their own, sized to the table's slot count, as the
-    kernels with global scratch keep them in shared memory."""
+    kernels with global scratch keep them in shared memory, and every fourth
+    one also reads fan entries rewritten to their slots' byte offsets, as
+    those kernels stage them."""
     cases = [("standard", ti.standard_triangulation(d))]
     if d >= 3:
         cases.append(("regular", ti.regular_triangulation(d, seed=100 + d)))
