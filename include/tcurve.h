@@ -199,9 +199,14 @@ ts_status ts_hist_clear(ts_hist *hist, void *stream);
  * positions 0, 1 and d+1 with TS_ENUM_REDUCED (bits carried past bit 63 go
  * to the second sign word); the splitmix64 stream with TS_ENUM_SPLITMIX.
  * Except with TS_ENUM_SPLITMIX, m(hi-1) < 2^|A| (a bound only for d <= 9
- * and, with TS_ENUM_REDUCED, d = 10).  One persistent launch on `stream`;
- * asynchronous.  Failed instances are counted, not inserted, and set the
- * histogram's error word. */
+ * and, with TS_ENUM_REDUCED, d = 10).  Persistent launches on `stream`
+ * (whole blocks of middle-row patterns, and a ragged head and tail mask by
+ * mask); asynchronous.  With TS_ENUM_FLIP the specialised kernels take a
+ * block of masks and the block of their complements (every bit flipped)
+ * together, evaluating the complements of half of them instead: the global
+ * sign flip keeps the curve, so the histogram is the one of the masks m(k).
+ * Failed instances are counted, not inserted, and set the histogram's
+ * error word. */
 ts_status ts_enumerate(const ts_tri *tri, uint64_t lo, uint64_t hi, uint32_t flags,
                        ts_hist *hist, void *stream);
 

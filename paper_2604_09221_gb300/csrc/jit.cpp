@@ -584,8 +584,31 @@ cudaError_t launch_enumerate_jit(ts_tri *t, uint64_t lo, uint64_t hi, uint32_t f
   const uint64_t a = ((lo + (1ull << ib) - 1) >> ib) << ib, b = (hi >> ib) << ib;
   if (a >= b) return enumerate_range(*m, h, lo, hi, flags, st);
   if (lo < a && (e = enumerate_range(*m, h, lo, a, flags, st)) != cudaSuccess) return e;
-  if ((e = enumerate_blocks(*m, h, a >> ib, (b - a) >> ib, oshift, ishift, (1u << ib) / 32u, st)) !=
-      cudaSuccess)
+  uint64_t h0 = a >> ib, h1 = b >> ib;  // whole blocks [h0, h1)
+  if ((flags & TS_ENUM_FLIP) && !(flags & TS_ENUM_REDUCED) && t->np - 1 - ib < 63) {
+    // Global sign flip: block h (masks with bit 0 clear) and block M - h
+    // (all high bits complemented) hold one representative of each class
+    // {sigma, ~sigma} whose high part is h or M - h; flipping the second
+    // block's masks gives block h with bit 0 set.  So a pair of blocks in
+    // the range is swept as the one unreduced block h with all 2^(d+1)
+    // middle-row patterns: the same schemes (the flip keeps the curve), and
+    // twice the patterns per half-diamond sweep.  Paired: h in [p, q]
+    // (symmetric about M / 2, both ends in the range); the rest as before.
+    const uint64_t M = (1ull << (t->np - 1 - ib)) - 1;
+    const uint64_t p = std::max<uint64_t>(h0, h1 > M ? 0 : M + 1 - h1);
+    const uint64_t q1 = std::min<uint64_t>(h1, h0 > M ? 0 : M - h0 + 1);  // q + 1
+    if (p < q1) {
+      const uint64_t half = (q1 - p) / 2;  // q1 - p is even: p + q = M, M odd
+      if (h0 < p && (e = enumerate_blocks(*m, h, h0, p - h0, oshift, ishift, (1u << ib) / 32u, st)) !=
+                        cudaSuccess)
+        return e;
+      if ((e = enumerate_blocks(*m, h, p, half, d + 1, 0, (1u << (d + 1)) / 32u, st)) != cudaSuccess)
+        return e;
+      h0 = q1;
+    }
+  }
+  if (h0 < h1 &&
+      (e = enumerate_blocks(*m, h, h0, h1 - h0, oshift, ishift, (1u << ib) / 32u, st)) != cudaSuccess)
     return e;
   if (b < hi && (e = enumerate_range(*m, h, b, hi, flags, st)) != cudaSuccess) return e;
   return cudaSuccess;

@@ -216,6 +216,28 @@ def test_enumerate_reduced_equals_full_over_8(eng, kind):
     assert full == collections.Counter({k: 8 * v for k, v in red.items()})
 
 
+@pytest.mark.parametrize("d", [5, 6])
+def test_flip_sweep_pairs_complementary_blocks(eng, orc, d):
+    """TS_ENUM_FLIP sweeps of the specialised kernel take a block of masks
+    and the block of its complement together, as one block with every
+    middle-row pattern (the global sign flip keeps the scheme).  Over the
+    whole range, over ranges whose unpaired blocks lie below or above the
+    paired ones (with ragged masks at both ends), against the oracle on
+    the masks k << 1; and every class counted twice by the plain sweep."""
+    e = ti.regular_triangulation(d, seed=80 + d)
+    tri = load(eng, d, e, "specialized")
+    N = ti.num_points(d)
+    full = 1 << (N - 1)
+    if d == 5:   # blocks of 2^5 values of k
+        for lo, hi in ((0, full), (37 * 32 + 5, full - 99 * 32 - 9), (300 * 32 + 5, full - 99 * 32 - 9)):
+            ks = np.arange(lo, hi, dtype=np.uint64)
+            want = oracle_hist(orc, d, e, (ks << np.uint64(1)).reshape(-1, 1))
+            assert gpu_hist(eng, tri, lo, hi, eng.TS_ENUM_FLIP) == want, (lo, hi)
+    plain = gpu_hist(eng, tri, 0, 1 << N)
+    flip = gpu_hist(eng, tri, 0, full, eng.TS_ENUM_FLIP)
+    assert plain == collections.Counter({k: 2 * v for k, v in flip.items()})
+
+
 @pytest.mark.parametrize("kind", KINDS)
 def test_enumerate_d7_full_size_slice(eng, orc, kind):
     """The benchmark workload (degree 7, masks [0, 2^32)) in the launch
