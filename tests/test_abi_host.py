@@ -172,3 +172,14 @@ def test_header_and_library_from_c(eng, tmp_path):
                     f"-Wl,-rpath,{os.path.dirname(lib)}"], check=True, capture_output=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True)
     assert out.returncode == 0, out.stdout + out.stderr
+
+
+def test_batch_launch_plan_calls_reject_bad_arguments(eng):
+    """The fused-launch and group-order calls refuse a null batch and
+    out-of-range values before they touch a device."""
+    lib = eng.library()
+    assert lib.ts_batch_set_fused(None, 1) == 1                        # TS_EINVAL
+    assert lib.ts_batch_set_fused(None, 0) == 1
+    assert lib.ts_batch_set_serial(None, 1) == 1
+    assert lib.ts_batch_set_fused_tile(None, 8, eng.TS_KERNEL_TABLE, 1024) == 1
+    assert lib.ts_batch_set_fused_tile(None, 8, eng.TS_KERNEL_WARP, 1024) == 1
