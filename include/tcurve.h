@@ -287,6 +287,17 @@ ts_status ts_batch_set_fused(ts_batch *batch, int fused);
  * degree the batch does not hold, or a tile whose launch does not fit (the
  * previous tile is kept). */
 ts_status ts_batch_set_fused_tile(ts_batch *batch, int d, int kind, int chunk);
+/* Query jobs in a batch (an engine facility): job `job` classifies the
+ * caller's sign vectors instead of its splitmix64 stream.
+ *   signs  device, counts[job] * ts_sign_words(tris[job]) uint64, read by
+ *          every run; the caller keeps it alive and unchanged while runs
+ *          may read it.  NULL returns the job to its splitmix64 stream.
+ * Such jobs run only in the fused launch (ts_batch_set_fused):
+ * ts_batch_run returns TS_EINVAL in the per-degree group mode while a job
+ * has caller sign vectors.  Waits for all work on the device first; the
+ * next run with use_graph captures a new graph.  TS_EINVAL for a bad job
+ * index. */
+ts_status ts_batch_set_signs(ts_batch *batch, int job, const uint64_t *signs);
 /* Clear the histograms and run every job, asynchronously on stream.  With
  * use_graph the work (clears, fork, per-degree kernels, join) is captured
  * into a CUDA graph on the first call (and after a tile change) and the graph

@@ -98,6 +98,7 @@ def _load():
                 "ts_batch_set_serial": ([P, I], I),
                 "ts_batch_set_fused": ([P, I], I),
                 "ts_batch_set_fused_tile": ([P, I, I, I], I),
+                "ts_batch_set_signs": ([P, I, P], I),
                 "ts_batch_info": ([P, I, ctypes.POINTER(BatchGroupInfo), ctypes.c_char_p,
                                    ctypes.c_size_t], I),
                 "ts_batch_specialized_link": ([I, I, P, P, ctypes.POINTER(ctypes.c_size_t),
@@ -368,6 +369,25 @@ class Batch:
         per sign vector, d >= 7), and sign vectors per work item."""
         _check(_lib.ts_batch_set_fused_tile(self._h, int(d), int(kind), int(chunk)),
                "ts_batch_set_fused_tile")
+
+    def set_signs(self, job: int, signs=None):
+        """Job ``job`` classifies these sign vectors (a CUDA tensor of 64-bit
+        words, counts[job] x sign_words, kept alive here) instead of its
+        splitmix64 stream; None returns it to the stream
+        (ts_batch_set_signs).  Such jobs run in the fused launch only."""
+        if not hasattr(self, "_signs"):
+            self._signs = {}
+        ptr = None
+        if signs is not None:
+            _check_words(signs, int(self.counts[job]) * self.tris[job].sign_words, "signs")
+            if not signs.is_contiguous():
+                raise ValueError("signs: the tensor must be contiguous")
+            ptr = ctypes.c_void_p(signs.data_ptr())
+        _check(_lib.ts_batch_set_signs(self._h, int(job), ptr), "ts_batch_set_signs")
+        if signs is None:
+            self._signs.pop(job, None)
+        else:
+            self._signs[job] = signs
 
     def info(self, d: int) -> dict:
         """Kernel family, tile and launch resources of the degree-d group

@@ -289,6 +289,7 @@ struct ts_batch {
   cudaGraphExec_t exec = nullptr;
   int device = 0;
   std::vector<ts_tri *> tris;  // triangulation of every job
+  std::vector<const uint64_t *> signs;  // caller sign vectors of every job (null: splitmix64)
   bool serial = false;         // degree groups one after the other (else concurrent streams)
   // fused launch (ts_batch_set_fused): one persistent kernel over all jobs
   bool fused = false;
@@ -402,6 +403,7 @@ cudaError_t prepare_fused(ts_batch *b) {
       x.hcnt = dj.hcnt;
       x.hslots = dj.hslots;
       x.item0 = items;
+      x.signs = reinterpret_cast<const unsigned long long *>(b->signs[j]);
       x.d = (uint32_t)g->d;
       x.chunk = (uint32_t)g->fchunk;
       x.warp = (uint32_t)g->fwarp;
@@ -621,6 +623,7 @@ ts_status ts_batch_create(int njobs, ts_tri *const *tris, const uint64_t *counts
     b->jobs.push_back(x);
     b->degree.push_back(t->d);
     b->tris.push_back(tris[j]);
+    b->signs.push_back(nullptr);
     if (!gi.count(t->d)) {
       gi[t->d] = (int)b->groups.size();
       ts_batch::Group g;
@@ -793,8 +796,28 @@ ts_status ts_batch_set_fused_tile(ts_batch *b, int d, int kind, int chunk) {
   return TS_EINVAL;
 }
 
+ts_status ts_batch_set_signs(ts_batch *b, int job, const uint64_t *signs) {
+  if (!b || job < 0 || job >= (int)b->jobs.size()) return TS_EINVAL;
+  if (b->signs[job] == signs) return TS_OK;
+  cudaError_t e = cudaDeviceSynchronize();  // a run launched before may still read the job table
+  if (e != cudaSuccess) return cuda_st(e);
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  b->signs[job] = signs;
+  if (b->fused) {
+    e = prepare_fused(b);
+    if (e != cudaSuccess) return cuda_st(e);
+  }
+  return TS_OK;
+}
+
 ts_status ts_batch_run(ts_batch *b, int use_graph, void *stream) {
   if (!b) return TS_EINVAL;
+  if (!b->fused)  // the degree-group kernels draw their sign vectors: caller inputs need the fused launch
+    for (const uint64_t *p : b->signs)
+      if (p) return TS_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   if (!use_graph) return cuda_st(enqueue(b, st));
   if (!b->exec) {

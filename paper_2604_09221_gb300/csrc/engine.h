@@ -208,6 +208,7 @@ struct FusedJob {
   uint32_t off_fan, off_vext;  // table-driven layout
   WarpLayout wl;               // warp layout
   uint32_t pad;
+  const unsigned long long *signs;  // the caller's sign vectors (n x words), or null: splitmix64
 };
 int fused_tier(int dmax);          // tier of a batch whose largest degree is dmax (-1: none)
 int fused_tier_degree(int tier);   // largest degree of a tier

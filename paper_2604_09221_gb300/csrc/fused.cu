@@ -4,7 +4,8 @@
 // one launch: blocks pull work items from one counter over all jobs (sorted
 // by degree), stage the job's tables into shared memory with cp.async.bulk
 // on an mbarrier (bounded wait) when they move to another triangulation,
-// draw the job's splitmix64 sign vectors on the device, classify them with
+// draw the job's splitmix64 sign vectors on the device (or read the
+// caller's, ts_batch_set_signs), classify them with
 // Algorithm 1 (Sec. 2) and add the codes to the job's device histogram.
 // The degree of a job selects the code path inside the kernel (a switch
 // over degree-templated bodies), and each degree has a tile of its own:
@@ -55,6 +56,23 @@ struct FusedSlab {
   static constexpr u32 WORDS = slab_words_upto(DHI);
 };
 
+// Sign vector idx of job J: the caller's (J.signs, W words each) or word w
+// of the splitmix64 stream, splitmix64((base + idx) * W + w); bits >= |A|
+// cleared.
+template <u32 W, u32 NPOINTS>
+__device__ __forceinline__ TcSig<W> job_sig(const FusedJob &__restrict__ J, u64 idx) {
+  TcSig<W> sg;
+  if (J.signs) {
+#pragma unroll
+    for (u32 w = 0; w < W; ++w) sg.w[w] = J.signs[idx * W + w];
+  } else {
+#pragma unroll
+    for (u32 w = 0; w < W; ++w) sg.w[w] = tc_splitmix64((J.base + idx) * W + w);
+  }
+  sg.w[W - 1] &= tc_top_mask(NPOINTS, W);
+  return sg;
+}
+
 // Thread per instance: chunk sign vectors of job J from index `first`.  The
 // label slots of the sweep (one load per fan entry) sit in shared memory
 // (ls: this thread's word 0, word i at ls[i * 128]), and the staged fan
@@ -71,10 +89,7 @@ __device__ __forceinline__ void thread_item(const FusedJob &__restrict__ J, u64 
     const u64 idx = first + k + threadIdx.x;
     TcCodeOut<K> key{};
     if (idx < J.n) {
-      TcSig<K::W> sg;
-#pragma unroll
-      for (u32 w = 0; w < K::W; ++w) sg.w[w] = tc_splitmix64((J.base + idx) * K::W + w);
-      sg.w[K::W - 1] &= tc_top_mask(K::NPOINTS, K::W);
+      const TcSig<K::W> sg = job_sig<K::W, K::NPOINTS>(J, idx);
       key = tc_table_classify<K, true>(sg, tab, J.off_fan, J.off_vext, S, err, ls);
       u64 any = 0;
 #pragma unroll
@@ -110,10 +125,7 @@ __device__ __forceinline__ void warp_item(const FusedJob &__restrict__ J, u64 fi
     for (u32 r = 0; r < 32u; ++r) {
       const u64 idx = first + g + r;
       if (idx >= J.n) break;  // warp-uniform
-      TcSig<K::W> sg;
-#pragma unroll
-      for (u32 w = 0; w < K::W; ++w) sg.w[w] = tc_splitmix64((J.base + idx) * K::W + w);
-      sg.w[K::W - 1] &= tc_top_mask(K::NPOINTS, K::W);
+      const TcSig<K::W> sg = job_sig<K::W, K::NPOINTS>(J, idx);
       u64 code[K::CW];
 #pragma unroll
       for (u32 w = 0; w < K::CW; ++w) code[w] = 0;

@@ -3,7 +3,8 @@ for every job of every degree.  Each job's histogram and stored codes equal
 the oracle's on the same splitmix64 sign vectors in every register tier
 (largest degree 6, 9, 11, 16), with thread and warp tiles, chunk changes,
 graph replay and launches without a graph, and the same as the per-degree
-group launches of the same batch; malformed tiles are refused."""
+group launches of the same batch; malformed tiles are refused; jobs that
+bring their own sign vectors run beside jobs on their streams."""
 import collections
 
 import numpy as np
@@ -125,4 +126,49 @@ def test_fused_tiles_are_validated(eng):
     for i, j in enumerate(jobs):
         codes, cnt, failed = batch.read(i)
         assert failed == 0 and int(cnt.sum()) == j["n"]
+    batch.close()
+
+
+def test_fused_launch_with_caller_sign_vectors(eng, orc):
+    """Jobs that classify the caller's sign vectors (ts_batch_set_signs)
+    beside jobs on their splitmix64 streams, in one fused launch, with thread
+    and warp tiles: codes and histograms equal the oracle's on the same
+    vectors (one, two and three sign words); the per-degree group mode
+    refuses to run such a batch; a job returned to its stream gives the
+    stream's schemes again."""
+    import torch
+    jobs = make_jobs(eng, [(6, 3000), (6, 1000), (9, 2000), (11, 900), (16, 400)], 4200)
+    tris = [j["tri"] for j in jobs]
+    outs = [torch.zeros((j["n"], j["tri"].code_words), dtype=torch.int64, device="cuda") for j in jobs]
+    batch = eng.Batch(tris, [j["n"] for j in jobs], [j["base"] for j in jobs], code_outputs=outs)
+    given = {}
+    for i in (0, 2, 3, 4):   # caller vectors; job 1 stays on its stream
+        j = jobs[i]
+        words = ti.random_masks(j["n"], j["d"], seed=4300 + i)
+        given[i] = words
+        batch.set_signs(i, torch.from_numpy(np.ascontiguousarray(words).view(np.int64)).cuda())
+    with pytest.raises(eng.TSError):
+        batch.run()                               # group mode: refused
+    batch.set_fused(True)
+
+    def check():
+        got = hists(eng, batch, len(jobs))
+        for i, j in enumerate(jobs):
+            d = j["d"]
+            if i in given:
+                want = orc.real_schemes(d, orc.triangles(d, j["edges"]), given[i])
+            else:
+                want = oracle_codes(orc, j)
+            assert got[i] == collections.Counter(orc.code_to_int(c) for c in want), (i, d)
+            assert (outs[i].cpu().numpy().view(np.uint64) == want).all(), (i, d)
+    batch.run(graph=True)
+    check()
+    batch.set_fused_tile(9, eng.TS_KERNEL_WARP, 256)   # warp tiles read the caller's vectors too
+    batch.set_fused_tile(16, eng.TS_KERNEL_WARP, 512)
+    batch.run(graph=False)
+    check()
+    batch.set_signs(3, None)                      # back to its splitmix64 stream
+    del given[3]
+    batch.run(graph=True)
+    check()
     batch.close()
