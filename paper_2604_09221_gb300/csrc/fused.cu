@@ -5,14 +5,16 @@
 // by degree), stage the job's tables into shared memory with cp.async.bulk
 // on an mbarrier (bounded wait) when they move to another triangulation,
 // draw the job's splitmix64 sign vectors on the device (or read the
-// caller's, ts_batch_set_signs), classify them with
-// Algorithm 1 (Sec. 2) and add the codes to the job's device histogram.
-// The degree of a job selects the code path inside the kernel (a switch
-// over degree-templated bodies), and each degree has a tile of its own:
+// caller's, ts_batch_set_signs), classify them with Algorithm 1 (Sec. 2)
+// and add the codes to the job's device histogram.  The degree of a job
+// selects the code path inside the kernel (a switch over degree-templated
+// bodies), and each degree has a tile of its own:
 //
 //   thread per instance  (TS_KERNEL_TABLE)  every thread classifies its own
-//        sign vector with the table-driven sweep, per-thread scratch in
-//        global memory (word-interleaved, L1/L2-resident);
+//        sign vector with the table-driven sweep: the label slots in shared
+//        memory, found through the staged fan entries' offsets, the rest
+//        of the per-thread scratch in global memory (word-interleaved,
+//        L1/L2-resident);
 //   warp per instance    (TS_KERNEL_WARP)   the 32 lanes of a warp classify
 //        one sign vector together (lock-free union-find in shared memory,
 //        tc_warp_sweep.cuh), 32 sign vectors per warp between histogram
@@ -21,7 +23,8 @@
 // plus the sign vectors per work item.  A kernel is compiled for a range of
 // degrees 1..DHI with a register budget that keeps the resident blocks of
 // that range's table-driven bodies (tiers below); the batch takes the tier
-// of its largest degree.
+// of its largest degree, or the widest tier's kernel with warp bodies when
+// a degree has a warp tile.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
