@@ -64,6 +64,16 @@ typedef enum ts_status {
                                bits >= |A| cleared (one word: splitmix64(k)): a sampled,
                                reproducible stream of sign vectors (the stream of
                                ts_splitmix_masks and ts_batch_create); no bound on hi */
+#define TS_ENUM_ORBITS 8u  /* one representative per (Z/2)^3 class (Sec. 3), other than
+                              TS_ENUM_REDUCED's: sigma(0,1) = 0, all d+1 middle-row bits
+                              free, the high part (bits d+2..|A|-1) the one of its coset
+                              under the class group with two pivot bits zero:
+                              m(k) = (h(k >> (d+1)) << (d+2)) | (k mod 2^(d+1)), h(u) = u
+                              with zeros inserted at the pivots p2 < p1 (tc_layout.h,
+                              tc_orbit_pivots).  Same histogram as TS_ENUM_REDUCED over the
+                              whole range, and any range [lo, hi) keeps every middle-row
+                              pattern, so chunked and sharded sweeps run whole blocks.
+                              2 <= d <= 9 (TS_EUNSUPPORTED above, TS_EINVAL below) */
 
 /* Human-readable name of a status code; never NULL. */
 const char *ts_status_str(int status);
@@ -197,7 +207,8 @@ ts_status ts_hist_clear(ts_hist *hist, void *stream);
  * [lo, hi), to `hist`, which must have ts_code_words(tri) words per code.
  * m(k) = k by default; k << 1 with TS_ENUM_FLIP; k with zero bits inserted at
  * positions 0, 1 and d+1 with TS_ENUM_REDUCED (bits carried past bit 63 go
- * to the second sign word); the splitmix64 stream with TS_ENUM_SPLITMIX.
+ * to the second sign word); the splitmix64 stream with TS_ENUM_SPLITMIX; the
+ * orbit representatives of TS_ENUM_ORBITS (at most one flag).
  * Except with TS_ENUM_SPLITMIX, m(hi-1) < 2^|A| (a bound only for d <= 9
  * and, with TS_ENUM_REDUCED, d = 10).  Persistent launches on `stream`
  * (whole blocks of middle-row patterns, and a ragged head and tail mask by

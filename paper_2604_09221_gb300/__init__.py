@@ -20,6 +20,7 @@ from . import build as _build
 TS_ENUM_FLIP = 1
 TS_ENUM_REDUCED = 2
 TS_ENUM_SPLITMIX = 4
+TS_ENUM_ORBITS = 8
 TS_KERNEL_AUTO = 0
 TS_KERNEL_TABLE = 1
 TS_KERNEL_SPECIALIZED = 2

@@ -654,11 +654,19 @@ ts_status ts_hist_clear(ts_hist *h, void *stream) {
 
 ts_status ts_enumerate(const ts_tri *t, uint64_t lo, uint64_t hi, uint32_t flags, ts_hist *h,
                        void *stream) {
-  const uint32_t kinds = flags & (TS_ENUM_FLIP | TS_ENUM_REDUCED | TS_ENUM_SPLITMIX);
+  const uint32_t kinds =
+      flags & (TS_ENUM_FLIP | TS_ENUM_REDUCED | TS_ENUM_SPLITMIX | TS_ENUM_ORBITS);
   if (!t || !h || hi < lo || (flags & ~kinds) || (kinds & (kinds - 1))) return TS_EINVAL;
   if (h->cw != t->cw) return TS_EINVAL;
-  int free_bits = t->np - ((flags & TS_ENUM_FLIP) ? 1 : 0) - ((flags & TS_ENUM_REDUCED) ? 3 : 0);
+  int free_bits = t->np - ((flags & TS_ENUM_FLIP) ? 1 : 0) -
+                  ((flags & (TS_ENUM_REDUCED | TS_ENUM_ORBITS)) ? 3 : 0);
   if (!(flags & TS_ENUM_SPLITMIX) && free_bits < 64 && hi > (1ull << free_bits)) return TS_EINVAL;
+  if (flags & TS_ENUM_ORBITS) {  // the kernels read the pivots from bits 8-23 of the flags
+    int p1 = 0, p2 = 0;
+    if (t->d > 9) return TS_EUNSUPPORTED;
+    if (!tc_orbit_pivots(t->d, &p1, &p2)) return TS_EINVAL;
+    flags |= ((uint32_t)p1 << 8) | ((uint32_t)p2 << 16);
+  }
   if (lo == hi) return TS_OK;
   ts_tri *tm = const_cast<ts_tri *>(t);
   if (tm->kernel == TS_KERNEL_WARP)

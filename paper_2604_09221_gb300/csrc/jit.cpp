@@ -543,7 +543,7 @@ cudaError_t enumerate_range(JitModule &m, ts_hist *h, uint64_t lo, uint64_t hi, 
 // One launch of the block sweep: masks (h << oshift) | (t << ishift) for
 // h in [hi0, hi0 + n_hi) and t < 32 * ireps (all middle-row patterns).
 cudaError_t enumerate_blocks(JitModule &m, ts_hist *h, uint64_t hi0, uint64_t n_hi, uint32_t oshift,
-                             uint32_t ishift, uint32_t ireps, cudaStream_t st) {
+                             uint32_t ishift, uint32_t ireps, uint32_t flags, cudaStream_t st) {
   const uint64_t warps = m.L.threads / 32;
   const uint64_t want = (n_hi + warps - 1) / warps;
   const uint64_t cap = (uint64_t)m.bpsm_blocks * sm_count_now();
@@ -553,9 +553,10 @@ cudaError_t enumerate_blocks(JitModule &m, ts_hist *h, uint64_t hi0, uint64_t n_
   JitScratch gs(m, grid, st);
   if ((e = gs.alloc()) != cudaSuccess) return e;
   uint64_t slots = h->slots;
-  void *args[] = {(void *)&hi0,      (void *)&n_hi,       (void *)&oshift,   (void *)&ishift,
-                  (void *)&ireps,    (void *)&h->d_keys,  (void *)&h->d_counts, (void *)&slots,
-                  (void *)&h->d_err, (void *)&h->d_failed, (void *)&h->d_work, (void *)&gs.p};
+  void *args[] = {(void *)&hi0,       (void *)&n_hi,      (void *)&oshift,     (void *)&ishift,
+                  (void *)&ireps,     (void *)&flags,     (void *)&h->d_keys,  (void *)&h->d_counts,
+                  (void *)&slots,     (void *)&h->d_err,  (void *)&h->d_failed, (void *)&h->d_work,
+                  (void *)&gs.p};
   if (driver().launch(m.blocks, grid, 1, 1, m.L.threads, 1, 1, (unsigned)m.smem_enum, (CUstream)st,
                       args, nullptr) != CUDA_SUCCESS)
     return cudaErrorLaunchFailure;
@@ -569,7 +570,9 @@ cudaError_t enumerate_blocks(JitModule &m, ts_hist *h, uint64_t hi0, uint64_t n_
 // sweep index k, the mask m(k) is (h << oshift) | (t << ishift) with
 // t = k mod 2^ib the middle-row pattern (ib free middle-row bits) and
 // h = k >> ib: ib = d + 1 without flags, d with TS_ENUM_FLIP (bit 0 fixed),
-// d - 1 with TS_ENUM_REDUCED (bits 0, 1 and d + 1 fixed).
+// d - 1 with TS_ENUM_REDUCED (bits 0, 1 and d + 1 fixed), d + 1 with
+// TS_ENUM_ORBITS (bit d + 1 fixed, h the block's high part with its pivots
+// zero, tc_orbit_high).
 cudaError_t launch_enumerate_jit(ts_tri *t, uint64_t lo, uint64_t hi, uint32_t flags, ts_hist *h,
                                  cudaStream_t st) {
   cudaError_t e = jit_prepare(t);
@@ -579,6 +582,7 @@ cudaError_t launch_enumerate_jit(ts_tri *t, uint64_t lo, uint64_t hi, uint32_t f
   uint32_t ib = d + 1, ishift = 0, oshift = d + 1;
   if (flags & TS_ENUM_FLIP) { ib = d; ishift = 1; oshift = d + 1; }
   if (flags & TS_ENUM_REDUCED) { ib = d - 1; ishift = 2; oshift = d + 2; }
+  if (flags & TS_ENUM_ORBITS) { ib = d + 1; ishift = 0; oshift = d + 2; }  // every pattern
   if (ib < 5 || (flags & TS_ENUM_SPLITMIX))  // fewer patterns than lanes / sampled masks
     return enumerate_range(*m, h, lo, hi, flags, st);
   const uint64_t a = ((lo + (1ull << ib) - 1) >> ib) << ib, b = (hi >> ib) << ib;
@@ -599,16 +603,19 @@ cudaError_t launch_enumerate_jit(ts_tri *t, uint64_t lo, uint64_t hi, uint32_t f
     const uint64_t q1 = std::min<uint64_t>(h1, h0 > M ? 0 : M - h0 + 1);  // q + 1
     if (p < q1) {
       const uint64_t half = (q1 - p) / 2;  // q1 - p is even: p + q = M, M odd
-      if (h0 < p && (e = enumerate_blocks(*m, h, h0, p - h0, oshift, ishift, (1u << ib) / 32u, st)) !=
-                        cudaSuccess)
+      if (h0 < p &&
+          (e = enumerate_blocks(*m, h, h0, p - h0, oshift, ishift, (1u << ib) / 32u, 0, st)) !=
+              cudaSuccess)
         return e;
-      if ((e = enumerate_blocks(*m, h, p, half, d + 1, 0, (1u << (d + 1)) / 32u, st)) != cudaSuccess)
+      if ((e = enumerate_blocks(*m, h, p, half, d + 1, 0, (1u << (d + 1)) / 32u, 0, st)) !=
+          cudaSuccess)
         return e;
       h0 = q1;
     }
   }
   if (h0 < h1 &&
-      (e = enumerate_blocks(*m, h, h0, h1 - h0, oshift, ishift, (1u << ib) / 32u, st)) != cudaSuccess)
+      (e = enumerate_blocks(*m, h, h0, h1 - h0, oshift, ishift, (1u << ib) / 32u,
+                            flags & (TS_ENUM_ORBITS | 0xFFFF00u), st)) != cudaSuccess)
     return e;
   if (b < hi && (e = enumerate_range(*m, h, b, hi, flags, st)) != cudaSuccess) return e;
   return cudaSuccess;

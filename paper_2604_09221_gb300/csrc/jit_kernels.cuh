@@ -76,13 +76,14 @@ extern "C" __global__ void __launch_bounds__(TcK::THREADS, TC_MINB_MASK)
 }
 
 // Exhaustive sweep of whole middle-row blocks: masks (h << oshift) |
-// (t << ishift) for h in [hi0, hi0 + n_hi) and every t < 32 * ireps.  Each
+// (t << ishift) for h in [hi0, hi0 + n_hi) (with TS_ENUM_ORBITS in flags,
+// h = the block's high part, tc_orbit_high) and every t < 32 * ireps.  Each
 // warp takes one h at a time; the two half-diamonds depend on h only and are
 // swept once, then every lane classifies ireps middle-row patterns
 // (tc_sweep_amortised).
 extern "C" __global__ void __launch_bounds__(TcK::THREADS, TcK::MINB)
-    tc_enumerate_blocks(u64 hi0, u64 n_hi, u32 oshift, u32 ishift, u32 ireps, u64 *gkeys,
-                        unsigned long long *gcnt, u64 gslots, u32 *gerr,
+    tc_enumerate_blocks(u64 hi0, u64 n_hi, u32 oshift, u32 ishift, u32 ireps, u32 flags,
+                        u64 *gkeys, unsigned long long *gcnt, u64 gslots, u32 *gerr,
                         unsigned long long *gfailed, unsigned long long *work, u32 *gscr) {
   extern __shared__ __align__(16) u32 tc_smem[];
   u64 *hkeys = reinterpret_cast<u64 *>(tc_smem + TC_SMEM_SCRATCH);
@@ -101,8 +102,10 @@ extern "C" __global__ void __launch_bounds__(TcK::THREADS, TcK::MINB)
     if (lane == 0) h = atomicAdd(work, 1ull);
     h = __shfl_sync(0xffffffffu, h, 0);
     if (h >= n_hi) break;
-    tc_sweep_amortised((hi0 + h) << oshift, ishift, ireps, S, err, hkeys, hcnt, gkeys, gcnt, gslots,
-                       gerr, failed);
+    // the orbit sweep's blocks: block index -> high part with the pivots zero
+    const u64 hh = (flags & 8u) ? tc_orbit_high(hi0 + h, flags) : hi0 + h;
+    tc_sweep_amortised(hh << oshift, ishift, ireps, S, err, hkeys, hcnt, gkeys, gcnt, gslots, gerr,
+                       failed);
   }
   __syncthreads();
   for (u32 s = threadIdx.x; s < TcK::HASH; s += TcK::THREADS)

@@ -94,3 +94,38 @@ constexpr TcLayout tc_layout(int d, bool vertex_labels, int max_threads) {
   L.ok = L.wcode <= L.wlab && wide_fits && d >= 1 && d <= 16 && L.cw <= 4 && L.sw <= 3;
   return L;
 }
+
+// Pivots of the orbit sweep (TS_ENUM_ORBITS, Sec. 3 symmetry).  The four
+// elements of (Z/2)^3 that keep sigma(0, 1) (sigma -> sigma + a + b i + c j
+// with a + c = 0 mod 2) change the high part of a mask (bits d+2 .. |A|-1:
+// every lattice point with j >= 1 but (0, 1), bit b = k(i, j) - d - 2) by
+// the span of A (points with i odd) and B (points with j even).  With A and
+// B in echelon form (top bits p1 > p2), every coset h + span{A, B} holds
+// exactly one high part whose bits p1 and p2 are zero.  Needs 2 <= d <= 9
+// (A and B independent; one sign word); returns false otherwise.
+constexpr bool tc_orbit_pivots(int d, int *p1, int *p2) {
+  if (d < 2 || d > 9) return false;
+  unsigned long long a = 0, b = 0;
+  for (int j = 1; j <= d; ++j)
+    for (int i = 0; i + j <= d; ++i) {
+      if (i == 0 && j == 1) continue;
+      const int k = j * (d + 1) - j * (j - 1) / 2 + i, bit = k - d - 2;
+      if (i % 2 == 1) a |= 1ull << bit;
+      if (j % 2 == 0) b |= 1ull << bit;
+    }
+  auto top = [](unsigned long long x) {
+    int t = -1;
+    for (int q = 0; q < 64; ++q)
+      if ((x >> q) & 1ull) t = q;
+    return t;
+  };
+  if (top(b) > top(a)) {
+    const unsigned long long x = a;
+    a = b;
+    b = x;
+  }
+  if (top(b) == top(a)) b ^= a;
+  *p1 = top(a);
+  *p2 = top(b);
+  return *p1 > *p2 && *p2 >= 0;
+}

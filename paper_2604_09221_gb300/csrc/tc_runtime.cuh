@@ -966,6 +966,17 @@ __device__ __forceinline__ u64 tc_top_mask(u32 np, u32 W) {
 
 // Enumeration masks (ts_enumerate flags): k, k << 1, k with zero bits
 // inserted at positions 0, 1 and d + 1, or splitmix64(k) cut to |A| bits.
+// x with a zero bit inserted at position p (higher bits move up one).
+__device__ __forceinline__ u64 tc_ins0(u64 x, u32 p) {
+  return ((x >> p) << (p + 1)) | (x & ((1ull << p) - 1));
+}
+
+// The orbit sweep's high part of block u: zeros inserted at the pivots p2 <
+// p1 (bits 8-15 and 16-23 of flags hold p1 and p2, set by the host).
+__device__ __forceinline__ u64 tc_orbit_high(u64 u, u32 flags) {
+  return tc_ins0(tc_ins0(u, (flags >> 16) & 0xFFu), (flags >> 8) & 0xFFu);
+}
+
 __device__ __forceinline__ u64 tc_enum_mask(u64 k, u32 flags, u32 d) {
   if (flags & 4u) {
     const u32 np = (d + 1) * (d + 2) / 2;
@@ -973,6 +984,8 @@ __device__ __forceinline__ u64 tc_enum_mask(u64 k, u32 flags, u32 d) {
   }
   if (flags & 1u) return k << 1;
   if (flags & 2u) return ((k & ((1ull << (d - 1)) - 1)) << 2) | ((k >> (d - 1)) << (d + 2));
+  if (flags & 8u)  // orbit sweep: every middle-row pattern, high part from the block index
+    return (tc_orbit_high(k >> (d + 1), flags) << (d + 2)) | (k & ((1ull << (d + 1)) - 1));
   return k;
 }
 
@@ -997,6 +1010,8 @@ __device__ __forceinline__ TcSig<W> tc_enum_sig(u64 k, u32 flags, u32 d) {
     const u64 h = k >> (d - 1);
     lo = ((k & ((1ull << (d - 1)) - 1)) << 2) | (h << (d + 2));
     hi = h >> (62 - d);
+  } else if (flags & 8u) {  // one sign word only (d <= 9)
+    lo = tc_enum_mask(k, flags, d);
   }
   s.w[0] = lo;
 #pragma unroll

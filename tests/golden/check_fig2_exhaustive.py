@@ -5,9 +5,11 @@ Fig. 2 of the paper gives, for three degree-8 triangulations, the percentage
 of the 2^42 sign-distribution classes (one representative per (Z/2)^3 orbit,
 Sec. 3) whose curve has k ovals, to four decimals, and the number of distinct
 real schemes each realizes (123, 359 and 353).  This script sweeps all 2^42
-representatives of one triangulation with ts_enumerate (TS_ENUM_REDUCED),
-checkpointing after every chunk, and compares both with the printed values
-stored in this directory.
+representatives of one triangulation with ts_enumerate (TS_ENUM_REDUCED,
+or with --orbits the TS_ENUM_ORBITS representatives, whose chunks keep every
+middle-row pattern), checkpointing after every chunk, and compares both with
+the printed values stored in this directory; --limit LOG2 only times the
+first 2^LOG2 classes.
 
     python tests/golden/check_fig2_exhaustive.py bow_tie [checkpoint.json]
 
@@ -45,7 +47,7 @@ def printed(name):
     return out
 
 
-def main(name, ckpt, shard=(0, 1)):
+def main(name, ckpt, shard=(0, 1), orbits=False, limit=None):
     import torch
 
     import paper_2604_09221_gb300 as eng
@@ -56,7 +58,21 @@ def main(name, ckpt, shard=(0, 1)):
     tri = eng.Triangulation(8, edges)
     tri.prepare()
     total = 1 << 42
-    fn = sweep.engine_chunk_fn(tri, flags=eng.TS_ENUM_REDUCED)
+    flags = eng.TS_ENUM_ORBITS if orbits else eng.TS_ENUM_REDUCED
+    fn = sweep.engine_chunk_fn(tri, flags=flags)
+    if limit is not None:  # a timed run over the first 2^limit classes of the shard, no check
+        lo, _ = sweep.shard_range(0, total, shard[0], shard[1])
+        fn(lo, lo + (1 << 10))  # warm-up
+        torch.cuda.synchronize()
+        t = time.time()
+        hist = fn(lo, lo + (1 << limit))
+        torch.cuda.synchronize()
+        dt = time.time() - t
+        assert sum(hist.values()) == 1 << limit
+        print(json.dumps({"triangulation": name, "flags": "TS_ENUM_ORBITS" if orbits else "TS_ENUM_REDUCED",
+                          "classes": 1 << limit, "seconds": dt, "classes_per_s": (1 << limit) / dt,
+                          "distinct_schemes": len(hist)}))
+        return 0
     t0 = time.time()
 
     def chunk(lo, hi):
@@ -65,7 +81,8 @@ def main(name, ckpt, shard=(0, 1)):
         return out
 
     lo, hi = sweep.shard_range(0, total, shard[0], shard[1])
-    run = sweep.CheckpointedSweep(lo, hi, 1 << 36, ckpt, chunk, tag=name)
+    run = sweep.CheckpointedSweep(lo, hi, 1 << 36, ckpt, chunk,
+                                  tag=name + ("/orbits" if orbits else ""))
     hist = run.run()
     assert run.done and sum(hist.values()) == hi - lo
     if shard[1] > 1:
@@ -103,9 +120,14 @@ if __name__ == "__main__":
     ap.add_argument("--shard", default="0/1", help="r/N: sweep shard r of N")
     ap.add_argument("--merge", nargs="+", metavar="CHECKPOINT",
                     help="merge finished shard checkpoints and compare with Fig. 2")
+    ap.add_argument("--orbits", action="store_true",
+                    help="sweep the TS_ENUM_ORBITS representatives (the same histogram)")
+    ap.add_argument("--limit", type=int, metavar="LOG2",
+                    help="only time the first 2^LOG2 classes of the shard")
     a = ap.parse_args()
     if a.merge:
         from paper_2604_09221_gb300 import sweep
-        sys.exit(report(a.name, sweep.merge_checkpoint_files(a.merge, 0, 1 << 42, tag=a.name)))
+        tag = a.name + ("/orbits" if a.orbits else "")
+        sys.exit(report(a.name, sweep.merge_checkpoint_files(a.merge, 0, 1 << 42, tag=tag)))
     r, n = (int(x) for x in a.shard.split("/"))
-    sys.exit(main(a.name, a.checkpoint or f"fig2_{a.name}.ckpt.json", (r, n)))
+    sys.exit(main(a.name, a.checkpoint or f"fig2_{a.name}.ckpt.json", (r, n), a.orbits, a.limit))

@@ -1,13 +1,15 @@
 // Test infrastructure: run the block sweep of a generated specialised source
 // (included as GEN) on the host, one lane at a time, for whole warps, and
 // compare each warp's histogram with the oracle's over the same masks.
-// Usage: run_block_sweep <edges file> <warps> [plain|flip|reduced|classify];
+// Usage: run_block_sweep <edges file> <warps> [plain|flip|reduced|orbits|classify];
 // the mask map of a warp is (h << oshift) | (t << ishift), t < 2^ib, as in
 // the sweeps without flags, with TS_ENUM_FLIP (bit 0 fixed) and with
-// TS_ENUM_REDUCED (bits 0, 1 and d + 1 fixed).  "classify" runs the per-mask
+// TS_ENUM_REDUCED (bits 0, 1 and d + 1 fixed), and blocks of TS_ENUM_ORBITS
+// (h the block's orbit high part, bit d + 1 fixed).  "classify" runs the per-mask
 // classifier tc_classify (query kernel, per-mask sweeps) on 64 x <warps>
 // random masks and the constant ones instead.  Exit status 0 when all match.
 #include "device_shims.h"
+#include "tc_layout.h"
 #include GEN
 extern "C" {
 #include "tcurve_oracle.h"
@@ -54,20 +56,26 @@ int main(int argc, char **argv) {
     printf("d=%d map=classify masks=%d differing=%d\n", d, n, bad);
     return bad != 0;
   }
-  unsigned ib = d + 1, oshift = d + 1, ishift = 0;
+  unsigned ib = d + 1, oshift = d + 1, ishift = 0, oflags = 0;
   if (mode == "flip") { ib = d; ishift = 1; }
   else if (mode == "reduced") { ib = d - 1; ishift = 2; oshift = d + 2; }
-  else if (mode != "plain") return 2;
+  else if (mode == "orbits") {  // blocks of orbit high parts (TS_ENUM_ORBITS)
+    int p1 = 0, p2 = 0;
+    if (!tc_orbit_pivots(d, &p1, &p2)) return 2;
+    oshift = d + 2;
+    oflags = 8u | ((unsigned)p1 << 8) | ((unsigned)p2 << 16);
+  } else if (mode != "plain") return 2;
   if (ib < 5) return 2;  // fewer middle-row patterns than lanes: no block sweep
   const unsigned ireps = (1u << ib) / 32u;
   std::vector<unsigned> scr((size_t)TcK::WORDS * TcK::THREADS + 64, 0xA5A5A5A5u);
   const unsigned npts = (d + 1) * (d + 2) / 2;
-  const unsigned long long hmax = 1ull << (npts - oshift);
+  const unsigned long long hmax = 1ull << (npts - oshift - (oflags ? 2 : 0));
   unsigned long long state = 12345;
   int bad = 0;
   for (int t = 0; t < nh; ++t) {
     state = state * 6364136223846793005ull + 1442695040888963407ull;
-    const unsigned long long h = t == 0 ? 0 : (t == 1 ? hmax - 1 : (state >> 11) % hmax);
+    const unsigned long long hb = t == 0 ? 0 : (t == 1 ? hmax - 1 : (state >> 11) % hmax);
+    const unsigned long long h = oflags ? tc_orbit_high(hb, oflags) : hb;  // as the kernel maps it
     std::vector<u64> hkeys(TcK::HASH, 0), gkeys(1 << 12, 0);
     std::vector<unsigned long long> hcnt(TcK::HASH, 0), gcnt(1 << 12, 0);
     u32 gerr = 0, err = 0;

@@ -140,3 +140,39 @@ def rohlin_viro(d: int, code: int) -> str:
     if d % 2:
         inner = "J" + (" + " + inner if inner else "")
     return f"<{inner or '0'}>"
+
+
+def orbit_pivots(d: int):
+    """The pivot bits (p1 > p2) of the high part of a mask for the orbit
+    sweep (TS_ENUM_ORBITS), from their definition: the class group's
+    elements that keep sigma(0, 1) = 0 add a + b i + c j with a = c, which on
+    the high bits (lattice points with j >= 1 other than (0, 1), bit
+    k(i, j) - d - 2) spans A = {i odd} and B = {j even}; the pivots are the
+    leading bits of A and B in echelon form."""
+    def k(i, j):
+        return j * (d + 1) - j * (j - 1) // 2 + i
+    a = b = 0
+    for j in range(1, d + 1):
+        for i in range(0, d + 1 - j):
+            if (i, j) == (0, 1):
+                continue
+            bit = k(i, j) - d - 2
+            a |= (i % 2) << bit
+            b |= (1 - j % 2) << bit
+    if b.bit_length() > a.bit_length():
+        a, b = b, a
+    if b.bit_length() == a.bit_length():
+        b ^= a
+    return a.bit_length() - 1, b.bit_length() - 1
+
+
+def orbit_mask(d: int, k: int) -> int:
+    """Mask m(k) of the orbit sweep: the middle-row pattern k mod 2^(d+1),
+    bit d + 1 clear, and the high part k >> (d + 1) with zero bits inserted
+    at the pivots (the lower one first)."""
+    p1, p2 = orbit_pivots(d)
+
+    def ins(x, p):
+        return ((x >> p) << (p + 1)) | (x & ((1 << p) - 1))
+    t, u = k & ((1 << (d + 1)) - 1), k >> (d + 1)
+    return (ins(ins(u, p2), p1) << (d + 2)) | t

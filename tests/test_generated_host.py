@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 import tcurve_inputs as ti
+from schemes import orbit_mask
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
@@ -52,6 +53,7 @@ def build_block_sweep(eng, tmp_path, d, edges, count_snap=False):
     exe = tmp_path / "run"
     cmd = ["g++", "-std=c++17", "-O1", "-w", f'-DGEN="{tmp_path / "gen.cu"}"', *flags,
            f"-I{os.path.join(HERE, 'host')}", f"-I{os.path.join(ROOT, 'oracle')}",
+           f"-I{os.path.join(ROOT, 'paper_2604_09221_gb300', 'csrc')}",
            "-o", str(exe), os.path.join(HERE, "host", "run_block_sweep.cpp"),
            "-x", "c", os.path.join(ROOT, "oracle", "tcurve_oracle.c"), "-x", "none", "-lpthread"]
     subprocess.run(cmd, check=True, capture_output=True)
@@ -69,10 +71,11 @@ def run_block_sweep(exe, tmp_path, warps, mode):
 @pytest.mark.parametrize("d,seed", [(4, 4), (5, 5), (7, 7), (8, 8), (9, 9)])
 def test_block_sweep_source_on_the_host(eng, tmp_path, d, seed):
     """Every mask map the block sweep serves: no flag (d + 1 middle-row bits),
-    TS_ENUM_FLIP (d) and TS_ENUM_REDUCED (d - 1), where 32 lanes fit; and the
-    per-mask classifier of the same source on random masks."""
+    TS_ENUM_FLIP (d), TS_ENUM_REDUCED (d - 1) and TS_ENUM_ORBITS (d + 1,
+    blocks of orbit high parts), where 32 lanes fit; and the per-mask
+    classifier of the same source on random masks."""
     exe = build_block_sweep(eng, tmp_path, d, ti.regular_triangulation(d, seed=seed))
-    for mode, ib in (("plain", d + 1), ("flip", d), ("reduced", d - 1)):
+    for mode, ib in (("plain", d + 1), ("flip", d), ("reduced", d - 1), ("orbits", d + 1)):
         if ib >= 5:
             run_block_sweep(exe, tmp_path, 6, mode)
     run_block_sweep(exe, tmp_path, 16, "classify")
@@ -182,8 +185,11 @@ def expected_mask_words(d, flags, k):
     """The masks of include/tcurve.h written out with Python integers: k;
     k << 1 (TS_ENUM_FLIP); k with zero bits inserted at positions 0, 1 and
     d + 1 (TS_ENUM_REDUCED); word w = splitmix64(k * W + w), bits >= |A|
-    cleared (TS_ENUM_SPLITMIX).  Words beyond the W sign words are dropped."""
+    cleared (TS_ENUM_SPLITMIX); schemes.orbit_mask (TS_ENUM_ORBITS, one
+    word).  Words beyond the W sign words are dropped."""
     W, npts, m64 = ti.sign_words(d), ti.num_points(d), (1 << 64) - 1
+    if flags == 8:
+        return [orbit_mask(d, k)] + [0] * (W - 1)
     if flags == 4:
         words = [ti.splitmix64_int((k * W + w) & m64) for w in range(W)]
         top = npts - 64 * (W - 1)
@@ -198,6 +204,29 @@ def expected_mask_words(d, flags, k):
     else:
         m = k
     return [(m >> (64 * w)) & m64 for w in range(W)]
+
+
+@pytest.mark.parametrize("d", [2, 3, 4, 5])
+def test_orbit_masks_are_one_per_class(d):
+    """TS_ENUM_ORBITS's masks over its whole range [0, 2^(|A|-3)) hold
+    exactly one sign distribution of every (Z/2)^3 class (Sec. 3: sigma ->
+    sigma + a + b i + c j mod 2), found by brute force over the group."""
+    npts = ti.num_points(d)
+    pts = [(i, j) for j in range(d + 1) for i in range(d + 1 - j)]   # bit k = index in this order
+    pats = []
+    for a in (0, 1):
+        for b in (0, 1):
+            for c in (0, 1):
+                pats.append(sum(((a + b * i + c * j) % 2) << k for k, (i, j) in enumerate(pts)))
+    assert len(set(pats)) == 8
+    seen = set()
+    for k in range(1 << (npts - 3)):
+        m = orbit_mask(d, k)
+        assert m < 1 << npts and not (m >> (d + 1)) & 1   # sigma(0, 1) = 0
+        cls = min(m ^ p for p in pats)
+        assert cls not in seen, (d, k)
+        seen.add(cls)
+    assert len(seen) == 1 << (npts - 3)
 
 
 @pytest.mark.skipif(shutil.which("g++") is None, reason="needs g++")
@@ -215,7 +244,9 @@ def test_sweep_mask_maps_on_the_host(tmp_path):
     for d in (4, 5, 9, 10, 11, 12, 15, 16):
         ks = {0, 1, 2, (1 << (d - 1)) - 1, 1 << (d - 1), (1 << 62) + 5, (1 << 63) - 1, 1 << 63,
               (1 << 64) - 1, *[int(x) for x in rng.integers(0, 1 << 63, 6, dtype=np.int64)]}
-        for flags in (0, 1, 2, 4):
+        for flags in (0, 1, 2, 4, 8):
+            if flags == 8 and ti.sign_words(d) > 1:
+                continue   # the orbit sweep: one sign word (d <= 9)
             for k in sorted(ks):
                 if ti.sign_words(d) == 1 and flags != 4 and k >= 1 << (ti.num_points(d) - 3):
                     continue   # one sign word: the ABI bounds the range so that masks fit

@@ -15,7 +15,7 @@ import numpy as np
 import pytest
 
 import tcurve_inputs as ti
-from schemes import check_classical
+from schemes import check_classical, orbit_mask
 
 pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -236,6 +236,40 @@ def test_flip_sweep_pairs_complementary_blocks(eng, orc, d):
     plain = gpu_hist(eng, tri, 0, 1 << N)
     flip = gpu_hist(eng, tri, 0, full, eng.TS_ENUM_FLIP)
     assert plain == collections.Counter({k: 2 * v for k, v in flip.items()})
+
+
+@pytest.mark.parametrize("kind", KINDS + ["warp"])
+def test_orbit_sweep(eng, orc, kind):
+    """TS_ENUM_ORBITS: over the whole range the histogram of TS_ENUM_REDUCED
+    (both pick one sign distribution per (Z/2)^3 class; d = 5, 6); over
+    ranges with ragged ends around whole blocks the oracle's histogram of the
+    same masks (d = 4, 7, 8, 9); refused for d = 1 and above d = 9."""
+    def loadk(d, e):
+        if kind != "warp":
+            return load(eng, d, e, kind)
+        t = eng.Triangulation(d, e)
+        t.set_kernel(eng.TS_KERNEL_WARP)
+        return t
+    for d in (5, 6):
+        e = ti.regular_triangulation(d, seed=90 + d)
+        tri = loadk(d, e)
+        full = 1 << (ti.num_points(d) - 3)
+        assert gpu_hist(eng, tri, 0, full, eng.TS_ENUM_ORBITS) == \
+            gpu_hist(eng, tri, 0, full, eng.TS_ENUM_REDUCED), d
+    for d in ((4, 7) if kind == "warp" else (4, 7, 8, 9)):
+        e = ti.regular_triangulation(d, seed=90 + d)
+        tri = loadk(d, e)
+        blk = 1 << (d + 1)
+        lo = 3 * blk + 77
+        hi = min(lo + 20 * blk + 999, 1 << (ti.num_points(d) - 3))
+        masks = np.array([orbit_mask(d, k) for k in range(lo, hi)], dtype=np.uint64).reshape(-1, 1)
+        assert gpu_hist(eng, tri, lo, hi, eng.TS_ENUM_ORBITS) == oracle_hist(orc, d, e, masks), d
+    for d, status in ((1, 1), (10, 8)):   # TS_EINVAL, TS_EUNSUPPORTED
+        t = eng.Triangulation(d, ti.standard_triangulation(d))
+        h = eng.Histogram(64, t.code_words)
+        with pytest.raises(eng.TSError) as err:
+            eng.enumerate_schemes(t, 0, 64, h, eng.TS_ENUM_ORBITS)
+        assert err.value.status == status
 
 
 @pytest.mark.parametrize("kind", KINDS)
