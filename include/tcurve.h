@@ -243,11 +243,16 @@ ts_status ts_hist_read(ts_hist *hist, uint64_t *codes, uint64_t *counts, uint64_
  * and adds each code to the job's own device histogram (room for
  * min(hist_capacity, counts[j]) distinct codes, hist_capacity <= 2^20); if code_outputs is
  * not NULL and code_outputs[j] is not NULL (device, counts[j] *
- * ts_code_words(tris[j]) uint64), it also stores every code there.  For each
- * degree present, one persistent kernel serves all jobs of that degree,
- * staging a job's tables into shared memory when it moves to that job; the
- * per-degree kernels run concurrently.  counts[j] <= 2^62 (TS_EINVAL above).  The triangulations must stay loaded
- * while the batch exists.  Allocates device memory at creation only. */
+ * ts_code_words(tris[j]) uint64), it also stores every code there.  By
+ * default, for each degree present one persistent kernel serves all jobs of
+ * that degree, staging a job's tables into shared memory when it moves to
+ * that job, and the per-degree kernels run concurrently
+ * (ts_batch_set_serial orders them; ts_batch_set_fused runs every job in
+ * one kernel).  counts[j] <= 2^62 (TS_EINVAL above).  The triangulations
+ * must stay loaded while the batch exists.  Allocates device memory at
+ * creation and when a tile or launch plan changes (ts_batch_set_tile,
+ * ts_batch_set_kernel, ts_batch_set_fused, ts_batch_set_fused_tile,
+ * ts_batch_set_signs), never in ts_batch_run. */
 typedef struct ts_batch ts_batch;
 ts_status ts_batch_create(int njobs, ts_tri *const *tris, const uint64_t *counts,
                           const uint64_t *bases, uint64_t *const *code_outputs,
