@@ -14,12 +14,16 @@ the enumeration kernel, the CPU oracle on a bounded sample, the plain
 one-launch query kernel (ts_real_schemes on materialised masks) beside the
 persistent sweep, SM clocks sampled during the timed region.
 
-The default line also carries a short serving run (Poisson job stream on the
+The default line also carries the d = 7 stretch sweep (all 2^35 classes of
+the global sign flip), the d = 4 and d = 6 plain query configurations, the
+mixed-degree batch and a short serving run (Poisson job stream on the
 continuous-batching server, p50/p99 job latency).  Other workloads:
 
   --workload mixed    the mixed-degree batch: 32 seeded triangulations for each
                       d in 5..10, sign-vector counts log-uniform in [2^10, 2^24],
-                      one CUDA-graph launch per step, autotuned tiles
+                      one CUDA-graph launch per step (the fastest of one fused
+                      persistent kernel and one kernel per degree), autotuned
+                      tiles
   --workload serving  a longer Poisson stream: d uniform in 6..16, 2^8..2^22
                       sign vectors per job, p50/p99 latency and schemes/s
 
