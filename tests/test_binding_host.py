@@ -1,6 +1,7 @@
 """Argument checks of the Python binding (no GPU needed).  The C ABI takes
 bare device pointers, so the binding refuses tensors of the wrong type or of
-too few words before it hands them to the library; these checks run before
+too few words (sign vectors, outputs, batch code outputs and batch jobs'
+own sign vectors) before it hands them to the library; these checks run before
 any library call, so CPU tensors and a triangulation object built without a
 device reach every one of them."""
 import pytest
@@ -53,3 +54,17 @@ def test_batch_rejects_mismatched_jobs_and_short_outputs():
     with pytest.raises(ValueError, match="79 words, 80 needed"):   # 20 vectors x 4 code words
         eng.Batch(tris, [10, 20], [0, 1],
                   code_outputs=[None, torch.zeros(79, dtype=torch.int64)])
+
+
+def test_batch_set_signs_rejects_bad_tensors():
+    import numpy as np
+    b = object.__new__(eng.Batch)
+    b._h = None
+    b.tris = [fake_tri(2, 2)]
+    b.counts = np.array([10], dtype=np.uint64)
+    with pytest.raises(ValueError, match="19 words, 20 needed"):   # 10 vectors x 2 sign words
+        b.set_signs(0, torch.zeros(19, dtype=torch.int64))
+    with pytest.raises(ValueError, match="64-bit integer"):
+        b.set_signs(0, torch.zeros(20, dtype=torch.int32))
+    with pytest.raises(ValueError, match="CUDA"):
+        b.set_signs(0, torch.zeros(20, dtype=torch.int64))
